@@ -1,0 +1,784 @@
+/*
+ * vk_oracle.c -- plain, slow CPU oracle for the topological Vicsek hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call this code:
+ * only the test suite, the package smoke check and the CPU-baseline leg of the
+ * benchmark load it.  It shares no source, header, table or helper with the
+ * CUDA implementation; both consume the same seeded integer inputs.
+ *
+ * What it computes (arxiv 2103.10239, "Non-metric interaction rules in models
+ * of active matter"):
+ *   - the k nearest neighbors of every particle in a periodic box, with no
+ *     distance cutoff (Sec. "Metric and topological flocking models": each
+ *     particle aligns with its k nearest neighbors regardless of distance),
+ *     by brute force over all pairs (the naive O(N^2) evaluation of Sec.
+ *     "Introduction");
+ *   - the Voronoi neighbors of every particle (Sec. "Computational tools:
+ *     Voronoi neighbor lists"): a Delaunay triangulation built by incremental
+ *     Bowyer-Watson insertion with exact integer orient/incircle predicates
+ *     (empty-circumcircle definition), from which an edge is kept iff its dual
+ *     Voronoi edge has positive length;
+ *   - one Vicsek update: the position step of Eq. (1) and the alignment rule of
+ *     Eq. (2), in FP64, with the noise drawn from Philox4x32-10 (Salmon, Moraes,
+ *     Dror & Shaw, SC'11) keyed by (seed) and countered by (id, step, replica);
+ *   - the polar order parameter |sum_i n_i| / N.
+ *
+ * Readings where the paper is silent (documented in the design notes):
+ *   - minimum image maps a difference into (-L/2, L/2];
+ *   - kNN order is (exact squared distance, id); self is excluded;
+ *   - the default noise is angular: theta = atan2(S) + eta*(u - 1/2);
+ *     Eq. (2)'s vectorial form is the alternative;
+ *   - advection uses the heading before the update (Eq. 1 literally), the step
+ *     s = fl32(v0*dt) * 2^F in grid units, rounded half-to-even to the grid.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+/* Status codes returned by the oracle entry points. */
+#define ORC_OK 0
+#define ORC_ERR_ARG 1
+#define ORC_ERR_OOM 2
+#define ORC_ERR_DEGENERATE 3
+#define ORC_ERR_INTERNAL 4
+
+/* ======================================================================== */
+/* Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64        */
+/* multiplies with the published multipliers and Weyl key increments.        */
+/* ======================================================================== */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u; /* golden ratio */
+      k1 += 0xBB67AE85u; /* sqrt(3) - 1 */
+    }
+    uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+    uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniform in [0,1) from the top 24 bits of a 32-bit word. */
+static double unit24(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0); }
+
+/* ======================================================================== */
+/* Periodic geometry on the integer grid                                     */
+/* ======================================================================== */
+
+/* Map a difference of two in-box coordinates into (-L/2, L/2]. */
+static int64_t min_image(int64_t d, int64_t L) {
+  if (2 * d > L) d -= L;
+  if (2 * d <= -L) d += L;
+  return d;
+}
+
+static uint64_t sqdist(int dim, const int32_t* a, const int32_t* b, const int64_t* box) {
+  uint64_t D = 0;
+  for (int ax = 0; ax < dim; ++ax) {
+    int64_t d = min_image((int64_t)b[ax] - (int64_t)a[ax], box[ax]);
+    D += (uint64_t)(d * d);
+  }
+  return D;
+}
+
+/* ======================================================================== */
+/* k nearest neighbors by brute force                                        */
+/* ======================================================================== */
+
+/* For each query particle q (all particles if query == NULL) write its k
+ * nearest other particles, ordered by (squared distance, id), into
+ * out[q*k .. q*k+k).  Requires 1 <= k <= n-1. */
+int orc_knn(int dim, int64_t n, const int32_t* pos, const int64_t* box, int k,
+            const int64_t* query, int64_t nq, int32_t* out) {
+  if (dim < 1 || dim > 3 || n < 2 || k < 1 || k > n - 1) return ORC_ERR_ARG;
+  for (int ax = 0; ax < dim; ++ax)
+    if (box[ax] < 1 || box[ax] > ((int64_t)1 << 31)) return ORC_ERR_ARG;
+  if (query == NULL) nq = n;
+  int bad = 0;
+#pragma omp parallel
+  {
+    uint64_t* bd = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)k);
+    int32_t* bi = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
+    if (!bd || !bi) {
+#pragma omp atomic write
+      bad = 1;
+    }
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t qq = 0; qq < nq; ++qq) {
+      if (!bd || !bi) continue;
+      int64_t i = query ? query[qq] : qq;
+      int filled = 0;
+      for (int64_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        uint64_t D = sqdist(dim, pos + i * dim, pos + j * dim, box);
+        /* keep the k smallest (D, j); j grows, so an equal D never displaces */
+        if (filled == k && D >= bd[k - 1]) continue;
+        int s = filled < k ? filled++ : k - 1;
+        while (s > 0 && bd[s - 1] > D) {
+          bd[s] = bd[s - 1];
+          bi[s] = bi[s - 1];
+          --s;
+        }
+        bd[s] = D;
+        bi[s] = (int32_t)j;
+      }
+      for (int s = 0; s < k; ++s) out[qq * k + s] = bi[s];
+    }
+    free(bd);
+    free(bi);
+  }
+  return bad ? ORC_ERR_OOM : ORC_OK;
+}
+
+/* ======================================================================== */
+/* Exact predicates on integer points                                        */
+/* ======================================================================== */
+
+/* orient(a,b,c) = sign of (b-a) x (c-a); |coords| < 2^37 keeps it in i128. */
+static int orient2(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t cx, int64_t cy) {
+  i128 v = (i128)(bx - ax) * (i128)(cy - ay) - (i128)(by - ay) * (i128)(cx - ax);
+  return (v > 0) - (v < 0);
+}
+
+/* Signed 256-bit integers, just enough for the incircle determinant. */
+typedef struct { uint64_t w[4]; } i256; /* two's complement, w[0] least significant */
+
+static i256 i256_zero(void) { i256 r = {{0, 0, 0, 0}}; return r; }
+
+static i256 i256_add(i256 a, i256 b) {
+  i256 r;
+  u128 carry = 0;
+  for (int t = 0; t < 4; ++t) {
+    u128 s = (u128)a.w[t] + (u128)b.w[t] + carry;
+    r.w[t] = (uint64_t)s;
+    carry = s >> 64;
+  }
+  return r;
+}
+
+static i256 i256_neg(i256 a) {
+  i256 r;
+  for (int t = 0; t < 4; ++t) r.w[t] = ~a.w[t];
+  i256 one = i256_zero();
+  one.w[0] = 1;
+  return i256_add(r, one);
+}
+
+/* Exact product of two signed 128-bit values with |a|,|b| < 2^127. */
+static i256 i256_mul(i128 a, i128 b) {
+  int neg = (a < 0) != (b < 0);
+  u128 ua = a < 0 ? (u128)(-a) : (u128)a;
+  u128 ub = b < 0 ? (u128)(-b) : (u128)b;
+  uint64_t a0 = (uint64_t)ua, a1 = (uint64_t)(ua >> 64);
+  uint64_t b0 = (uint64_t)ub, b1 = (uint64_t)(ub >> 64);
+  u128 p00 = (u128)a0 * b0, p01 = (u128)a0 * b1, p10 = (u128)a1 * b0, p11 = (u128)a1 * b1;
+  i256 r = i256_zero();
+  r.w[0] = (uint64_t)p00;
+  u128 mid = (p00 >> 64) + (uint64_t)p01 + (uint64_t)p10;
+  r.w[1] = (uint64_t)mid;
+  u128 hi = (mid >> 64) + (p01 >> 64) + (p10 >> 64) + (uint64_t)p11;
+  r.w[2] = (uint64_t)hi;
+  r.w[3] = (uint64_t)((hi >> 64) + (p11 >> 64));
+  return neg ? i256_neg(r) : r;
+}
+
+static int i256_sign(i256 a) {
+  if (a.w[3] >> 63) return -1;
+  return (a.w[0] | a.w[1] | a.w[2] | a.w[3]) ? 1 : 0;
+}
+
+/* incircle(a,b,c,d) > 0 iff d lies strictly inside the circle through a,b,c
+ * when a,b,c are counter-clockwise (the empty-circumcircle test). */
+static int incircle(const int64_t* a, const int64_t* b, const int64_t* c, const int64_t* d) {
+  i128 adx = a[0] - d[0], ady = a[1] - d[1];
+  i128 bdx = b[0] - d[0], bdy = b[1] - d[1];
+  i128 cdx = c[0] - d[0], cdy = c[1] - d[1];
+  i128 al = adx * adx + ady * ady;
+  i128 bl = bdx * bdx + bdy * bdy;
+  i128 cl = cdx * cdx + cdy * cdy;
+  i128 bc = bdx * cdy - bdy * cdx;
+  i128 ca = cdx * ady - cdy * adx;
+  i128 ab = adx * bdy - ady * bdx;
+  i256 det = i256_add(i256_add(i256_mul(al, bc), i256_mul(bl, ca)), i256_mul(cl, ab));
+  return i256_sign(det);
+}
+
+/* Exported for the tests: the same predicates on explicit points. */
+int orc_orient2d(const int64_t* a, const int64_t* b, const int64_t* c) {
+  return orient2(a[0], a[1], b[0], b[1], c[0], c[1]);
+}
+int orc_incircle(const int64_t* a, const int64_t* b, const int64_t* c, const int64_t* d) {
+  return incircle(a, b, c, d);
+}
+
+/* ======================================================================== */
+/* Bowyer-Watson Delaunay triangulation of a finite integer point set         */
+/* ======================================================================== */
+
+typedef struct {
+  int32_t v[3];  /* vertices, counter-clockwise */
+  int32_t nb[3]; /* nb[e] = triangle across the edge opposite v[e]; -1 = none */
+  int32_t alive;
+  int32_t mark;
+} tri_t;
+
+typedef struct {
+  int64_t* xy;   /* 2 * npts coordinates, the last three are the super-triangle */
+  int32_t npts;
+  tri_t* t;
+  int32_t nt, cap;
+  int32_t* freelist;
+  int32_t nfree;
+  int32_t stamp;
+  int32_t* stack;  /* scratch for the cavity search */
+  int32_t* cav;
+  int32_t scap;
+} dt_t;
+
+static int dt_newtri(dt_t* D) {
+  if (D->nfree > 0) return D->freelist[--D->nfree];
+  if (D->nt == D->cap) {
+    int32_t nc = D->cap * 2;
+    tri_t* nt = (tri_t*)realloc(D->t, sizeof(tri_t) * (size_t)nc);
+    int32_t* nf = (int32_t*)realloc(D->freelist, sizeof(int32_t) * (size_t)nc);
+    if (!nt || !nf) { if (nt) D->t = nt; if (nf) D->freelist = nf; return -1; }
+    D->t = nt;
+    D->freelist = nf;
+    D->cap = nc;
+  }
+  return D->nt++;
+}
+
+static const int64_t* P(const dt_t* D, int32_t v) { return D->xy + 2 * (int64_t)v; }
+
+static int tri_incircle(const dt_t* D, int32_t t, int32_t p) {
+  const tri_t* T = &D->t[t];
+  return incircle(P(D, T->v[0]), P(D, T->v[1]), P(D, T->v[2]), P(D, p));
+}
+
+static int grow_scratch(dt_t* D, int32_t need) {
+  if (need <= D->scap) return 0;
+  int32_t nc = D->scap * 2;
+  while (nc < need) nc *= 2;
+  int32_t* s = (int32_t*)realloc(D->stack, sizeof(int32_t) * (size_t)nc);
+  if (!s) return -1;
+  D->stack = s;
+  int32_t* c = (int32_t*)realloc(D->cav, sizeof(int32_t) * (size_t)nc);
+  if (!c) return -1;
+  D->cav = c;
+  D->scap = nc;
+  return 0;
+}
+
+/* Insert point p.  *hint is a live triangle to start the walk from; on return
+ * it holds one of the new triangles. */
+static int dt_insert(dt_t* D, int32_t p, int32_t* hint) {
+  const int64_t* q = P(D, p);
+  /* 1. locate: straight visibility walk (terminates on a Delaunay mesh) */
+  int32_t t = *hint;
+  int64_t guard = 0;
+  for (;;) {
+    if (++guard > 4 * (int64_t)D->nt + 64) return ORC_ERR_INTERNAL;
+    tri_t* T = &D->t[t];
+    int moved = 0;
+    for (int e = 0; e < 3; ++e) {
+      const int64_t* a = P(D, T->v[(e + 1) % 3]);
+      const int64_t* b = P(D, T->v[(e + 2) % 3]);
+      if (orient2(a[0], a[1], b[0], b[1], q[0], q[1]) < 0) {
+        if (T->nb[e] < 0) return ORC_ERR_INTERNAL; /* outside the super-triangle */
+        t = T->nb[e];
+        moved = 1;
+        break;
+      }
+    }
+    if (!moved) break;
+  }
+  for (int e = 0; e < 3; ++e) {
+    const int64_t* a = P(D, D->t[t].v[e]);
+    if (a[0] == q[0] && a[1] == q[1]) return ORC_ERR_DEGENERATE; /* coincident point */
+  }
+  /* 2. cavity: every triangle whose circumcircle strictly contains p,
+   *    grown from the containing triangle across shared edges */
+  D->stamp++;
+  int32_t ncav = 0, sp = 0;
+  if (grow_scratch(D, 16)) return ORC_ERR_OOM;
+  D->stack[sp++] = t;
+  D->t[t].mark = D->stamp;
+  while (sp > 0) {
+    int32_t c = D->stack[--sp];
+    if (grow_scratch(D, ncav + sp + 8)) return ORC_ERR_OOM;
+    D->cav[ncav++] = c;
+    for (int e = 0; e < 3; ++e) {
+      int32_t nb = D->t[c].nb[e];
+      if (nb < 0 || D->t[nb].mark == D->stamp) continue;
+      if (tri_incircle(D, nb, p) > 0) {
+        D->t[nb].mark = D->stamp;
+        D->stack[sp++] = nb;
+      }
+    }
+  }
+  /* 3. boundary edges (a -> b, counter-clockwise seen from inside) */
+  int32_t nbd = 0;
+  int32_t bcap = ncav + 2;
+  int32_t* ba = (int32_t*)malloc(sizeof(int32_t) * (size_t)bcap * 3);
+  if (!ba) return ORC_ERR_OOM;
+  int32_t* bb = ba + bcap;
+  int32_t* bo = bb + bcap;
+  for (int32_t ci = 0; ci < ncav; ++ci) {
+    tri_t* C = &D->t[D->cav[ci]];
+    for (int e = 0; e < 3; ++e) {
+      int32_t nb = C->nb[e];
+      if (nb >= 0 && D->t[nb].mark == D->stamp) continue;
+      if (nbd == bcap) { free(ba); return ORC_ERR_INTERNAL; }
+      ba[nbd] = C->v[(e + 1) % 3];
+      bb[nbd] = C->v[(e + 2) % 3];
+      bo[nbd] = nb;
+      ++nbd;
+    }
+  }
+  if (nbd != ncav + 2) { free(ba); return ORC_ERR_INTERNAL; }
+  /* 4. retriangulate the star-shaped cavity as a fan around p */
+  for (int32_t ci = 0; ci < ncav; ++ci) {
+    D->t[D->cav[ci]].alive = 0;
+    D->freelist[D->nfree++] = D->cav[ci];
+  }
+  int32_t* nt = (int32_t*)malloc(sizeof(int32_t) * (size_t)nbd);
+  if (!nt) { free(ba); return ORC_ERR_OOM; }
+  for (int32_t k = 0; k < nbd; ++k) {
+    int32_t id = dt_newtri(D);
+    if (id < 0) { free(ba); free(nt); return ORC_ERR_OOM; }
+    nt[k] = id;
+    tri_t* T = &D->t[id];
+    T->v[0] = p; T->v[1] = ba[k]; T->v[2] = bb[k];
+    T->nb[0] = bo[k]; T->nb[1] = -1; T->nb[2] = -1;
+    T->alive = 1;
+    T->mark = 0;
+    if (bo[k] >= 0) { /* re-point the outside neighbor at the new triangle */
+      tri_t* O = &D->t[bo[k]];
+      for (int e = 0; e < 3; ++e)
+        if (O->v[(e + 1) % 3] == bb[k] && O->v[(e + 2) % 3] == ba[k]) O->nb[e] = id;
+    }
+  }
+  for (int32_t k = 0; k < nbd; ++k) {
+    tri_t* T = &D->t[nt[k]];
+    for (int32_t m = 0; m < nbd; ++m) {
+      if (ba[m] == T->v[2]) T->nb[1] = nt[m]; /* across edge (b, p) */
+      if (bb[m] == T->v[1]) T->nb[2] = nt[m]; /* across edge (p, a) */
+    }
+  }
+  *hint = nt[0];
+  free(nt);
+  free(ba);
+  return ORC_OK;
+}
+
+static void dt_free(dt_t* D) {
+  free(D->t); free(D->freelist); free(D->stack); free(D->cav);
+}
+
+/* Triangulate npts points (coords in xy[0 .. 2*npts), xy must have room for
+ * three more points).  Insertion follows `order`. */
+static int dt_build(dt_t* D, int64_t* xy, int32_t npts, const int32_t* order) {
+  memset(D, 0, sizeof(*D));
+  D->xy = xy;
+  D->npts = npts;
+  const int64_t T0 = (int64_t)1 << 34; /* encloses [-2^34, 2^34)^2 */
+  xy[2 * (int64_t)npts + 0] = -T0;     xy[2 * (int64_t)npts + 1] = -T0;
+  xy[2 * (int64_t)npts + 2] = 3 * T0;  xy[2 * (int64_t)npts + 3] = -T0;
+  xy[2 * (int64_t)npts + 4] = -T0;     xy[2 * (int64_t)npts + 5] = 3 * T0;
+  D->cap = 2 * npts + 64;
+  D->t = (tri_t*)malloc(sizeof(tri_t) * (size_t)D->cap);
+  D->freelist = (int32_t*)malloc(sizeof(int32_t) * (size_t)D->cap);
+  D->scap = 64;
+  D->stack = (int32_t*)malloc(sizeof(int32_t) * 64);
+  D->cav = (int32_t*)malloc(sizeof(int32_t) * 64);
+  if (!D->t || !D->freelist || !D->stack || !D->cav) return ORC_ERR_OOM;
+  D->nt = 1;
+  tri_t* S = &D->t[0];
+  S->v[0] = npts; S->v[1] = npts + 1; S->v[2] = npts + 2;
+  S->nb[0] = S->nb[1] = S->nb[2] = -1;
+  S->alive = 1;
+  S->mark = 0;
+  int32_t hint = 0;
+  for (int32_t k = 0; k < npts; ++k) {
+    int rc = dt_insert(D, order[k], &hint);
+    if (rc) return rc;
+  }
+  return ORC_OK;
+}
+
+/* ======================================================================== */
+/* Periodic Voronoi neighbors                                                */
+/* ======================================================================== */
+
+typedef struct { int32_t a, b; } pair_t;
+
+static int cmp_pair(const void* x, const void* y) {
+  const pair_t* p = (const pair_t*)x;
+  const pair_t* q = (const pair_t*)y;
+  if (p->a != q->a) return p->a < q->a ? -1 : 1;
+  if (p->b != q->b) return p->b < q->b ? -1 : 1;
+  return 0;
+}
+
+/* Circumdisk of a triangle inside [xlo, xhi) x [ylo, yhi) (with a safety allowance)? */
+static int disk_inside(const int64_t* a, const int64_t* b, const int64_t* c, double xlo, double xhi,
+                       double ylo, double yhi) {
+  long double bx = (long double)(b[0] - a[0]), by = (long double)(b[1] - a[1]);
+  long double cx = (long double)(c[0] - a[0]), cy = (long double)(c[1] - a[1]);
+  long double d = 2.0L * (bx * cy - by * cx);
+  if (d == 0.0L) return 0;
+  long double b2 = bx * bx + by * by, c2 = cx * cx + cy * cy;
+  long double ux = (cy * b2 - by * c2) / d;
+  long double uy = (bx * c2 - cx * b2) / d;
+  long double R = sqrtl(ux * ux + uy * uy);
+  long double ox = (long double)a[0] + ux, oy = (long double)a[1] + uy;
+  long double tol = 1e-9L * (fabsl(ox) + fabsl(oy) + R) + 4.0L;
+  return ox - R - tol >= xlo && ox + R + tol < xhi && oy - R - tol >= ylo && oy + R + tol < yhi;
+}
+
+typedef struct {
+  int64_t* xy;
+  int32_t* orig;  /* original id of every tiled point */
+  int32_t npts;
+  dt_t D;
+  int built;
+} vtess_t;
+
+static void vtess_free(vtess_t* V) {
+  if (V->built) dt_free(&V->D);
+  free(V->xy);
+  free(V->orig);
+  memset(V, 0, sizeof(*V));
+}
+
+static uint64_t spread_bits(uint32_t v) { /* 16 -> 32 bit interleave helper */
+  uint64_t x = v & 0xFFFFu;
+  x = (x | (x << 8)) & 0x00FF00FFu;
+  x = (x | (x << 4)) & 0x0F0F0F0Fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x;
+}
+
+typedef struct { uint64_t key; int32_t idx; } keyed_t;
+static int cmp_keyed(const void* x, const void* y) {
+  const keyed_t* p = (const keyed_t*)x;
+  const keyed_t* q = (const keyed_t*)y;
+  if (p->key != q->key) return p->key < q->key ? -1 : 1;
+  return p->idx < q->idx ? -1 : (p->idx > q->idx);
+}
+
+/* Build the triangulation of the originals plus their periodic images within
+ * `margin` of the box, and check that every triangle touching an original
+ * point is a triangle of the periodic Delaunay triangulation.
+ * Returns ORC_OK, a failure code, or -1 if the margin was too small. */
+static int vtess_build(vtess_t* V, int64_t n, const int32_t* pos, const int64_t* box, int64_t margin) {
+  memset(V, 0, sizeof(*V));
+  int64_t Lx = box[0], Ly = box[1];
+  int64_t mx = margin < Lx ? margin : Lx, my = margin < Ly ? margin : Ly;
+  int64_t cap = 9 * n;
+  V->xy = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * cap + 6));
+  V->orig = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
+  if (!V->xy || !V->orig) return ORC_ERR_OOM;
+  int32_t m = 0;
+  /* originals first (indices 0..n-1), then images */
+  for (int pass = 0; pass < 2; ++pass)
+    for (int sy = -1; sy <= 1; ++sy)
+      for (int sx = -1; sx <= 1; ++sx) {
+        int center = (sx == 0 && sy == 0);
+        if ((pass == 0) != center) continue;
+        for (int64_t i = 0; i < n; ++i) {
+          int64_t x = (int64_t)pos[2 * i] + sx * Lx;
+          int64_t y = (int64_t)pos[2 * i + 1] + sy * Ly;
+          if (x < -mx || x >= Lx + mx || y < -my || y >= Ly + my) continue;
+          V->xy[2 * (int64_t)m] = x;
+          V->xy[2 * (int64_t)m + 1] = y;
+          V->orig[m] = (int32_t)i;
+          ++m;
+        }
+      }
+  V->npts = m;
+  /* spatially coherent insertion order (Morton order of a coarse grid) keeps
+   * the point-location walks short */
+  keyed_t* ks = (keyed_t*)malloc(sizeof(keyed_t) * (size_t)m);
+  int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)m);
+  if (!ks || !order) { free(ks); free(order); return ORC_ERR_OOM; }
+  long double spanx = (long double)(Lx + 2 * mx), spany = (long double)(Ly + 2 * my);
+  for (int32_t i = 0; i < m; ++i) {
+    uint32_t gx = (uint32_t)((long double)(V->xy[2 * (int64_t)i] + mx) / spanx * 65535.0L);
+    uint32_t gy = (uint32_t)((long double)(V->xy[2 * (int64_t)i + 1] + my) / spany * 65535.0L);
+    ks[i].key = spread_bits(gx) | (spread_bits(gy) << 1);
+    ks[i].idx = i;
+  }
+  qsort(ks, (size_t)m, sizeof(keyed_t), cmp_keyed);
+  for (int32_t i = 0; i < m; ++i) order[i] = ks[i].idx;
+  free(ks);
+  int rc = dt_build(&V->D, V->xy, m, order);
+  free(order);
+  V->built = 1;
+  if (rc) return rc;
+  /* verification of the stars of the originals */
+  double xlo = (double)(-mx), xhi = (double)(Lx + mx), ylo = (double)(-my), yhi = (double)(Ly + my);
+  for (int32_t t = 0; t < V->D.nt; ++t) {
+    tri_t* T = &V->D.t[t];
+    if (!T->alive) continue;
+    int touches = 0, super = 0;
+    for (int e = 0; e < 3; ++e) {
+      if (T->v[e] < n) touches = 1;
+      if (T->v[e] >= m) super = 1;
+    }
+    if (!touches) continue;
+    if (super) return -1;
+    if (!disk_inside(P(&V->D, T->v[0]), P(&V->D, T->v[1]), P(&V->D, T->v[2]), xlo, xhi, ylo, yhi))
+      return -1;
+  }
+  return ORC_OK;
+}
+
+static int vtess_build_auto(vtess_t* V, int64_t n, const int32_t* pos, const int64_t* box) {
+  int64_t L = box[0] > box[1] ? box[0] : box[1];
+  double spacing = sqrt((double)box[0] * (double)box[1] / (double)n);
+  int64_t margin = (int64_t)ceil(8.0 * spacing);
+  for (;;) {
+    if (margin > L) margin = L;
+    int rc = vtess_build(V, n, pos, box, margin);
+    if (rc == ORC_OK) return ORC_OK;
+    vtess_free(V);
+    if (rc > 0) return rc;
+    if (margin == L) return ORC_ERR_INTERNAL;
+    margin *= 2;
+  }
+}
+
+/* Voronoi neighbors of every particle in a periodic rectangular box.  On success
+ * offsets[0..n] is a CSR index into ids (sorted by id within a row).  If
+ * `cap` is too small, *nnz receives the size needed and ORC_ERR_ARG is
+ * returned with nothing written to ids. */
+int orc_voronoi(int64_t n, const int32_t* pos, const int64_t* box, int64_t* offsets,
+                int32_t* ids, int64_t cap, int64_t* nnz) {
+  if (n < 1 || box[0] < 2 || box[1] < 2 || box[0] > ((int64_t)1 << 31) || box[1] > ((int64_t)1 << 31))
+    return ORC_ERR_ARG;
+  for (int64_t i = 0; i < n; ++i)
+    if (pos[2 * i] < 0 || pos[2 * i] >= box[0] || pos[2 * i + 1] < 0 || pos[2 * i + 1] >= box[1])
+      return ORC_ERR_ARG;
+  vtess_t V;
+  int rc = vtess_build_auto(&V, n, pos, box);
+  if (rc) return rc;
+  dt_t* D = &V.D;
+  int64_t pcap = 8 * n + 64, np = 0;
+  pair_t* pr = (pair_t*)malloc(sizeof(pair_t) * (size_t)pcap);
+  if (!pr) { vtess_free(&V); return ORC_ERR_OOM; }
+  for (int32_t t = 0; t < D->nt; ++t) {
+    tri_t* T = &D->t[t];
+    if (!T->alive) continue;
+    for (int e = 0; e < 3; ++e) {
+      int32_t a = T->v[(e + 1) % 3], b = T->v[(e + 2) % 3];
+      if (a >= n) continue; /* only edges leaving an original point */
+      int32_t u = T->nb[e];
+      if (u < 0) { free(pr); vtess_free(&V); return ORC_ERR_INTERNAL; }
+      int32_t w = -1;
+      for (int f = 0; f < 3; ++f)
+        if (D->t[u].v[f] != a && D->t[u].v[f] != b) w = D->t[u].v[f];
+      /* the dual Voronoi edge has zero length iff the four points are cocircular */
+      if (incircle(P(D, T->v[0]), P(D, T->v[1]), P(D, T->v[2]), P(D, w)) == 0) continue;
+      int32_t jb = V.orig[b];
+      if (jb == a) continue; /* an image of the particle itself */
+      if (np == pcap) {
+        pcap *= 2;
+        pair_t* q = (pair_t*)realloc(pr, sizeof(pair_t) * (size_t)pcap);
+        if (!q) { free(pr); vtess_free(&V); return ORC_ERR_OOM; }
+        pr = q;
+      }
+      pr[np].a = a;
+      pr[np].b = jb;
+      ++np;
+    }
+  }
+  vtess_free(&V);
+  qsort(pr, (size_t)np, sizeof(pair_t), cmp_pair);
+  int64_t u = 0;
+  for (int64_t s = 0; s < np; ++s)
+    if (s == 0 || pr[s].a != pr[s - 1].a || pr[s].b != pr[s - 1].b) pr[u++] = pr[s];
+  *nnz = u;
+  if (ids == NULL) { free(pr); return ORC_OK; } /* size query */
+  if (u > cap) { free(pr); return ORC_ERR_ARG; }
+  int64_t s = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    offsets[i] = s;
+    while (s < u && pr[s].a == i) { ids[s] = pr[s].b; ++s; }
+  }
+  offsets[n] = s;
+  free(pr);
+  return ORC_OK;
+}
+
+/* The triangles of the periodic Delaunay triangulation that touch an original
+ * point, as tiled coordinates (6 int64 per triangle, counter-clockwise) and
+ * original ids (3 per triangle).  For the empty-circumcircle checks. */
+int orc_delaunay_star_triangles(int64_t n, const int32_t* pos, const int64_t* box,
+                                int64_t* coords, int32_t* tids, int64_t cap, int64_t* ntri) {
+  vtess_t V;
+  int rc = vtess_build_auto(&V, n, pos, box);
+  if (rc) return rc;
+  int64_t c = 0;
+  for (int32_t t = 0; t < V.D.nt; ++t) {
+    tri_t* T = &V.D.t[t];
+    if (!T->alive) continue;
+    if (T->v[0] >= n && T->v[1] >= n && T->v[2] >= n) continue;
+    if (c < cap) {
+      for (int e = 0; e < 3; ++e) {
+        coords[6 * c + 2 * e] = V.xy[2 * (int64_t)T->v[e]];
+        coords[6 * c + 2 * e + 1] = V.xy[2 * (int64_t)T->v[e] + 1];
+        tids[3 * c + e] = V.orig[T->v[e]];
+      }
+    }
+    ++c;
+  }
+  *ntri = c;
+  vtess_free(&V);
+  return c > cap ? ORC_ERR_ARG : ORC_OK;
+}
+
+/* ======================================================================== */
+/* One Vicsek update: Eq. (2) alignment + noise, Eq. (1) advection           */
+/* ======================================================================== */
+
+typedef struct {
+  int32_t dim;
+  int32_t frac_bits;
+  int32_t noise;        /* 0 angular (2D), 1 vectorial (Eq. 2) */
+  int32_t include_self; /* 0: sum over the neighbors only */
+  int32_t advect_new;   /* 0: Eq. (1) with n_i(t); 1: with n_i(t+dt) */
+  float v0, dt, eta;
+  uint64_t seed;
+} orc_params;
+
+/* pos (n*dim int32) and dir (n*dim float32) hold the state at step `step`;
+ * nb_off/nb_ids is the neighbor CSR in canonical order.  Writes the state at
+ * step+1: positions (exact), headings in FP64, and (2D) angles in [0, 2pi). */
+int orc_vicsek_step(const orc_params* prm, int64_t n, const int32_t* pos, const float* dir,
+                    const int64_t* box, const int64_t* nb_off, const int32_t* nb_ids,
+                    int64_t step, uint32_t replica, int32_t* pos_out, double* dir_out,
+                    double* theta_out) {
+  const int dim = prm->dim;
+  if (dim < 2 || dim > 3 || n < 1) return ORC_ERR_ARG;
+  if (dim == 3 && prm->noise == 0) return ORC_ERR_ARG;
+  /* grid step per unit heading: fl32(v0*dt) scaled by 2^F (exact) */
+  float vdt = prm->v0 * prm->dt;
+  double s = ldexp((double)vdt, prm->frac_bits);
+  const uint32_t key[2] = {(uint32_t)prm->seed, (uint32_t)(prm->seed >> 32)};
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double S[3] = {0.0, 0.0, 0.0};
+    int64_t m = 0;
+    if (prm->include_self) {
+      for (int a = 0; a < dim; ++a) S[a] += (double)dir[i * dim + a];
+      ++m;
+    }
+    for (int64_t q = nb_off[i]; q < nb_off[i + 1]; ++q) {
+      int64_t j = nb_ids[q];
+      for (int a = 0; a < dim; ++a) S[a] += (double)dir[j * dim + a];
+      ++m;
+    }
+    uint32_t ctr[4] = {(uint32_t)i, (uint32_t)step, replica, 0u}, w[4];
+    orc_philox4x32_10(ctr, key, w);
+    double u = unit24(w[0]), u1 = unit24(w[1]);
+    double nn[3] = {0.0, 0.0, 0.0};
+    if (prm->noise == 0) {
+      double th;
+      if (S[0] == 0.0 && S[1] == 0.0)
+        th = atan2((double)dir[i * dim + 1], (double)dir[i * dim]);
+      else
+        th = atan2(S[1], S[0]);
+      th += (double)prm->eta * (u - 0.5);
+      nn[0] = cos(th);
+      nn[1] = sin(th);
+    } else {
+      const double twopi = 6.283185307179586476925286766559;
+      double xi[3];
+      if (dim == 2) {
+        xi[0] = cos(twopi * u);
+        xi[1] = sin(twopi * u);
+        xi[2] = 0.0;
+      } else {
+        double z = 2.0 * u1 - 1.0, r = sqrt(fmax(0.0, 1.0 - z * z));
+        xi[0] = r * cos(twopi * u);
+        xi[1] = r * sin(twopi * u);
+        xi[2] = z;
+      }
+      double v[3], norm2 = 0.0;
+      for (int a = 0; a < dim; ++a) {
+        v[a] = (double)prm->eta * xi[a] + (m > 0 ? S[a] / (double)m : 0.0);
+        norm2 += v[a] * v[a];
+      }
+      if (norm2 == 0.0) {
+        for (int a = 0; a < dim; ++a) nn[a] = (double)dir[i * dim + a];
+      } else {
+        double inv = 1.0 / sqrt(norm2);
+        for (int a = 0; a < dim; ++a) nn[a] = v[a] * inv;
+      }
+    }
+    for (int a = 0; a < dim; ++a) {
+      dir_out[i * dim + a] = nn[a];
+      double h = prm->advect_new ? nn[a] : (double)dir[i * dim + a];
+      /* s*h is exact in FP64 (two 24-bit significands); round half to even */
+      double delta = nearbyint(s * h);
+      int64_t L = box[a];
+      int64_t p = ((int64_t)pos[i * dim + a] + (int64_t)delta) % L;
+      if (p < 0) p += L;
+      pos_out[i * dim + a] = (int32_t)p;
+    }
+    if (dim == 2 && theta_out) {
+      const double twopi = 6.283185307179586476925286766559;
+      double th = atan2(nn[1], nn[0]);
+      if (th < 0.0) th += twopi;
+      if (th >= twopi) th -= twopi;
+      theta_out[i] = th;
+    }
+  }
+  return ORC_OK;
+}
+
+/* Polar order parameter |sum_i n_i| / N in FP64. */
+double orc_order_parameter_f32(int dim, int64_t n, const float* dir) {
+  double S[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = 0; i < n; ++i)
+    for (int a = 0; a < dim; ++a) S[a] += (double)dir[i * dim + a];
+  double r = 0.0;
+  for (int a = 0; a < dim; ++a) r += S[a] * S[a];
+  return sqrt(r) / (double)n;
+}
+
+double orc_order_parameter_f64(int dim, int64_t n, const double* dir) {
+  double S[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = 0; i < n; ++i)
+    for (int a = 0; a < dim; ++a) S[a] += dir[i * dim + a];
+  double r = 0.0;
+  for (int a = 0; a < dim; ++a) r += S[a] * S[a];
+  return sqrt(r) / (double)n;
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

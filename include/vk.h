@@ -1,0 +1,201 @@
+/*
+ * vk.h -- C ABI of libvk_nm: non-metric (k-nearest and Voronoi) neighbor
+ * lists fused with the Vicsek alignment + position update, on one GB300.
+ *
+ * The method is the topological Vicsek model of arxiv 2103.10239 ("Non-metric
+ * interaction rules in models of active matter", Sec. "Metric and
+ * topological flocking models" and Sec. "Computational tools: Voronoi
+ * neighbor lists"):
+ *   Eq. (1)  Delta r_i = (v0 dt) n_i(t)
+ *   Eq. (2)  n_i(t+dt) = N( eta xi_i^t + (1/m_i^t) sum_<ij> n_j(t) )
+ * where the neighbors <ij> of particle i are either its k nearest particles
+ * at any distance (not reciprocal) or its Voronoi neighbors (reciprocal).
+ *
+ * Conventions shared by every call
+ *   - Positions are fixed-point grid coordinates: int32 pos_q in [0, L_q) per
+ *     axis, real coordinate = pos_q * 2^-F.  The box is periodic with edge
+ *     L_q <= 2^31 grid units (<= 2^30 for the Voronoi rule).  Distances use the
+ *     minimum image, differences mapped into (-L_q/2, L_q/2], and are compared
+ *     as exact integer squared distances D.
+ *   - kNN lists are ordered by (D, id) ascending (ties broken by the smaller
+ *     particle id); self is excluded.  Voronoi lists hold the ids whose
+ *     Voronoi cell shares an edge of positive length with the particle's cell
+ *     (Delaunay edges between cocircular points are dropped), sorted by id.
+ *   - Headings are FP32 unit vectors (the authoritative state).  In 2D the
+ *     angle theta = atan2(n_y, n_x) in [0, 2pi) is also exported.
+ *   - Noise: Philox4x32-10 keyed by the 64-bit seed, counter (particle id,
+ *     step, replica, 0); u = (word0 >> 8) * 2^-24.  Angular noise (2D
+ *     default): theta' = atan2(S) + eta (u - 1/2), S = sum of neighbor
+ *     headings.  Vectorial noise (Eq. 2 literally): n' = N(eta xi + S/m).
+ *   - Advection uses the heading before the update (Eq. 1): the grid step
+ *     Delta_q = round-half-even(s * n_a) with s = fl32(v0*dt) * 2^F, exact;
+ *     requires s <= 2^22.  Positions wrap modulo L_q.
+ *
+ * Memory and ownership
+ *   - Every array argument may be a host or a device pointer (detected with
+ *     cudaPointerGetAttributes).  The caller owns it; the library copies what
+ *     it needs before the call returns (device copies are stream-ordered).
+ *   - The library owns all device state of a vk_sim; vk_destroy frees it.
+ *   - All device work runs on the stream given at init (NULL: the library
+ *     creates its own non-blocking stream).  vk_step is asynchronous.
+ *
+ * Errors
+ *   - Every call returns a vk_status and never aborts.  Device-side failures
+ *     (capacity overflow, coincident points under the Voronoi rule) latch a
+ *     sticky status word on the device; it is returned by the next vk_sync or
+ *     vk_get_* call.  vk_last_error gives a message for the last failure.
+ */
+#ifndef VK_NM_H
+#define VK_NM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vk_sim vk_sim; /* opaque; owned by the library */
+
+typedef enum {
+  VK_OK = 0,
+  VK_ERR_ARG = 1,        /* invalid argument (null pointer, k >= N, bad rule ...) */
+  VK_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+  VK_ERR_OOM = 3,        /* device allocation failed */
+  VK_ERR_CAPACITY = 4,   /* an output buffer or an internal bound was too small */
+  VK_ERR_RANGE = 5,      /* box / fixed-point range outside the supported limits */
+  VK_ERR_DEGENERATE = 6, /* coincident points under the Voronoi rule */
+  VK_ERR_TIMEOUT = 7,    /* a bounded device wait gave up */
+  VK_ERR_STATE = 8       /* call not valid in the current state */
+} vk_status;
+
+typedef enum { VK_RULE_KNN = 0, VK_RULE_VORONOI = 1 } vk_rule;
+typedef enum { VK_NOISE_ANGULAR = 0, VK_NOISE_VECTORIAL = 1 } vk_noise;
+typedef enum { VK_SUM_PLAIN = 0, VK_SUM_COMPENSATED = 1, VK_SUM_FP64 = 2 } vk_sum_mode;
+typedef enum { VK_HEADING_DIR = 0, VK_HEADING_THETA = 1 } vk_heading_kind;
+
+/* Periodic box: dim (2 or 3), fractional bits F (0..30) and L_q per axis. */
+typedef struct {
+  int32_t dim;
+  int32_t frac_bits;
+  uint32_t box_q[3];
+} vk_box;
+
+/* Run parameters (Eq. 1 and Eq. 2).  eta is the noise strength: radians of
+ * the uniform angular kick in angular mode, the weight of the random unit
+ * vector in vectorial mode. */
+typedef struct {
+  int32_t rule;         /* vk_rule */
+  int32_t k;            /* neighbors for VK_RULE_KNN, 1..32, k <= N-1 */
+  float v0;             /* self-propulsion speed (length units per time) */
+  float dt;             /* time step */
+  float eta;            /* noise strength (per-replica values override in batches) */
+  uint64_t seed;        /* Philox key */
+  int32_t noise;        /* vk_noise; 3D requires VK_NOISE_VECTORIAL */
+  int32_t include_self; /* 1: add n_i(t) to the sum (default 0, Eq. 2 literally) */
+  int32_t advect_new;   /* 1: advect with n_i(t+dt) instead of n_i(t) (default 0) */
+  int32_t sum_mode;     /* vk_sum_mode for the heading sums (default compensated) */
+  float cell_occupancy; /* target particles per cell of the search grid; 0 = default */
+  int32_t phi_capacity; /* order-parameter history kept per replica; 0 = 4096 steps */
+} vk_params;
+
+/* Fills p with the defaults: kNN, k = 7, v0 = 0.5, dt = 1, eta = 0.3, seed = 1,
+ * angular noise, compensated sums, default cell occupancy and history. */
+void vk_default_params(vk_params* p);
+
+/* Create a simulation of one periodic system (Sec. "Metric and topological
+ * flocking models").  pos_q: n*dim int32, row-major (particle-major);
+ * heading: n*dim FP32 unit vectors (VK_HEADING_DIR) or n angles in radians
+ * (VK_HEADING_THETA, 2D only; converted on the device with sincosf).
+ * The particle id is the row index.  The step counter starts at 0. */
+vk_status vk_init(const int32_t* pos_q, const float* heading, int32_t heading_kind, int64_t n,
+                  const vk_box* box, const vk_params* params, void* cuda_stream, vk_sim** out);
+
+/* Create n_rep independent systems (replicas) that step together in one
+ * launch per kernel.  Replica r has n_r[r] particles stored contiguously in
+ * pos_q / heading after those of replicas 0..r-1, its own box boxes[r] and its
+ * own noise strength eta_r[r] (NULL: params->eta for all).  Particle ids are
+ * local to each replica (0..n_r-1); the replica index enters the noise
+ * counter.  All replicas share the other parameters and the dimension. */
+vk_status vk_batch_init(int32_t n_rep, const int64_t* n_r, const int32_t* pos_q,
+                        const float* heading, int32_t heading_kind, const vk_box* boxes,
+                        const float* eta_r, const vk_params* params, void* cuda_stream,
+                        vk_sim** out);
+
+/* Advance nsteps time steps of Alg. 1 (build the neighbor lists, align with
+ * noise, advect).  Asynchronous on the sim's stream. */
+vk_status vk_step(vk_sim* sim, int64_t nsteps);
+
+/* Neighbor lists of the CURRENT positions of one replica, in id order:
+ * offsets (n+1 int64, CSR) and ids (int32).  If ids_capacity is too small
+ * (or ids is NULL), *nnz_needed receives the count and VK_ERR_CAPACITY is
+ * returned (VK_OK when ids is NULL).  Synchronous. */
+vk_status vk_get_neighbors(vk_sim* sim, int32_t replica, int64_t* offsets, int32_t* ids,
+                           int64_t ids_capacity, int64_t* nnz_needed);
+
+/* Polar order parameter phi(t) = |sum_i n_i(t)| / N of one replica after
+ * each of the last *count steps (oldest first; at most phi_capacity and at
+ * most max_values are written).  Sums are FP32 compensated per block and FP64
+ * across blocks.  Synchronous. */
+vk_status vk_get_order_parameter(vk_sim* sim, int32_t replica, double* phi, int64_t max_values,
+                                 int64_t* count);
+
+/* Current state of one replica in id order: pos_q (n*dim int32), dir (n*dim
+ * FP32), theta (n FP32, 2D; may be NULL), step counter.  Any output may be
+ * NULL.  Synchronous. */
+vk_status vk_get_state(vk_sim* sim, int32_t replica, int32_t* pos_q, float* dir, float* theta,
+                       int64_t* step);
+
+/* Overwrite the state of one replica (id order) and, if step >= 0, the step
+ * counter of the whole simulation (teacher forcing, checkpoint resume). */
+vk_status vk_set_state(vk_sim* sim, int32_t replica, const int32_t* pos_q, const float* dir,
+                       int64_t step);
+
+/* Wait for the sim's stream and return the sticky device status. */
+vk_status vk_sync(vk_sim* sim);
+
+/* Message for the last failure of this sim (or of the last init when sim is
+ * NULL); never NULL. */
+const char* vk_last_error(const vk_sim* sim);
+const char* vk_status_string(int32_t status);
+
+void vk_destroy(vk_sim* sim);
+
+/* Capture vk_step's launches in CUDA graphs of `steps_per_graph` steps (0
+ * turns graphs off; default 0).  Each replay advances a device-side step
+ * counter, so a graph is reused for any number of steps. */
+vk_status vk_set_graph_steps(vk_sim* sim, int32_t steps_per_graph);
+
+/* Tracing: when enabled, vk_step launches kernels directly (no graph) and
+ * brackets every kernel phase with CUDA events on the sim's stream.
+ * vk_get_profile returns, per phase, the summed event time in ms and the
+ * launch count since profiling was enabled, plus the phase names. */
+vk_status vk_set_profiling(vk_sim* sim, int32_t enable);
+vk_status vk_get_profile(vk_sim* sim, double* ms, int64_t* launches, int32_t max_phases,
+                         int32_t* n_phases);
+const char* vk_phase_name(int32_t phase);
+
+/* Sizes chosen at init: total particles, replicas, cells of the search grid. */
+typedef struct {
+  int64_t n_total;
+  int32_t n_rep;
+  int32_t dim;
+  int64_t n_cells;
+  int64_t step;
+  int32_t kernels_per_step;
+  int32_t rule;
+  int32_t k;
+} vk_info;
+vk_status vk_get_info(vk_sim* sim, vk_info* out);
+
+/* Re-pick the search grid (particles per cell) by timing `trial_steps` steps
+ * for each candidate occupancy on a scratch copy of the state; the state and
+ * the step counter are restored afterwards.  Results never depend on the
+ * grid; only the speed does.  On return *best holds the chosen occupancy. */
+vk_status vk_autotune(vk_sim* sim, const float* candidates, int32_t n_candidates,
+                      int32_t trial_steps, float* best);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VK_NM_H */

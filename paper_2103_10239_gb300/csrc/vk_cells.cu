@@ -1,0 +1,316 @@
+// vk_cells.cu -- the cell-list build of the search grid (Sec. "Introduction":
+// partition the domain into cells so that only nearby cells are searched):
+// an atomic histogram of particles per cell, an exclusive scan of the counts,
+// and a scatter of the state into cell-sorted order.  Also the import/export
+// of user arrays (id order) to and from the sorted layout.
+#include "vk_internal.cuh"
+
+namespace vk {
+
+namespace {
+
+// user arrays (row-major, concatenated over replicas) -> U, with validation
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) load_kernel(const Rep* __restrict__ reps,
+                                                      const BlockTask* __restrict__ tasks,
+                                                      const int32_t* __restrict__ pos_in,
+                                                      const float* __restrict__ head_in, int heading_kind,
+                                                      typename Vec<DIM>::P* __restrict__ U_pos,
+                                                      typename Vec<DIM>::F* __restrict__ U_dir,
+                                                      int32_t* __restrict__ U_id, int32_t* status) {
+  using P = typename Vec<DIM>::P;
+  using F = typename Vec<DIM>::F;
+  const BlockTask t = tasks[blockIdx.x];
+  const Rep R = reps[t.rep];
+  const int li = t.first + (int)threadIdx.x;
+  if (li >= R.n) return;
+  const int64_t s = R.p0 + li;
+  int32_t p[3] = {0, 0, 0};
+  float h[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    p[a] = pos_in[s * DIM + a];
+    if (p[a] < 0 || (uint32_t)p[a] >= R.L[a]) set_status(status, kStRange);
+  }
+  if (heading_kind == 1) {
+    const float th = head_in[s];
+    if (!isfinite(th)) set_status(status, kStArg);
+    sincosf(th, &h[1], &h[0]);
+  } else {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      h[a] = head_in[s * DIM + a];
+      if (!isfinite(h[a])) set_status(status, kStArg);
+    }
+  }
+  U_pos[s] = make_p(p, (P*)nullptr);
+  U_dir[s] = make_f(h, (F*)nullptr);
+  U_id[s] = li;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) count_kernel(const Rep* __restrict__ reps,
+                                                       const BlockTask* __restrict__ tasks,
+                                                       const typename Vec<DIM>::P* __restrict__ U_pos,
+                                                       uint32_t* __restrict__ counts,
+                                                       uint32_t* __restrict__ U_rank) {
+  const BlockTask t = tasks[blockIdx.x];
+  const Rep R = reps[t.rep];
+  const int li = t.first + (int)threadIdx.x;
+  if (li >= R.n) return;
+  const int64_t s = R.p0 + li;
+  int32_t p[3];
+  unpack(U_pos[s], p);
+  U_rank[s] = atomicAdd(counts + linear_cell<DIM>(R, p), 1u);
+}
+
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kBlock * kScanItems;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t warp_tot[kBlock / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = lane < kBlock / 32 ? warp_tot[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kBlock / 32) warp_tot[lane] = w;  // inclusive warp prefix
+  }
+  __syncthreads();
+  const uint32_t before = (wid > 0 ? warp_tot[wid - 1] : 0u) + x - v;
+  *total = warp_tot[kBlock / 32 - 1];
+  __syncthreads();
+  return before;
+}
+
+__global__ void __launch_bounds__(kBlock) scan_reduce_kernel(const uint32_t* __restrict__ counts, int64_t n,
+                                                             uint32_t* __restrict__ bsum) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  uint32_t v = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    const int64_t c = base + (int64_t)j * kBlock + threadIdx.x;
+    if (c < n) v += counts[c];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __shared__ uint32_t w[kBlock / 32];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int i = 0; i < kBlock / 32; ++i) t += w[i];
+    bsum[blockIdx.x] = t;
+  }
+}
+
+// one block: exclusive scan of the block sums in place; writes the grand total
+__global__ void __launch_bounds__(kBlock) scan_bsum_kernel(uint32_t* __restrict__ bsum, int nb,
+                                                           uint32_t* __restrict__ offsets, int64_t n) {
+  uint32_t carry = 0;
+  for (int base = 0; base < nb; base += kBlock) {
+    const int i = base + (int)threadIdx.x;
+    const uint32_t v = i < nb ? bsum[i] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan(v, &tot);
+    if (i < nb) bsum[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) offsets[n] = carry;
+}
+
+// offsets[c] = exclusive prefix of counts; counts are cleared for the next step
+__global__ void __launch_bounds__(kBlock) scan_apply_kernel(uint32_t* __restrict__ counts, int64_t n,
+                                                            const uint32_t* __restrict__ bsum,
+                                                            uint32_t* __restrict__ offsets) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t tsum = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    const int64_t c = base + j;
+    v[j] = c < n ? counts[c] : 0u;
+    tsum += v[j];
+  }
+  uint32_t tot;
+  uint32_t run = bsum[blockIdx.x] + block_exclusive_scan(tsum, &tot);
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    const int64_t c = base + j;
+    if (c < n) {
+      offsets[c] = run;
+      counts[c] = 0u;
+    }
+    run += v[j];
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) scatter_kernel(const Rep* __restrict__ reps,
+                                                         const BlockTask* __restrict__ tasks,
+                                                         const typename Vec<DIM>::P* __restrict__ U_pos,
+                                                         const typename Vec<DIM>::F* __restrict__ U_dir,
+                                                         const int32_t* __restrict__ U_id,
+                                                         const uint32_t* __restrict__ U_rank,
+                                                         const uint32_t* __restrict__ offsets,
+                                                         typename Vec<DIM>::P* __restrict__ S_pos,
+                                                         typename Vec<DIM>::F* __restrict__ S_dir,
+                                                         int32_t* __restrict__ S_id, int advance_step,
+                                                         int64_t* d_step, double* phi_acc, int n_rep,
+                                                         int phi_cap) {
+  const BlockTask t = tasks[blockIdx.x];
+  const Rep R = reps[t.rep];
+  const int li = t.first + (int)threadIdx.x;
+  if (advance_step && blockIdx.x == 0) {
+    // clear the order-parameter slot of the next step, then advance the step
+    const int64_t nxt = *d_step + 1;
+    double* slot = phi_acc + (size_t)(nxt % phi_cap) * (size_t)n_rep * 3;
+    for (int i = threadIdx.x; i < n_rep * 3; i += blockDim.x) slot[i] = 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) *d_step = nxt;
+  }
+  if (li >= R.n) return;
+  const int64_t s = R.p0 + li;
+  const typename Vec<DIM>::P pv = U_pos[s];
+  int32_t p[3];
+  unpack(pv, p);
+  const uint32_t dst = offsets[linear_cell<DIM>(R, p)] + U_rank[s];
+  S_pos[dst] = pv;
+  S_dir[dst] = U_dir[s];
+  S_id[dst] = U_id[s];
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) export_state_kernel(
+    const typename Vec<DIM>::P* __restrict__ S_pos, const typename Vec<DIM>::F* __restrict__ S_dir,
+    const int32_t* __restrict__ S_id, int64_t p0, int32_t n, int32_t* __restrict__ pos_out,
+    float* __restrict__ dir_out, float* __restrict__ theta_out) {
+  const int li = blockIdx.x * kBlock + (int)threadIdx.x;
+  if (li >= n) return;
+  const int64_t s = p0 + li;
+  const int32_t id = S_id[s];
+  int32_t p[3];
+  float h[3];
+  unpack(S_pos[s], p);
+  unpack(S_dir[s], h);
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    if (pos_out) pos_out[(int64_t)id * DIM + a] = p[a];
+    if (dir_out) dir_out[(int64_t)id * DIM + a] = h[a];
+  }
+  if (DIM == 2 && theta_out) {
+    const float two_pi = 6.28318530717958647692f;
+    float th = atan2f(h[1], h[0]);
+    if (th < 0.f) th += two_pi;
+    if (th >= two_pi) th = 0.f;
+    theta_out[id] = th;
+  }
+}
+
+// user arrays of one replica (id order) -> U slots of that replica
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) import_state_kernel(
+    const int32_t* __restrict__ pos_in, const float* __restrict__ dir_in, int64_t p0, int32_t n,
+    const uint32_t* L, typename Vec<DIM>::P* __restrict__ U_pos, typename Vec<DIM>::F* __restrict__ U_dir,
+    int32_t* __restrict__ U_id, int32_t* status) {
+  using P = typename Vec<DIM>::P;
+  using F = typename Vec<DIM>::F;
+  const int li = blockIdx.x * kBlock + (int)threadIdx.x;
+  if (li >= n) return;
+  int32_t p[3] = {0, 0, 0};
+  float h[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    p[a] = pos_in[(int64_t)li * DIM + a];
+    h[a] = dir_in[(int64_t)li * DIM + a];
+    if (p[a] < 0 || (uint32_t)p[a] >= L[a]) set_status(status, kStRange);
+    if (!isfinite(h[a])) set_status(status, kStArg);
+  }
+  U_pos[p0 + li] = make_p(p, (P*)nullptr);
+  U_dir[p0 + li] = make_f(h, (F*)nullptr);
+  U_id[p0 + li] = li;
+}
+
+}  // namespace
+
+cudaError_t launch_load(const Geometry& g, const Buffers& b, const int32_t* pos_in, const float* head_in,
+                        int heading_kind, cudaStream_t st) {
+  if (g.dim == 2)
+    load_kernel<2><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, pos_in, head_in, heading_kind,
+                                                  (int2*)b.U_pos, (float2*)b.U_dir, b.U_id, b.d_status);
+  else
+    load_kernel<3><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, pos_in, head_in, heading_kind,
+                                                  (int4*)b.U_pos, (float4*)b.U_dir, b.U_id, b.d_status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count(const Geometry& g, const Buffers& b, cudaStream_t st) {
+  if (g.dim == 2)
+    count_kernel<2><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int2*)b.U_pos, b.counts, b.U_rank);
+  else
+    count_kernel<3><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int4*)b.U_pos, b.counts, b.U_rank);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const Geometry& g, const Buffers& b, cudaStream_t st) {
+  const int nb = (int)((g.n_cells + kScanTile - 1) / kScanTile);
+  scan_reduce_kernel<<<nb, kBlock, 0, st>>>(b.counts, g.n_cells, b.bsum);
+  scan_bsum_kernel<<<1, kBlock, 0, st>>>(b.bsum, nb, b.offsets, g.n_cells);
+  scan_apply_kernel<<<nb, kBlock, 0, st>>>(b.counts, g.n_cells, b.bsum, b.offsets);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const Geometry& g, const Buffers& b, const StepParams& P, int advance_step,
+                           cudaStream_t st) {
+  if (g.dim == 2)
+    scatter_kernel<2><<<g.n_tasks, kBlock, 0, st>>>(
+        g.reps, g.tasks, (const int2*)b.U_pos, (const float2*)b.U_dir, b.U_id, b.U_rank, b.offsets,
+        (int2*)b.S_pos, (float2*)b.S_dir, b.S_id, advance_step, b.d_step, b.phi_acc, P.n_rep, P.phi_cap);
+  else
+    scatter_kernel<3><<<g.n_tasks, kBlock, 0, st>>>(
+        g.reps, g.tasks, (const int4*)b.U_pos, (const float4*)b.U_dir, b.U_id, b.U_rank, b.offsets,
+        (int4*)b.S_pos, (float4*)b.S_dir, b.S_id, advance_step, b.d_step, b.phi_acc, P.n_rep, P.phi_cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_state(const Geometry& g, const Buffers& b, int rep, int64_t p0, int32_t n,
+                                int32_t* pos_out, float* dir_out, float* theta_out, cudaStream_t st) {
+  (void)rep;
+  const int nb = (n + kBlock - 1) / kBlock;
+  if (nb == 0) return cudaSuccess;
+  if (g.dim == 2)
+    export_state_kernel<2><<<nb, kBlock, 0, st>>>((const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id, p0, n,
+                                                   pos_out, dir_out, theta_out);
+  else
+    export_state_kernel<3><<<nb, kBlock, 0, st>>>((const int4*)b.S_pos, (const float4*)b.S_dir, b.S_id, p0, n,
+                                                   pos_out, dir_out, theta_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_import_state(const Geometry& g, const Buffers& b, int rep, int64_t p0, int32_t n,
+                                const int32_t* pos_in, const float* dir_in, cudaStream_t st) {
+  const int nb = (n + kBlock - 1) / kBlock;
+  if (nb == 0) return cudaSuccess;
+  const uint32_t* L = reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(g.reps + rep) +
+                                                        offsetof(Rep, L));
+  if (g.dim == 2)
+    import_state_kernel<2><<<nb, kBlock, 0, st>>>(pos_in, dir_in, p0, n, L, (int2*)b.U_pos, (float2*)b.U_dir,
+                                                   b.U_id, b.d_status);
+  else
+    import_state_kernel<3><<<nb, kBlock, 0, st>>>(pos_in, dir_in, p0, n, L, (int4*)b.U_pos, (float4*)b.U_dir,
+                                                   b.U_id, b.d_status);
+  return cudaGetLastError();
+}
+
+}  // namespace vk

@@ -1,0 +1,463 @@
+// vk_internal.cuh -- device-side building blocks shared by the libvk_nm kernels.
+//
+// Data layout (HBM, all replicas concatenated):
+//   * particle state in cell-sorted order (the "S" buffers): position as
+//     int2 (2D) / int4 (3D, w unused), heading as float2 / float4, replica-local
+//     id as int32;
+//   * the "U" buffers hold the next state in the order of S (written by the
+//     search+update kernel), plus the rank of each particle inside its new cell;
+//   * counts[c] / offsets[c] over the concatenated cells of all replicas; an
+//     exclusive scan of the counts gives global slot offsets directly;
+//   * a per-replica table (Rep) and a per-block task table (BlockTask), so a
+//     256-thread block never straddles two replicas.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vk {
+
+constexpr int kBlock = 256;
+constexpr int kMaxK = 32;
+
+// device status codes (same values as vk_status)
+enum : int32_t {
+  kStOk = 0,
+  kStCapacity = 4,
+  kStRange = 5,
+  kStDegenerate = 6,
+  kStArg = 1,
+};
+
+struct Rep {
+  int64_t p0;      // first slot of the replica in the particle arrays
+  int64_t c0;      // first cell of the replica in counts / offsets
+  int32_t n;       // particles
+  int32_t nc[3];   // cells per axis
+  uint32_t L[3];   // box edge per axis (grid units)
+  float eta;       // noise strength
+  float s;         // grid units per unit heading and step: fl32(v0*dt) * 2^F
+  uint32_t replica;
+};
+
+struct BlockTask {
+  int32_t rep;
+  int32_t first;  // replica-local index of the block's first particle
+};
+
+struct StepParams {
+  int32_t k;
+  int32_t noise;         // 0 angular, 1 vectorial
+  int32_t include_self;
+  int32_t advect_new;
+  int32_t sum_mode;      // 0 plain, 1 compensated, 2 fp64
+  uint32_t seed_lo, seed_hi;
+  int32_t n_rep;
+  int32_t phi_cap;
+};
+
+template <int DIM> struct Vec;
+template <> struct Vec<2> { using P = int2; using F = float2; };
+template <> struct Vec<3> { using P = int4; using F = float4; };
+
+template <int DIM> __device__ __forceinline__ int32_t comp(const typename Vec<DIM>::P& p, int a) {
+  return a == 0 ? p.x : (a == 1 ? p.y : reinterpret_cast<const int4&>(p).z);
+}
+
+__device__ __forceinline__ int2 make_p(const int32_t* v, int2*) { return make_int2(v[0], v[1]); }
+__device__ __forceinline__ int4 make_p(const int32_t* v, int4*) { return make_int4(v[0], v[1], v[2], 0); }
+__device__ __forceinline__ float2 make_f(const float* v, float2*) { return make_float2(v[0], v[1]); }
+__device__ __forceinline__ float4 make_f(const float* v, float4*) { return make_float4(v[0], v[1], v[2], 0.f); }
+__device__ __forceinline__ void unpack(const int2& p, int32_t* v) { v[0] = p.x; v[1] = p.y; }
+__device__ __forceinline__ void unpack(const int4& p, int32_t* v) { v[0] = p.x; v[1] = p.y; v[2] = p.z; }
+__device__ __forceinline__ void unpack(const float2& p, float* v) { v[0] = p.x; v[1] = p.y; }
+__device__ __forceinline__ void unpack(const float4& p, float* v) { v[0] = p.x; v[1] = p.y; v[2] = p.z; }
+
+// --------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), written for the device.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ float unit24(uint32_t w) {
+  return (float)(w >> 8) * 5.9604644775390625e-08f;  // exact: 24-bit integer * 2^-24
+}
+
+// --------------------------------------------------------------------------
+// Periodic integer geometry
+// --------------------------------------------------------------------------
+
+// cell index along one axis of a coordinate p in [0, L): floor(p * n / L)
+__device__ __forceinline__ int32_t cell_of(int32_t p, int32_t n, uint32_t L) {
+  return (int32_t)(((uint64_t)(uint32_t)p * (uint64_t)n) / (uint64_t)L);
+}
+
+// smallest unwrapped coordinate whose (unwrapped) cell index is >= b
+__device__ __forceinline__ int64_t cell_lo(int64_t b, int32_t n, int64_t L) {
+  int64_t q = b >= 0 ? b / n : -((-b + n - 1) / n);
+  int64_t r = b - q * n;
+  return q * L + (r * L + n - 1) / n;
+}
+
+// difference mapped into (-L/2, L/2]
+__device__ __forceinline__ int64_t min_image(int64_t d, int64_t L) {
+  if (2 * d > L) d -= L;
+  if (2 * d <= -L) d += L;
+  return d;
+}
+
+// ring r of the search block covers offsets [ring_lo, ring_hi] along an axis
+// of n cells, clamped so that no cell is visited twice
+__device__ __forceinline__ int ring_lo(int r, int n) { return -min(r, (n - 1) / 2); }
+__device__ __forceinline__ int ring_hi(int r, int n) { return min(r, n / 2); }
+
+// --------------------------------------------------------------------------
+// Eq. (1): exact grid step round-half-even(s * h) for |s| <= 2^22, |h| <= 1.
+// p = fl(s*h) and e = s*h - p (exact, from an FMA) decide the rounding of the
+// exact product; only a half-way p needs e.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ int32_t grid_step(float s, float h) {
+  const float p = __fmul_rn(s, h);
+  const float e = __fmaf_rn(s, h, -p);
+  float r = rintf(p);
+  if (fabsf(__fsub_rn(p, r)) == 0.5f) {
+    if (e > 0.f) r = __fadd_rn(p, 0.5f);
+    else if (e < 0.f) r = __fsub_rn(p, 0.5f);
+  }
+  return (int32_t)r;
+}
+
+// global cell index of a position in replica R (x fastest)
+template <int DIM>
+__device__ __forceinline__ int64_t linear_cell(const Rep& R, const int32_t* p) {
+  int64_t c = 0;
+#pragma unroll
+  for (int a = DIM - 1; a >= 0; --a) c = c * R.nc[a] + cell_of(p[a], R.nc[a], R.L[a]);
+  return R.c0 + c;
+}
+
+__device__ __forceinline__ int wrap_index(int x, int n) {
+  x %= n;
+  return x < 0 ? x + n : x;
+}
+
+__device__ __forceinline__ int32_t wrap_add(int32_t p, int32_t d, uint32_t L) {
+  int64_t q = ((int64_t)p + (int64_t)d) % (int64_t)L;
+  if (q < 0) q += (int64_t)L;
+  return (int32_t)q;
+}
+
+// --------------------------------------------------------------------------
+// Ring walk over the cells around a particle.  Ring r is the (2r+1)^DIM block
+// of cells minus the (2r-1)^DIM block, clamped per axis so that no cell is
+// visited twice in small boxes.  Each row segment of a ring is one contiguous
+// run [qb, qe) of the cell-sorted arrays and is handed to run(qb, qe).  After
+// ring r, stop(B2) is asked whether to stop, where B2 is the exact squared
+// distance from the particle to the nearest point outside the scanned block
+// (over the axes the block does not yet cover).  Returns true iff the whole
+// box was scanned.
+// --------------------------------------------------------------------------
+template <class RunFn>
+__device__ __forceinline__ void walk_row(const Rep& R, int cx, int a, int b, int64_t rowbase,
+                                         const uint32_t* __restrict__ off, RunFn& run) {
+  if (a > b) return;
+  const int nx = R.nc[0];
+  const int start = wrap_index(cx + a, nx);
+  const int len = b - a + 1;
+  const int end1 = min(start + len, nx);
+  run(off[rowbase + start], off[rowbase + end1]);
+  if (start + len > nx) run(off[rowbase], off[rowbase + start + len - nx]);
+}
+
+template <int DIM, class RunFn, class StopFn>
+__device__ __forceinline__ bool ring_walk(const Rep& R, const int32_t* pi, const uint32_t* __restrict__ off,
+                                          RunFn& run, StopFn& stop) {
+  int c[3] = {0, 0, 0};
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) c[a] = cell_of(pi[a], R.nc[a], R.L[a]);
+  for (int r = 0;; ++r) {
+    int lo[3], hi[3], plo[3], phi[3];
+    bool full_all = true, any_new = (r == 0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      lo[a] = ring_lo(r, R.nc[a]);
+      hi[a] = ring_hi(r, R.nc[a]);
+      plo[a] = r ? ring_lo(r - 1, R.nc[a]) : 1;
+      phi[a] = r ? ring_hi(r - 1, R.nc[a]) : 0;
+      full_all = full_all && (hi[a] - lo[a] + 1 == R.nc[a]);
+      any_new = any_new || lo[a] < plo[a] || hi[a] > phi[a];
+    }
+    if (!any_new) return true;
+    if (DIM == 2) {
+      for (int oy = lo[1]; oy <= hi[1]; ++oy) {
+        const int64_t rowbase = R.c0 + (int64_t)wrap_index(c[1] + oy, R.nc[1]) * R.nc[0];
+        if (oy < plo[1] || oy > phi[1]) {
+          walk_row(R, c[0], lo[0], hi[0], rowbase, off, run);
+        } else {
+          walk_row(R, c[0], lo[0], plo[0] - 1, rowbase, off, run);
+          walk_row(R, c[0], phi[0] + 1, hi[0], rowbase, off, run);
+        }
+      }
+    } else {
+      for (int oz = lo[2]; oz <= hi[2]; ++oz) {
+        const int64_t zb = (int64_t)wrap_index(c[2] + oz, R.nc[2]) * R.nc[1];
+        const bool oldz = !(oz < plo[2] || oz > phi[2]);
+        for (int oy = lo[1]; oy <= hi[1]; ++oy) {
+          const int64_t rowbase = R.c0 + (zb + wrap_index(c[1] + oy, R.nc[1])) * R.nc[0];
+          if (!oldz || oy < plo[1] || oy > phi[1]) {
+            walk_row(R, c[0], lo[0], hi[0], rowbase, off, run);
+          } else {
+            walk_row(R, c[0], lo[0], plo[0] - 1, rowbase, off, run);
+            walk_row(R, c[0], phi[0] + 1, hi[0], rowbase, off, run);
+          }
+        }
+      }
+    }
+    if (full_all) return true;
+    int64_t B = INT64_MAX;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      if (hi[a] - lo[a] + 1 == R.nc[a]) continue;
+      const int64_t bl = (int64_t)pi[a] - cell_lo((int64_t)c[a] - r, R.nc[a], R.L[a]) + 1;
+      const int64_t bh = cell_lo((int64_t)c[a] + r + 1, R.nc[a], R.L[a]) - (int64_t)pi[a];
+      B = min(B, min(bl, bh));
+    }
+    if (stop((uint64_t)B * (uint64_t)B)) return false;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Heading sums in the canonical neighbor order (plain / Neumaier / FP64)
+// --------------------------------------------------------------------------
+template <int DIM>
+struct HeadSum {
+  float s[DIM];
+  float c[DIM];
+  double d[DIM];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) { s[a] = 0.f; c[a] = 0.f; d[a] = 0.0; }
+  }
+  __device__ __forceinline__ void add(const float* v, int mode) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      if (mode == 2) {
+        d[a] += (double)v[a];
+      } else if (mode == 1) {
+        const float t = __fadd_rn(s[a], v[a]);
+        if (fabsf(s[a]) >= fabsf(v[a])) c[a] = __fadd_rn(c[a], __fadd_rn(__fsub_rn(s[a], t), v[a]));
+        else c[a] = __fadd_rn(c[a], __fadd_rn(__fsub_rn(v[a], t), s[a]));
+        s[a] = t;
+      } else {
+        s[a] = __fadd_rn(s[a], v[a]);
+      }
+    }
+  }
+};
+
+// --------------------------------------------------------------------------
+// Eq. (2) alignment + noise and Eq. (1) advection for one particle.
+// --------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ void align_advect(const Rep& R, const StepParams& P, uint32_t step,
+                                             int32_t id, const float* ni, const HeadSum<DIM>& H,
+                                             int m, const int32_t* pi, int32_t* pout, float* nout) {
+  const uint4 w = philox4x32_10(make_uint4((uint32_t)id, step, R.replica, 0u),
+                                make_uint2(P.seed_lo, P.seed_hi));
+  const float u = unit24(w.x);
+  if (P.sum_mode == 2) {
+    double S[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) S[a] = H.d[a];
+    if (P.noise == 0) {
+      double th = (S[0] == 0.0 && S[1] == 0.0) ? atan2((double)ni[1], (double)ni[0]) : atan2(S[1], S[0]);
+      th += (double)R.eta * ((double)u - 0.5);
+      double sn, cs;
+      sincos(th, &sn, &cs);
+      nout[0] = (float)cs;
+      nout[1] = (float)sn;
+    } else {
+      double xi[3];
+      double sx, cx;
+      sincospi(2.0 * (double)u, &sx, &cx);
+      if (DIM == 2) {
+        xi[0] = cx; xi[1] = sx; xi[2] = 0.0;
+      } else {
+        const double z = 2.0 * (double)unit24(w.y) - 1.0, r = sqrt(fmax(0.0, 1.0 - z * z));
+        xi[0] = r * cx; xi[1] = r * sx; xi[2] = z;
+      }
+      double v[DIM], n2 = 0.0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        v[a] = (double)R.eta * xi[a] + (m > 0 ? S[a] / (double)m : 0.0);
+        n2 += v[a] * v[a];
+      }
+      if (n2 == 0.0) {
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) nout[a] = ni[a];
+      } else {
+        const double inv = 1.0 / sqrt(n2);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) nout[a] = (float)(v[a] * inv);
+      }
+    }
+  } else {
+    float S[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) S[a] = (P.sum_mode == 1) ? __fadd_rn(H.s[a], H.c[a]) : H.s[a];
+    if (P.noise == 0) {
+      float th = (S[0] == 0.f && S[1] == 0.f) ? atan2f(ni[1], ni[0]) : atan2f(S[1], S[0]);
+      th = th + R.eta * (u - 0.5f);
+      float sn, cs;
+      sincosf(th, &sn, &cs);
+      nout[0] = cs;
+      nout[1] = sn;
+    } else {
+      float xi[3];
+      float sx, cx;
+      sincospif(2.0f * u, &sx, &cx);
+      if (DIM == 2) {
+        xi[0] = cx; xi[1] = sx; xi[2] = 0.f;
+      } else {
+        const float z = 2.0f * unit24(w.y) - 1.0f, r = sqrtf(fmaxf(0.f, 1.0f - z * z));
+        xi[0] = r * cx; xi[1] = r * sx; xi[2] = z;
+      }
+      float v[DIM], n2 = 0.f;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        v[a] = R.eta * xi[a] + (m > 0 ? S[a] / (float)m : 0.f);
+        n2 += v[a] * v[a];
+      }
+      if (n2 == 0.f) {
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) nout[a] = ni[a];
+      } else {
+        const float nrm = sqrtf(n2);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) nout[a] = v[a] / nrm;
+      }
+    }
+  }
+  const float* h = P.advect_new ? nout : ni;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) pout[a] = wrap_add(pi[a], grid_step(R.s, h[a]), R.L[a]);
+}
+
+// --------------------------------------------------------------------------
+// Order parameter: compensated FP32 block partials -> FP64 atomics
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Block-wide compensated sum of v[0..DIM) over the block; thread 0 adds the
+// result into acc[0..DIM) with FP64 atomics.  All threads must call it.
+template <int DIM>
+__device__ __forceinline__ void block_phi_accumulate(const float* v, double* acc) {
+  __shared__ float sh_s[kBlock / 32][3];
+  __shared__ float sh_c[kBlock / 32][3];
+  float s[DIM], c[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) { s[a] = v[a]; c[a] = 0.f; }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const float os = __shfl_xor_sync(0xffffffffu, s[a], o);
+      const float oc = __shfl_xor_sync(0xffffffffu, c[a], o);
+      float t, e;
+      two_sum(s[a], os, t, e);
+      s[a] = t;
+      c[a] = __fadd_rn(__fadd_rn(c[a], oc), e);
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) { sh_s[wid][a] = s[a]; sh_c[wid][a] = c[a]; }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      double t = 0.0;
+      for (int w2 = 0; w2 < kBlock / 32; ++w2) t += (double)sh_s[w2][a] + (double)sh_c[w2][a];
+      atomicAdd(acc + a, t);
+    }
+  }
+}
+
+__device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
+  atomicCAS(status, 0, code);
+}
+
+}  // namespace vk
+
+// host-side launchers (defined in the .cu files)
+namespace vk {
+
+struct Buffers {
+  // sorted current state
+  void* S_pos;
+  void* S_dir;
+  int32_t* S_id;
+  // next state in S order + rank in the new cell
+  void* U_pos;
+  void* U_dir;
+  int32_t* U_id;
+  uint32_t* U_rank;
+  uint32_t* counts;   // n_cells
+  uint32_t* offsets;  // n_cells + 1
+  uint32_t* bsum;     // scan block sums
+  double* phi_acc;    // phi_cap * n_rep * 3
+  int64_t* d_step;
+  int32_t* d_status;
+};
+
+struct Geometry {
+  int dim;
+  int rule;
+  int n_rep;
+  int64_t n_total;
+  int64_t n_cells;
+  int n_tasks;
+  const Rep* reps;
+  const BlockTask* tasks;
+};
+
+// vk_cells.cu
+cudaError_t launch_load(const Geometry& g, const Buffers& b, const int32_t* pos_in, const float* head_in,
+                        int heading_kind, cudaStream_t st);
+cudaError_t launch_count(const Geometry& g, const Buffers& b, cudaStream_t st);
+cudaError_t launch_scan(const Geometry& g, const Buffers& b, cudaStream_t st);
+cudaError_t launch_scatter(const Geometry& g, const Buffers& b, const StepParams& P, int advance_step,
+                           cudaStream_t st);
+cudaError_t launch_export_state(const Geometry& g, const Buffers& b, int rep, int64_t p0, int32_t n,
+                                int32_t* pos_out, float* dir_out, float* theta_out, cudaStream_t st);
+cudaError_t launch_import_state(const Geometry& g, const Buffers& b, int rep, int64_t p0, int32_t n,
+                                const int32_t* pos_in, const float* dir_in, cudaStream_t st);
+
+// vk_knn.cu
+cudaError_t launch_knn_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st);
+cudaError_t launch_knn_export(const Geometry& g, const Buffers& b, int k, int rep, int n, int32_t* out,
+                              cudaStream_t st);
+
+// vk_voronoi.cu
+cudaError_t launch_voronoi_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st);
+cudaError_t launch_voronoi_export(const Geometry& g, const Buffers& b, int rep, int n, int32_t* deg,
+                                  int32_t* nbr, cudaStream_t st);
+constexpr int kVoronoiMaxDeg = 32;
+
+}  // namespace vk

@@ -1,0 +1,207 @@
+// vk_knn.cu -- k-nearest-neighbor rule (Sec. "Metric and topological flocking
+// models": each particle aligns with its k nearest neighbors, at any distance,
+// so the relation is not reciprocal) fused with the Vicsek update of Eq. (1)
+// and Eq. (2).
+//
+// One thread per particle, in cell-sorted order.  The search walks rings of
+// cells around the particle's cell; each row segment of a ring is one
+// contiguous run of the sorted arrays.  The k best (exact int64 squared
+// distance, id) pairs live in registers, sorted.  After ring r the search
+// stops once the k-th best distance is below the exact integer distance from
+// the particle to the boundary of the scanned (2r+1)^d block.
+#include <climits>
+
+#include "vk_internal.cuh"
+
+namespace vk {
+
+namespace {
+
+// Top-k list of KC register slots.  For k < KC the first KC-k slots hold
+// sentinels that order before every real candidate, so the threshold is
+// always slot KC-1 and no register array is indexed dynamically.
+template <int KC>
+struct TopK {
+  uint64_t d[KC];
+  int32_t id[KC];
+  int32_t slot[KC];
+};
+
+template <int KC>
+__device__ __forceinline__ void topk_init(TopK<KC>& T, int k) {
+#pragma unroll
+  for (int s = 0; s < KC; ++s) {
+    const bool sentinel = s < KC - k;
+    T.d[s] = sentinel ? 0ull : ~0ull;
+    T.id[s] = sentinel ? INT_MIN : INT_MAX;
+    T.slot[s] = -1;
+  }
+}
+
+template <int KC>
+__device__ __forceinline__ void topk_insert(TopK<KC>& T, uint64_t D, int32_t idj, int32_t q) {
+  bool placed = false;
+#pragma unroll
+  for (int s = KC - 1; s > 0; --s) {
+    const bool before = (D < T.d[s - 1]) || (D == T.d[s - 1] && idj < T.id[s - 1]);
+    if (!placed) {
+      if (before) {
+        T.d[s] = T.d[s - 1];
+        T.id[s] = T.id[s - 1];
+        T.slot[s] = T.slot[s - 1];
+      } else {
+        T.d[s] = D;
+        T.id[s] = idj;
+        T.slot[s] = q;
+        placed = true;
+      }
+    }
+  }
+  if (!placed) {
+    T.d[0] = D;
+    T.id[0] = idj;
+    T.slot[0] = q;
+  }
+}
+
+template <int DIM, int KC>
+__device__ __forceinline__ void knn_search(const Rep& R, int64_t self, const int32_t* pi,
+                                           const typename Vec<DIM>::P* __restrict__ pos,
+                                           const int32_t* __restrict__ ids, const uint32_t* __restrict__ off,
+                                           TopK<KC>& T) {
+  auto run = [&](uint32_t qb, uint32_t qe) {
+    for (uint32_t q = qb; q < qe; ++q) {
+      if ((int64_t)q == self) continue;
+      int32_t pj[3];
+      unpack(pos[q], pj);
+      uint64_t D = 0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const int64_t d = min_image((int64_t)pj[a] - (int64_t)pi[a], (int64_t)R.L[a]);
+        D += (uint64_t)(d * d);
+      }
+      if (D <= T.d[KC - 1]) {
+        const int32_t idj = ids[q];
+        if (D < T.d[KC - 1] || idj < T.id[KC - 1]) topk_insert<KC>(T, D, idj, (int32_t)q);
+      }
+    }
+  };
+  // every unscanned particle is at squared distance >= B2: stop once the
+  // k-th best is strictly closer (an equal distance could still win on id)
+  auto stop = [&](uint64_t B2) { return T.d[KC - 1] < B2; };
+  ring_walk<DIM>(R, pi, off, run, stop);
+}
+
+template <int DIM, int KC>
+__global__ void __launch_bounds__(kBlock) knn_step_kernel(
+    const Rep* __restrict__ reps, const BlockTask* __restrict__ tasks,
+    const typename Vec<DIM>::P* __restrict__ S_pos, const typename Vec<DIM>::F* __restrict__ S_dir,
+    const int32_t* __restrict__ S_id, const uint32_t* __restrict__ off, typename Vec<DIM>::P* __restrict__ U_pos,
+    typename Vec<DIM>::F* __restrict__ U_dir, int32_t* __restrict__ U_id, uint32_t* __restrict__ U_rank,
+    uint32_t* __restrict__ counts, double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P) {
+  using PV = typename Vec<DIM>::P;
+  using FV = typename Vec<DIM>::F;
+  const BlockTask t = tasks[blockIdx.x];
+  const Rep R = reps[t.rep];
+  const int li = t.first + (int)threadIdx.x;
+  const int64_t step = *d_step;
+  float nnew[3] = {0.f, 0.f, 0.f};
+  if (li < R.n) {
+    const int64_t s = R.p0 + li;
+    int32_t pi[3] = {0, 0, 0};
+    float ni[3] = {0.f, 0.f, 0.f};
+    unpack(S_pos[s], pi);
+    unpack(S_dir[s], ni);
+    const int32_t id = S_id[s];
+    TopK<KC> T;
+    topk_init<KC>(T, P.k);
+    knn_search<DIM, KC>(R, s, pi, S_pos, S_id, off, T);
+    HeadSum<DIM> H;
+    H.init();
+    if (P.include_self) H.add(ni, P.sum_mode);
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+      if (j >= KC - P.k) {
+        float v[3];
+        unpack(S_dir[T.slot[j]], v);
+        H.add(v, P.sum_mode);
+      }
+    }
+    int32_t pout[3] = {0, 0, 0};
+    align_advect<DIM>(R, P, (uint32_t)step, id, ni, H, P.k + (P.include_self ? 1 : 0), pi, pout, nnew);
+    U_pos[s] = make_p(pout, (PV*)nullptr);
+    U_dir[s] = make_f(nnew, (FV*)nullptr);
+    U_id[s] = id;
+    U_rank[s] = atomicAdd(counts + linear_cell<DIM>(R, pout), 1u);
+  }
+  block_phi_accumulate<DIM>(nnew, phi_acc + ((size_t)(step % P.phi_cap) * (size_t)P.n_rep + (size_t)t.rep) * 3);
+}
+
+// neighbor lists of the current positions of one replica, written by id
+template <int DIM, int KC>
+__global__ void __launch_bounds__(kBlock) knn_export_kernel(const Rep* __restrict__ reps, int rep,
+                                                            const typename Vec<DIM>::P* __restrict__ S_pos,
+                                                            const int32_t* __restrict__ S_id,
+                                                            const uint32_t* __restrict__ off, int k,
+                                                            int32_t* __restrict__ out) {
+  const Rep R = reps[rep];
+  const int li = blockIdx.x * kBlock + (int)threadIdx.x;
+  if (li >= R.n) return;
+  const int64_t s = R.p0 + li;
+  int32_t pi[3] = {0, 0, 0};
+  unpack(S_pos[s], pi);
+  const int32_t id = S_id[s];
+  TopK<KC> T;
+  topk_init<KC>(T, k);
+  knn_search<DIM, KC>(R, s, pi, S_pos, S_id, off, T);
+#pragma unroll
+  for (int j = 0; j < KC; ++j)
+    if (j >= KC - k) out[(int64_t)id * k + (j - (KC - k))] = T.id[j];
+}
+
+template <int DIM, int KC>
+cudaError_t step_dispatch(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st) {
+  using PV = typename Vec<DIM>::P;
+  using FV = typename Vec<DIM>::F;
+  knn_step_kernel<DIM, KC><<<g.n_tasks, kBlock, 0, st>>>(
+      g.reps, g.tasks, (const PV*)b.S_pos, (const FV*)b.S_dir, b.S_id, b.offsets, (PV*)b.U_pos, (FV*)b.U_dir,
+      b.U_id, b.U_rank, b.counts, b.phi_acc, b.d_step, P);
+  return cudaGetLastError();
+}
+
+template <int DIM, int KC>
+cudaError_t export_dispatch(const Geometry& g, const Buffers& b, int k, int rep, int n, int32_t* out,
+                            cudaStream_t st) {
+  using PV = typename Vec<DIM>::P;
+  const int nb = (n + kBlock - 1) / kBlock;
+  if (nb == 0) return cudaSuccess;
+  knn_export_kernel<DIM, KC><<<nb, kBlock, 0, st>>>(g.reps, rep, (const PV*)b.S_pos, b.S_id, b.offsets, k, out);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_knn_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st) {
+  if (g.dim == 2) {
+    if (P.k <= 8) return step_dispatch<2, 8>(g, b, P, st);
+    if (P.k <= 16) return step_dispatch<2, 16>(g, b, P, st);
+    return step_dispatch<2, 32>(g, b, P, st);
+  }
+  if (P.k <= 8) return step_dispatch<3, 8>(g, b, P, st);
+  if (P.k <= 16) return step_dispatch<3, 16>(g, b, P, st);
+  return step_dispatch<3, 32>(g, b, P, st);
+}
+
+cudaError_t launch_knn_export(const Geometry& g, const Buffers& b, int k, int rep, int n, int32_t* out,
+                              cudaStream_t st) {
+  if (g.dim == 2) {
+    if (k <= 8) return export_dispatch<2, 8>(g, b, k, rep, n, out, st);
+    if (k <= 16) return export_dispatch<2, 16>(g, b, k, rep, n, out, st);
+    return export_dispatch<2, 32>(g, b, k, rep, n, out, st);
+  }
+  if (k <= 8) return export_dispatch<3, 8>(g, b, k, rep, n, out, st);
+  if (k <= 16) return export_dispatch<3, 16>(g, b, k, rep, n, out, st);
+  return export_dispatch<3, 32>(g, b, k, rep, n, out, st);
+}
+
+}  // namespace vk

@@ -1,0 +1,128 @@
+"""GPU parity of the update rule (Eq. 1 and Eq. 2) in every mode, the
+order parameter, determinism, checkpoint/resume and CUDA-graph replay."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_10239_gb300 import vk
+from paper_2103_10239_gb300 import workloads as W
+from parity import check_step, angle_between, PHI_TOL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("mode", [
+    dict(), dict(noise="vectorial"), dict(include_self=True), dict(sum_mode="plain"),
+    dict(sum_mode="fp64"), dict(advect_new=True), dict(noise="vectorial", include_self=True),
+])
+def test_update_modes_teacher_forced(mode):
+    w = W.uniform_system(1500, 38.7, 16, 2, input_seed=11, rule="knn", k=7, v0=0.5, eta=0.6)
+    kw = {k: v for k, v in mode.items()}
+    if "noise" in kw:
+        w.noise = kw["noise"]
+    with vk.from_workload(w, **kw) as sim:
+        for _ in range(4):
+            check_step(sim, w, "knn", include_self=kw.get("include_self", False),
+                       advect_new=kw.get("advect_new", False))
+
+
+def test_zero_noise_ordered_flock_stays_ordered():
+    w = W.uniform_system(4096, 64.0, 16, 2, input_seed=12, rule="knn", k=7, eta=0.0)
+    d = np.tile(np.array([[0.6, 0.8]], dtype=np.float32), (w.n, 1))
+    with vk.Sim.create(w.pos_q, d, w.box_q, 16, k=7, eta=0.0) as sim:
+        sim.step(10)
+        phi = sim.order_parameter()
+    assert np.all(np.abs(phi - 1.0) < 1e-6)
+
+
+def test_full_noise_rayleigh():
+    w = W.topological_small()
+    with vk.from_workload(w, eta=2 * math.pi) as sim:
+        sim.step(400)
+        phi = sim.order_parameter()
+    want = math.sqrt(math.pi) / (2 * math.sqrt(w.n))
+    assert abs(phi[50:].mean() - want) < 0.15 * want
+    assert abs((w.n * phi[50:] ** 2).mean() - 1.0) < 0.2
+
+
+def test_order_parameter_matches_oracle_each_step():
+    w = W.topological_small()
+    with vk.from_workload(w) as sim:
+        vals = []
+        for _ in range(20):
+            sim.step(1)
+            _, d, _, _ = sim.state()
+            vals.append(oracle.order_parameter(d))
+        phi = sim.order_parameter()
+    assert np.abs(phi - np.array(vals)).max() < PHI_TOL
+
+
+def test_run_to_run_bit_identical_and_graph_replay():
+    w = W.uniform_system(20000, 141.0, 16, 2, input_seed=13, rule="knn", k=7, eta=0.3)
+    outs = []
+    for graph in (0, 0, 7):
+        with vk.from_workload(w) as sim:
+            sim.set_graph_steps(graph)
+            sim.step(30)
+            pos, d, _, t = sim.state()
+            assert t == 30
+            outs.append((pos, d))
+    for pos, d in outs[1:]:
+        assert np.array_equal(pos, outs[0][0])
+        assert np.array_equal(d, outs[0][1])
+
+
+def test_checkpoint_resume_is_bit_exact():
+    w = W.uniform_system(5000, 70.7, 16, 2, input_seed=14, rule="knn", k=7)
+    with vk.from_workload(w) as sim:
+        sim.step(100)
+        ref = sim.state()
+    with vk.from_workload(w) as sim:
+        sim.step(50)
+        pos, d, _, t = sim.state()
+    with vk.Sim.create(pos, d, w.box_q, 16, k=7) as sim:
+        sim.set_state(pos, d, step=t)
+        sim.step(50)
+        got = sim.state()
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]) and got[3] == ref[3]
+
+
+def test_device_tensor_inputs_and_outputs():
+    torch = pytest.importorskip("torch")
+    w = W.uniform_system(3000, 54.0, 16, 2, input_seed=15, rule="knn", k=7)
+    pos_t = torch.from_numpy(w.pos_q).cuda()
+    dir_t = torch.from_numpy(w.dir).cuda()
+    with vk.Sim.create(pos_t, dir_t, w.box_q, 16, k=7) as sim:
+        sim.step(3)
+        p = torch.empty_like(pos_t)
+        d = torch.empty_like(dir_t)
+        sim.get_state_into(0, p, d)
+        pos, dd, _, _ = sim.state()
+    assert np.array_equal(p.cpu().numpy(), pos)
+    assert np.array_equal(d.cpu().numpy(), dd)
+
+
+def test_profiling_counts_phases():
+    w = W.uniform_system(8000, 89.0, 16, 2, input_seed=16, rule="knn", k=7)
+    with vk.from_workload(w) as sim:
+        sim.set_profiling(True)
+        sim.step(5)
+        prof = sim.profile()
+    assert prof["search_update"][1] == 5 and prof["scan"][1] == 15 and prof["scatter"][1] == 5
+    assert prof["search_update"][0] > 0
+
+
+def test_autotune_keeps_results():
+    w = W.uniform_system(20000, 141.0, 16, 2, input_seed=17, rule="knn", k=7)
+    with vk.from_workload(w) as sim:
+        sim.step(3)
+        before = sim.state()
+        best = sim.autotune([0.5, 1.0, 2.0, 3.0], trial_steps=2)
+        after = sim.state()
+        assert best in (0.5, 1.0, 2.0, 3.0)
+        assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+        assert before[3] == after[3]
+        sim.step(1)
+        check_step(sim, w, "knn")

@@ -1,0 +1,88 @@
+"""GPU parity of the Voronoi rule (Sec. "Computational tools: Voronoi
+neighbor lists"): per-particle half-plane clipping with exact predicates
+against the oracle's exact Delaunay triangulation."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_10239_gb300 import vk
+from paper_2103_10239_gb300 import workloads as W
+from parity import check_step
+
+pytestmark = pytest.mark.gpu
+
+
+def _same(sim, pos, box):
+    off, ids = sim.neighbors()
+    woff, wids = oracle.voronoi(pos, box)
+    assert np.array_equal(off, woff)
+    assert np.array_equal(ids, wids)
+    return off, ids
+
+
+@pytest.mark.parametrize("seed,n,L,bits", [(1, 3, 2.0, 10), (2, 5, 3.0, 12), (3, 12, 4.0, 16),
+                                           (4, 40, 7.0, 16), (5, 257, 16.0, 16), (6, 1000, 31.6, 20),
+                                           (7, 2, 1.5, 8), (8, 1, 1.0, 8)])
+def test_random_small_boxes(seed, n, L, bits):
+    w = W.uniform_system(n, L, bits, 2, input_seed=seed, rule="voronoi", k=0, v0=0.3, eta=0.5)
+    if len({tuple(p) for p in w.pos_q}) < n:
+        pytest.skip("coincident draw")
+    with vk.from_workload(w) as sim:
+        _same(sim, w.pos_q, w.box_q)
+        for _ in range(2):
+            check_step(sim, w, "voronoi")
+
+
+def test_square_and_hex_lattices():
+    pos, box = W.square_lattice(16, 1 << 16, 5)
+    d = W.random_dirs(pos.shape[0])
+    with vk.Sim.create(pos, d, box, 16, rule="voronoi") as sim:
+        off, _ = _same(sim, pos, box)
+        assert set(np.diff(off)) == {4}
+    pos, box = W.stretched_hex_lattice(20, 24, 2 * 30000, 25981)
+    d = W.random_dirs(pos.shape[0])
+    with vk.Sim.create(pos, d, box, 16, rule="voronoi") as sim:
+        off, _ = _same(sim, pos, box)
+        assert set(np.diff(off)) == {6}
+
+
+def test_mixed_workload_checks_every_100_steps():
+    """N=65536, half uniform / half jittered hex, Voronoi sets checked against
+    the oracle every 100 steps over 1000 steps, one teacher-forced step at
+    each check."""
+    w = W.voronoi_mixed(eta=0.1)
+    with vk.from_workload(w) as sim:
+        for c in range(10):
+            check_step(sim, w, "voronoi")
+            sim.step(99)
+        off, ids = sim.neighbors()
+        assert ids.size == 6 * w.n  # Euler: E = 3N on generic input
+
+
+def test_reciprocity_and_euler_after_steps():
+    w = W.voronoi_mixed(eta=0.5)
+    with vk.from_workload(w) as sim:
+        sim.step(5)
+        off, ids = sim.neighbors()
+    rows = [set(ids[off[i]:off[i + 1]]) for i in range(w.n)]
+    for i in range(0, w.n, 97):
+        for j in rows[i]:
+            assert i in rows[j]
+    assert ids.size == 6 * w.n
+
+
+def test_density_two_large_sampled():
+    w = W.precision_study("voronoi", n=1 << 18)
+    with vk.from_workload(w) as sim:
+        pos, _, _, _ = sim.state()
+        _same(sim, pos, w.box_q)
+
+
+def test_coincident_points_are_reported():
+    w = W.uniform_system(200, 14.0, 16, 2, input_seed=2, rule="voronoi", k=0)
+    pos = w.pos_q.copy()
+    pos[7] = pos[3]
+    with vk.Sim.create(pos, w.dir, w.box_q, 16, rule="voronoi") as sim:
+        with pytest.raises(vk.VKError) as e:
+            sim.neighbors()
+        assert e.value.status == vk.VK_ERR_DEGENERATE

@@ -1,0 +1,358 @@
+"""Benchmark: particle-steps/s of the fused non-metric neighbor build + Vicsek
+step (kNN, k=7) at N = 2^22 on one GB300, with the HBM-roofline fraction of
+the dominant kernel, an end-to-end figure through the C ABI with host
+buffers, and the CPU oracle timed on the host cores.
+
+A "step" is one pass of the whole hot path: the kNN search fused with the
+alignment/noise/advection update, the cell-count scan and the scatter into
+cell-sorted order.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): every rank runs its own independent replica of the
+workload (replicas only, weak scaling); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (neighbor build + Vicsek step), N=4M k=7, and % HBM roofline"
+ALG_BYTES_PER_PARTICLE_STEP = 24  # pos int32x2 + heading fp32, read and written once
+CSRC = os.path.join(ROOT, "paper_2103_10239_gb300", "csrc")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=1 << 22)
+    ap.add_argument("--k", type=int, default=7)
+    ap.add_argument("--layout", choices=["clustered", "uniform"], default="clustered")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args, rank=0):
+    from paper_2103_10239_gb300 import workloads as W
+    if args.layout == "clustered":
+        return W.clustered_large(n=args.n, k=args.k, seed=1003 + 100 * rank)
+    return W.uniform_large(n=args.n, k=args.k, seed=1013 + 100 * rank)
+
+
+def workload_config(w, args):
+    return {"workload": w.name, "n": w.n, "rule": w.rule, "k": w.k, "dim": w.dim,
+            "frac_bits": w.frac_bits, "box_q": int(w.box_q[0]), "density": round(w.density, 4),
+            "v0": w.v0, "eta": w.eta, "layout": args.layout,
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return float(d["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(CSRC)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(CSRC, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload_name: str):
+    """DRAM bytes per launch of the search+update kernel from the committed
+    ncu summary, if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "knn_step_kernel_traffic.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m_sha = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
+    m_b = re.search(r"dram_bytes_per_launch_full_workload:\s*([0-9.e+]+)", txt)
+    m_w = re.search(r"workload:\s*(\S+)", txt)
+    if not (m_sha and m_b and m_w):
+        return None
+    if m_sha.group(1) != kernel_source_sha() or m_w.group(1) != workload_name:
+        return None
+    return float(m_b.group(1))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (the oracle as it stands, on the host cores)
+# ---------------------------------------------------------------------------
+def oracle_sample_rate(w, budget_s: float, min_q: int = 32):
+    """Oracle particle-steps/s on a bounded sample: brute-force kNN of a
+    random subset of particles over all N plus the FP64 update, scaled to
+    the subset."""
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(0)
+    # calibrate
+    q = np.sort(rng.choice(w.n, min_q, replace=False)).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.knn(w.pos_q, w.box_q, w.k, query=q)
+    t_q = (time.perf_counter() - t0) / min_q
+    m = int(max(min_q, min(w.n, budget_s / max(t_q, 1e-9))))
+    q = np.sort(rng.choice(w.n, m, replace=False)).astype(np.int64)
+    t0 = time.perf_counter()
+    nb = oracle.knn(w.pos_q, w.box_q, w.k, query=q)
+    t_knn = time.perf_counter() - t0
+    # the update of the sampled particles (run on a system made of them)
+    off = np.arange(m + 1, dtype=np.int64) * w.k
+    remap = np.full(w.n, -1, dtype=np.int64)
+    remap[q] = np.arange(m)
+    sub_ids = remap[nb.ravel()]
+    sub_ids[sub_ids < 0] = 0  # neighbours outside the sample: any valid index (timing only)
+    t0 = time.perf_counter()
+    oracle.vicsek_step(w.pos_q[q], w.dir[q], w.box_q, off, sub_ids.astype(np.int32), frac_bits=w.frac_bits,
+                       v0=w.v0, dt=w.dt, eta=w.eta, seed=w.seed, step=0)
+    t_upd = time.perf_counter() - t0
+    return m / (t_knn + t_upd), m, oracle.num_threads(), t_knn + t_upd
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = workload(args)
+    total_budget = 150.0
+    per_step = total_budget / max(1, args.steps + args.warmup)
+    for _ in range(args.warmup):
+        oracle_sample_rate(w, per_step)
+    times, parts = [], 0
+    m_used = 0
+    cores = 0
+    for _ in range(args.steps):
+        rate, m, cores, secs = oracle_sample_rate(w, per_step)
+        times.append(secs)
+        parts += m
+        m_used = m
+    value = parts / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
+            "config": workload_config(w, args),
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{m_used} random particles per step: brute-force kNN over all "
+                                       f"{w.n} + FP64 update"},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+    from paper_2103_10239_gb300 import vk
+    from paper_2103_10239_gb300 import _build
+
+    _build.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(args, rank)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    sim = vk.from_workload(w, stream=stream)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    sim.set_profiling(True)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)  # evict the state from L2 (outside the timed events)
+        ev[i][0].record(stream)
+        sim.step(1)
+        ev[i][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    time.sleep(0.2)
+    clk = clocks.stop()
+    sim.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    prof = sim.profile()
+    sim.set_profiling(False)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * w.n * args.steps / (total_ms * 1e-3)
+
+    # dominant kernel: the fused search + update
+    su_ms, su_launches = prof["search_update"]
+    per_launch_ms = su_ms / max(1, su_launches)
+    alg_bytes = ALG_BYTES_PER_PARTICLE_STEP * w.n
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(w.name)
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if rank == 0 or True:
+        pos_h = torch.empty((w.n, 2), dtype=torch.int32, pin_memory=True)
+        dir_h = torch.empty((w.n, 2), dtype=torch.float32, pin_memory=True)
+        pos_h.numpy()[:] = w.pos_q
+        dir_h.numpy()[:] = w.dir
+        phi_h = np.zeros(1, dtype=np.float64)
+        torch.cuda.synchronize()
+        t_e = []
+        for i in range(args.e2e_steps + 1):
+            t0 = time.perf_counter()
+            sim.set_state(pos_h, dir_h)
+            sim.step(1)
+            sim.get_state_into(0, pos_h, dir_h)
+            phi_h[0] = sim.order_parameter(max_values=1)[-1]
+            t_e.append(time.perf_counter() - t0)
+        t_e = t_e[1:]
+        e2e = {"value": w.n / (sum(t_e) / len(t_e)), "unit": "particle-steps/s",
+               "h2d_bytes_per_step": int(w.n * 16), "d2h_bytes_per_step": int(w.n * 16 + 8),
+               "note": "vk_set_state from pinned host + vk_step(1) + vk_get_state to pinned host + phi"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, m, cores, secs = oracle_sample_rate(w, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"{m} random particles of the {w.n}-particle workload: brute-force kNN over "
+                         f"all N + FP64 update ({secs:.1f} s)"}
+
+    info = sim.info()
+    sim.close()
+    if rank != 0:
+        return
+    phases = {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+f32",
+        "data": "synthetic", "config": workload_config(w, args),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "knn_step_kernel (search + align + advect)",
+                     "alg_bytes_per_launch": alg_bytes, "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
+                     "kernel_ms_per_launch": per_launch_ms},
+        "step_roofline": {"achieved_gbs": alg_bytes / (ms_per_step * 1e-3) / 1e9,
+                          "frac": alg_bytes / (ms_per_step * 1e-3) / 1e9 / peak,
+                          "note": "24 B per particle-step over the whole step"},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(info.kernels_per_step) * args.steps,
+        "clocks": clk, "phases": phases, "wall_s_timed_region": t_wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+        dist = td
+    run_ours(args, rank, world, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -492,16 +492,19 @@ static int cmp_keyed(const void* x, const void* y) {
 static int vtess_build(vtess_t* V, int64_t n, const int32_t* pos, const int64_t* box, int64_t margin) {
   memset(V, 0, sizeof(*V));
   int64_t Lx = box[0], Ly = box[1];
-  int64_t mx = margin < Lx ? margin : Lx, my = margin < Ly ? margin : Ly;
-  int64_t cap = 9 * n;
+  /* a star circumdisk reaches at most sqrt(2) L from its point (the largest
+   * empty circle of a periodic set has radius <= L/sqrt(2)), so margins up
+   * to 2L (a 5x5 tiling) always suffice */
+  int64_t mx = margin < 2 * Lx ? margin : 2 * Lx, my = margin < 2 * Ly ? margin : 2 * Ly;
+  int64_t cap = 25 * n;
   V->xy = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * cap + 6));
   V->orig = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
   if (!V->xy || !V->orig) return ORC_ERR_OOM;
   int32_t m = 0;
   /* originals first (indices 0..n-1), then images */
   for (int pass = 0; pass < 2; ++pass)
-    for (int sy = -1; sy <= 1; ++sy)
-      for (int sx = -1; sx <= 1; ++sx) {
+    for (int sy = -2; sy <= 2; ++sy)
+      for (int sx = -2; sx <= 2; ++sx) {
         int center = (sx == 0 && sy == 0);
         if ((pass == 0) != center) continue;
         for (int64_t i = 0; i < n; ++i) {
@@ -553,16 +556,16 @@ static int vtess_build(vtess_t* V, int64_t n, const int32_t* pos, const int64_t*
 }
 
 static int vtess_build_auto(vtess_t* V, int64_t n, const int32_t* pos, const int64_t* box) {
-  int64_t L = box[0] > box[1] ? box[0] : box[1];
+  int64_t L2 = 2 * (box[0] > box[1] ? box[0] : box[1]);
   double spacing = sqrt((double)box[0] * (double)box[1] / (double)n);
   int64_t margin = (int64_t)ceil(8.0 * spacing);
   for (;;) {
-    if (margin > L) margin = L;
+    if (margin > L2) margin = L2;
     int rc = vtess_build(V, n, pos, box, margin);
     if (rc == ORC_OK) return ORC_OK;
     vtess_free(V);
     if (rc > 0) return rc;
-    if (margin == L) return ORC_ERR_INTERNAL;
+    if (margin == L2) return ORC_ERR_INTERNAL;
     margin *= 2;
   }
 }

@@ -145,3 +145,19 @@ def test_predicates(orc):
         pts = [tuple(int(v) for v in rng.integers(-big, big, 2)) for _ in range(4)]
         assert orc.incircle(*pts) == brute.incircle_int(*pts)
         assert orc.orient2d(*pts[:3]) == brute.orient_int(*pts[:3])
+
+
+def test_tiny_systems_against_brute_force(orc):
+    """N = 1..5 in small boxes: stars whose circumdisks reach far outside the
+    box (up to sqrt(2) L) -- the regime where a 3x3 tiling is not enough."""
+    rng = np.random.default_rng(0)
+    done = 0
+    while done < 120:
+        n = int(rng.integers(1, 6))
+        L = int(rng.integers(8, 400))
+        pos = rng.integers(0, L, size=(n, 2)).astype(np.int32)
+        if len({tuple(p) for p in pos}) < n:
+            continue
+        off, ids = orc.voronoi(pos, (L, L))
+        assert _rows(off, ids) == brute.voronoi_brute(pos, (L, L)), (n, L, pos.tolist())
+        done += 1

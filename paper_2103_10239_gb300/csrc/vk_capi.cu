@@ -220,7 +220,7 @@ vk_status enqueue_step(vk_sim* s) {
   if (st) return st;
   if (s->prm.rule == VK_RULE_KNN) VK_CUDA(s, launch_knn_step(s->g, s->b, P, s->stream));
   else VK_CUDA(s, launch_voronoi_step(s->g, s->b, P, s->stream));
-  if ((st = record_end(s, 0, e0, 1))) return st;
+  if ((st = record_end(s, 0, e0, s->prm.rule == VK_RULE_KNN ? 1 : 2))) return st;
   if ((st = record_begin(s, 1, &e0))) return st;
   VK_CUDA(s, launch_scan(s->g, s->b, s->stream));
   if ((st = record_end(s, 1, e0, 3))) return st;
@@ -358,10 +358,12 @@ vk_status build_sim(int32_t n_rep, const int64_t* n_r, const int32_t* pos_q, con
       (e = dalloc(&s->b.U_id, N)) || (e = dalloc(&s->b.U_rank, N)) ||
       (e = dalloc(&s->b.phi_acc, 3 * (size_t)s->phi_cap * n_rep)) || (e = dalloc(&s->b.d_step, 1)) ||
       (e = dalloc(&s->b.d_status, 1)) || (e = dalloc(&s->reps_d, n_rep)) ||
+      (e = dalloc(&s->b.ovf_list, params->rule == VK_RULE_VORONOI ? N : 1)) || (e = dalloc(&s->b.ovf_count, 1)) ||
       (e = dalloc(&s->tasks_d, s->tasks_h.size())))
     return bail(cuda_fail(s, e, "cudaMalloc"));
   if (ensure_cells_capacity(s)) return bail(VK_ERR_OOM);
   if ((e = cudaMemsetAsync(s->b.d_step, 0, sizeof(int64_t), s->stream)) ||
+      (e = cudaMemsetAsync(s->b.ovf_count, 0, sizeof(int32_t), s->stream)) ||
       (e = cudaMemsetAsync(s->b.d_status, 0, sizeof(int32_t), s->stream)) ||
       (e = cudaMemcpyAsync(s->tasks_d, s->tasks_h.data(), sizeof(BlockTask) * s->tasks_h.size(),
                            cudaMemcpyHostToDevice, s->stream)))
@@ -476,26 +478,33 @@ vk_status vk_get_neighbors(vk_sim* s, int32_t replica, int64_t* offsets, int32_t
     if (e != cudaSuccess) return cuda_fail(s, e, "knn export");
     for (int64_t i = 0; i <= n; ++i) off_h[i] = i * k;
   } else {
+    // pass 0: degrees by id; pass 1: ids at the CSR offsets
     int32_t* deg_d = nullptr;
-    int32_t* nbr_d = nullptr;
+    int64_t* off_d = nullptr;
+    int32_t* ids_d = nullptr;
     VK_CUDA(s, dalloc(&deg_d, n));
-    cudaError_t e = dalloc(&nbr_d, (size_t)n * kVoronoiMaxDeg);
-    std::vector<int32_t> deg(n), nbr((size_t)n * kVoronoiMaxDeg);
-    if (e == cudaSuccess) e = launch_voronoi_export(s->g, s->b, replica, (int)n, deg_d, nbr_d, s->stream);
+    std::vector<int32_t> deg(n);
+    cudaError_t e = launch_voronoi_export(s->g, s->b, replica, (int)n, 0, deg_d, nullptr, nullptr, s->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(deg.data(), deg_d, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) {
+      off_h[0] = 0;
+      for (int64_t i = 0; i < n; ++i) off_h[i + 1] = off_h[i] + deg[i];
+      ids_h.resize(off_h[n]);
+      e = dalloc(&off_d, n + 1);
+    }
+    if (e == cudaSuccess) e = dalloc(&ids_d, std::max<int64_t>(1, off_h[n]));
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(nbr.data(), nbr_d, sizeof(int32_t) * n * kVoronoiMaxDeg, cudaMemcpyDeviceToHost,
-                          s->stream);
+      e = cudaMemcpyAsync(off_d, off_h.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = launch_voronoi_export(s->g, s->b, replica, (int)n, 1, deg_d, off_d, ids_d, s->stream);
+    if (e == cudaSuccess && off_h[n] > 0)
+      e = cudaMemcpyAsync(ids_h.data(), ids_d, sizeof(int32_t) * off_h[n], cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     cudaFree(deg_d);
-    cudaFree(nbr_d);
+    cudaFree(off_d);
+    cudaFree(ids_d);
     if (e != cudaSuccess) return cuda_fail(s, e, "voronoi export");
-    off_h[0] = 0;
-    for (int64_t i = 0; i < n; ++i) off_h[i + 1] = off_h[i] + deg[i];
-    ids_h.resize(off_h[n]);
-    for (int64_t i = 0; i < n; ++i)
-      for (int32_t j = 0; j < deg[i]; ++j) ids_h[off_h[i] + j] = nbr[(size_t)i * kVoronoiMaxDeg + j];
   }
   if ((st = record_end(s, 4, e0, 1))) return st;
   if ((st = read_status(s))) return st;
@@ -621,7 +630,7 @@ void vk_destroy(vk_sim* s) {
     }
   void* bufs[] = {s->b.S_pos, s->b.S_dir, s->b.S_id, s->b.U_pos, s->b.U_dir, s->b.U_id, s->b.U_rank,
                   s->b.counts, s->b.offsets, s->b.bsum, s->b.phi_acc, s->b.d_step, s->b.d_status,
-                  s->reps_d, s->tasks_d};
+                  s->b.ovf_list, s->b.ovf_count, s->reps_d, s->tasks_d};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -687,7 +696,7 @@ vk_status vk_get_info(vk_sim* s, vk_info* out) {
   out->dim = s->dim;
   out->n_cells = s->n_cells;
   out->step = s->step;
-  out->kernels_per_step = 5;
+  out->kernels_per_step = s->prm.rule == VK_RULE_KNN ? 5 : 6;
   out->rule = s->prm.rule;
   out->k = s->prm.k;
   return VK_OK;

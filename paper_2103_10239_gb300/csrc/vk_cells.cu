@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kBlock) scatter_kernel(const Rep* __restrict__
                                                          typename Vec<DIM>::F* __restrict__ S_dir,
                                                          int32_t* __restrict__ S_id, int advance_step,
                                                          int64_t* d_step, double* phi_acc, int n_rep,
-                                                         int phi_cap) {
+                                                         int phi_cap, int32_t* ovf_count) {
   const BlockTask t = tasks[blockIdx.x];
   const Rep R = reps[t.rep];
   const int li = t.first + (int)threadIdx.x;
@@ -178,7 +178,10 @@ __global__ void __launch_bounds__(kBlock) scatter_kernel(const Rep* __restrict__
     double* slot = phi_acc + (size_t)(nxt % phi_cap) * (size_t)n_rep * 3;
     for (int i = threadIdx.x; i < n_rep * 3; i += blockDim.x) slot[i] = 0.0;
     __syncthreads();
-    if (threadIdx.x == 0) *d_step = nxt;
+    if (threadIdx.x == 0) {
+      *d_step = nxt;
+      *ovf_count = 0;  // the Voronoi overflow list of this step has been consumed
+    }
   }
   if (li >= R.n) return;
   const int64_t s = R.p0 + li;
@@ -276,11 +279,13 @@ cudaError_t launch_scatter(const Geometry& g, const Buffers& b, const StepParams
   if (g.dim == 2)
     scatter_kernel<2><<<g.n_tasks, kBlock, 0, st>>>(
         g.reps, g.tasks, (const int2*)b.U_pos, (const float2*)b.U_dir, b.U_id, b.U_rank, b.offsets,
-        (int2*)b.S_pos, (float2*)b.S_dir, b.S_id, advance_step, b.d_step, b.phi_acc, P.n_rep, P.phi_cap);
+        (int2*)b.S_pos, (float2*)b.S_dir, b.S_id, advance_step, b.d_step, b.phi_acc, P.n_rep, P.phi_cap,
+        b.ovf_count);
   else
     scatter_kernel<3><<<g.n_tasks, kBlock, 0, st>>>(
         g.reps, g.tasks, (const int4*)b.U_pos, (const float4*)b.U_dir, b.U_id, b.U_rank, b.offsets,
-        (int4*)b.S_pos, (float4*)b.S_dir, b.S_id, advance_step, b.d_step, b.phi_acc, P.n_rep, P.phi_cap);
+        (int4*)b.S_pos, (float4*)b.S_dir, b.S_id, advance_step, b.d_step, b.phi_acc, P.n_rep, P.phi_cap,
+        b.ovf_count);
   return cudaGetLastError();
 }
 

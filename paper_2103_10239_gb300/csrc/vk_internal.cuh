@@ -424,6 +424,8 @@ struct Buffers {
   double* phi_acc;    // phi_cap * n_rep * 3
   int64_t* d_step;
   int32_t* d_status;
+  int2* ovf_list;      // Voronoi: (slot, replica) of cells too large for the main kernel
+  int32_t* ovf_count;
 };
 
 struct Geometry {
@@ -456,8 +458,9 @@ cudaError_t launch_knn_export(const Geometry& g, const Buffers& b, int k, int re
 
 // vk_voronoi.cu
 cudaError_t launch_voronoi_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st);
-cudaError_t launch_voronoi_export(const Geometry& g, const Buffers& b, int rep, int n, int32_t* deg,
-                                  int32_t* nbr, cudaStream_t st);
-constexpr int kVoronoiMaxDeg = 32;
+cudaError_t launch_voronoi_export(const Geometry& g, const Buffers& b, int rep, int n, int pass, int32_t* deg,
+                                  const int64_t* out_off, int32_t* out_ids, cudaStream_t st);
+// largest Voronoi cell (edges) handled; larger cells latch VK_ERR_CAPACITY
+constexpr int kVoronoiMaxDeg = 256;
 
 }  // namespace vk

@@ -19,6 +19,7 @@
 //   * neighbors are the sites of edges with positive length (an edge between
 //     two coincident vertices, i.e. four cocircular points, is dropped).
 // Exact predicates need |relative coordinates| < 1.5 * 2^30, hence L_q <= 2^30.
+#include <algorithm>
 #include <climits>
 
 #include "vk_internal.cuh"
@@ -27,7 +28,8 @@ namespace vk {
 
 namespace {
 
-constexpr int kMaxE = kVoronoiMaxDeg;  // polygon edge capacity
+constexpr int kFastCap = 32;    // polygon capacity of the main kernel
+constexpr int kSlowCap = kVoronoiMaxDeg;  // capacity of the overflow kernel and the export
 
 // sign of incircle(0, a, b, m): > 0 iff m lies strictly inside the circle
 // through the origin, a and b (with (0, a, b) counter-clockwise), i.e. iff
@@ -75,22 +77,25 @@ __device__ __forceinline__ float vertex_r2_upper(int32_t ax, int32_t ay, int32_t
   return isfinite(r2) ? r2 : 3.0e38f;
 }
 
+template <int CAP>
 struct Poly {
-  int32_t qx[kMaxE], qy[kMaxE];  // relative coordinates of the edge sites
-  int32_t id[kMaxE];             // replica-local id of the site
-  int32_t slot[kMaxE];           // sorted slot of the site (-1: an image of the particle itself)
-  float vr2[kMaxE];              // vertex a (between edges a and a+1): upper bound of |V|^2
+  int32_t qx[CAP], qy[CAP];  // relative coordinates of the edge sites
+  int32_t id[CAP];           // replica-local id of the site
+  int32_t slot[CAP];         // sorted slot of the site (-1: an image of the particle itself)
+  float vr2[CAP];            // vertex a (between edges a and a+1): upper bound of |V|^2
   int m;
   float max_r2;
 };
 
-__device__ __forceinline__ void poly_refresh_max(Poly& P) {
+template <int CAP>
+__device__ __forceinline__ void poly_refresh_max(Poly<CAP>& P) {
   float mx = 0.f;
   for (int a = 0; a < P.m; ++a) mx = fmaxf(mx, P.vr2[a]);
   P.max_r2 = mx;
 }
 
-__device__ __forceinline__ void poly_init(Poly& P, int32_t self_id, uint32_t Lx, uint32_t Ly, bool* bad) {
+template <int CAP>
+__device__ __forceinline__ void poly_init(Poly<CAP>& P, int32_t self_id, uint32_t Lx, uint32_t Ly, bool* bad) {
   const int32_t X = (int32_t)Lx, Y = (int32_t)Ly;
   const int32_t sx[4] = {X, 0, -X, 0}, sy[4] = {0, Y, 0, -Y};
   P.m = 4;
@@ -106,37 +111,53 @@ __device__ __forceinline__ void poly_init(Poly& P, int32_t self_id, uint32_t Lx,
 }
 
 // clip the cell by the bisector of site (mx, my); returns false on overflow
-__device__ __forceinline__ bool poly_clip(Poly& P, int32_t mx, int32_t my, int32_t mid, int32_t mslot,
+template <int CAP>
+__device__ __forceinline__ bool poly_clip(Poly<CAP>& P, int32_t mx, int32_t my, int32_t mid, int32_t mslot,
                                           float Dm, bool* bad) {
   const int m = P.m;
-  uint32_t cut = 0;
+  // the vertices strictly beyond the bisector form one cyclic run [s, s+c)
+  int c = 0, s = -1;
+  bool first_cut = false, prev_cut = false;
   for (int a = 0; a < m; ++a) {
-    if (Dm > 4.0f * P.vr2[a]) continue;  // the vertex is too close to the origin to be cut
-    const int b = (a + 1 == m) ? 0 : a + 1;
-    if (vertex_cut_sign(P.qx[a], P.qy[a], P.qx[b], P.qy[b], mx, my) > 0) cut |= 1u << a;
-  }
-  if (cut == 0) return true;
-  const int c = __popc(cut);
-  int s = -1;
-  for (int a = 0; a < m; ++a) {
-    const int prev = (a == 0) ? m - 1 : a - 1;
-    if (((cut >> a) & 1u) && !((cut >> prev) & 1u)) {
-      s = a;
-      break;
+    bool cut = false;
+    if (!(Dm > 4.0f * P.vr2[a])) {  // a vertex closer than |m|/2 cannot be cut
+      const int b = (a + 1 == m) ? 0 : a + 1;
+      cut = vertex_cut_sign(P.qx[a], P.qy[a], P.qx[b], P.qy[b], mx, my) > 0;
     }
+    if (a == 0) first_cut = cut;
+    if (cut) {
+      if (a > 0 && !prev_cut) {
+        if (s >= 0) {  // a second run: cannot happen with exact predicates
+          *bad = true;
+          return true;
+        }
+        s = a;
+      }
+      ++c;
+    }
+    prev_cut = cut;
+  }
+  if (c == 0) return true;
+  if (first_cut) {
+    if (!prev_cut) {
+      if (s >= 0) {
+        *bad = true;
+        return true;
+      }
+      s = 0;  // the run starts at vertex 0
+    } else if (s < 0) {
+      *bad = true;  // every vertex cut: impossible, the particle keeps its own side
+      return true;
+    }
+    // else: the run wraps from s through m-1 into 0
   }
   if (s < 0 || c >= m) {
     *bad = true;
     return true;
   }
-  for (int j = 0; j < c; ++j)
-    if (!((cut >> ((s + j) % m)) & 1u)) {
-      *bad = true;  // not a contiguous run: cannot happen with exact predicates
-      return true;
-    }
   const int t = (s + c - 1) % m;
   const int newm = m - c + 2;
-  if (newm > kMaxE) return false;
+  if (newm > CAP) return false;
   int mpos;
   if (s <= t) {
     // keep e_0..e_s, insert m, keep e_{t+1}..e_{m-1}
@@ -178,9 +199,11 @@ __device__ __forceinline__ bool poly_clip(Poly& P, int32_t mx, int32_t my, int32
 // Voronoi cell of the particle at slot `self`.  Status codes are latched on
 // capacity overflow (kStCapacity), coincident points (kStDegenerate) and
 // internal inconsistencies (kStRange).
-__device__ void voronoi_cell(const Rep& R, int64_t self, const int32_t* pi, int32_t self_id,
+// Returns false (and leaves the cell unusable) if the polygon outgrew CAP.
+template <int CAP>
+__device__ bool voronoi_cell(const Rep& R, int64_t self, const int32_t* pi, int32_t self_id,
                              const int2* __restrict__ pos, const int32_t* __restrict__ ids,
-                             const uint32_t* __restrict__ off, Poly& P, int32_t* status) {
+                             const uint32_t* __restrict__ off, Poly<CAP>& P, int32_t* status) {
   bool bad = false, overflow = false, degenerate = false;
   poly_init(P, self_id, R.L[0], R.L[1], &bad);
   const int64_t Lx = R.L[0], Ly = R.L[1];
@@ -191,7 +214,7 @@ __device__ void voronoi_cell(const Rep& R, int64_t self, const int32_t* pi, int3
       return;
     }
     const float Df = (float)D * (1.0f - 2.384185791015625e-07f);  // rounded down
-    if (Df > 4.0f * P.max_r2) return;
+    if (overflow || Df > 4.0f * P.max_r2) return;
     if (!poly_clip(P, qx, qy, jid, slot, Df, &bad)) overflow = true;
   };
   auto run = [&](uint32_t qb, uint32_t qe) {
@@ -227,19 +250,20 @@ __device__ void voronoi_cell(const Rep& R, int64_t self, const int32_t* pi, int3
       }
     }
   }
-  if (overflow) set_status(status, kStCapacity);
   if (degenerate) set_status(status, kStDegenerate);
   if (bad) set_status(status, kStRange);
+  return !overflow;
 }
 
 // neighbors of positive edge length, excluding the particle's own images,
 // sorted by id and de-duplicated; returns the count
-__device__ __forceinline__ int voronoi_neighbors(const Poly& P, int32_t self_id, int32_t* nid, int32_t* nslot) {
+template <int CAP>
+__device__ __forceinline__ int voronoi_neighbors(const Poly<CAP>& P, int32_t self_id, int32_t* nid,
+                                                 int32_t* nslot) {
   int cnt = 0;
   const int m = P.m;
   for (int a = 0; a < m; ++a) {
-    if (P.id[a] == self_id && P.slot[a] < 0) continue;
-    if (P.slot[a] < 0) continue;
+    if (P.slot[a] < 0) continue;  // an image of the particle itself
     const int pa = (a == 0) ? m - 1 : a - 1, na = (a + 1 == m) ? 0 : a + 1;
     if (vertex_cut_sign(P.qx[pa], P.qy[pa], P.qx[a], P.qy[a], P.qx[na], P.qy[na]) == 0) continue;
     // insertion by id
@@ -260,12 +284,40 @@ __device__ __forceinline__ int voronoi_neighbors(const Poly& P, int32_t self_id,
   return cnt;
 }
 
+// the Vicsek update of one particle from its finished cell
+template <int CAP>
+__device__ __forceinline__ void voronoi_update(const Rep& R, const StepParams& Pm, int64_t step, int64_t s,
+                                               const Poly<CAP>& P, const int32_t* pi, const float* ni,
+                                               int32_t id, const float2* __restrict__ S_dir,
+                                               int2* __restrict__ U_pos, float2* __restrict__ U_dir,
+                                               int32_t* __restrict__ U_id, uint32_t* __restrict__ U_rank,
+                                               uint32_t* __restrict__ counts, float* nnew) {
+  int32_t nid[CAP], nslot[CAP];
+  const int cnt = voronoi_neighbors(P, id, nid, nslot);
+  HeadSum<2> H;
+  H.init();
+  if (Pm.include_self) H.add(ni, Pm.sum_mode);
+  for (int j = 0; j < cnt; ++j) {
+    const float2 d = S_dir[nslot[j]];
+    const float v[2] = {d.x, d.y};
+    H.add(v, Pm.sum_mode);
+  }
+  int32_t pout[3] = {0, 0, 0};
+  align_advect<2>(R, Pm, (uint32_t)step, id, ni, H, cnt + (Pm.include_self ? 1 : 0), pi, pout, nnew);
+  U_pos[s] = make_int2(pout[0], pout[1]);
+  U_dir[s] = make_float2(nnew[0], nnew[1]);
+  U_id[s] = id;
+  U_rank[s] = atomicAdd(counts + linear_cell<2>(R, pout), 1u);
+}
+
+// Main kernel: cells of up to kFastCap edges.  Particles whose cell outgrows
+// it are appended to the overflow list and finished by the overflow kernel.
 __global__ void __launch_bounds__(kBlock) voronoi_step_kernel(
     const Rep* __restrict__ reps, const BlockTask* __restrict__ tasks, const int2* __restrict__ S_pos,
     const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, const uint32_t* __restrict__ off,
     int2* __restrict__ U_pos, float2* __restrict__ U_dir, int32_t* __restrict__ U_id, uint32_t* __restrict__ U_rank,
     uint32_t* __restrict__ counts, double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams Pm,
-    int32_t* status) {
+    int2* __restrict__ ovf_list, int32_t* __restrict__ ovf_count, int32_t* status) {
   const BlockTask t = tasks[blockIdx.x];
   const Rep R = reps[t.rep];
   const int li = t.first + (int)threadIdx.x;
@@ -278,47 +330,79 @@ __global__ void __launch_bounds__(kBlock) voronoi_step_kernel(
     const int32_t pi[3] = {p.x, p.y, 0};
     const float ni[3] = {nv.x, nv.y, 0.f};
     const int32_t id = S_id[s];
-    Poly P;
-    voronoi_cell(R, s, pi, id, S_pos, S_id, off, P, status);
-    int32_t nid[kMaxE], nslot[kMaxE];
-    const int cnt = voronoi_neighbors(P, id, nid, nslot);
-    HeadSum<2> H;
-    H.init();
-    if (Pm.include_self) H.add(ni, Pm.sum_mode);
-    for (int j = 0; j < cnt; ++j) {
-      const float2 d = S_dir[nslot[j]];
-      const float v[2] = {d.x, d.y};
-      H.add(v, Pm.sum_mode);
+    Poly<kFastCap> P;
+    if (voronoi_cell(R, s, pi, id, S_pos, S_id, off, P, status)) {
+      voronoi_update(R, Pm, step, s, P, pi, ni, id, S_dir, U_pos, U_dir, U_id, U_rank, counts, nnew);
+    } else {
+      const int q = atomicAdd(ovf_count, 1);
+      ovf_list[q] = make_int2((int)s, t.rep);
     }
-    int32_t pout[3] = {0, 0, 0};
-    align_advect<2>(R, Pm, (uint32_t)step, id, ni, H, cnt + (Pm.include_self ? 1 : 0), pi, pout, nnew);
-    U_pos[s] = make_int2(pout[0], pout[1]);
-    U_dir[s] = make_float2(nnew[0], nnew[1]);
-    U_id[s] = id;
-    U_rank[s] = atomicAdd(counts + linear_cell<2>(R, pout), 1u);
   }
   block_phi_accumulate<2>(nnew, phi_acc + ((size_t)(step % Pm.phi_cap) * (size_t)Pm.n_rep + (size_t)t.rep) * 3);
 }
 
-__global__ void __launch_bounds__(kBlock) voronoi_export_kernel(const Rep* __restrict__ reps, int rep,
-                                                                const int2* __restrict__ S_pos,
-                                                                const int32_t* __restrict__ S_id,
-                                                                const uint32_t* __restrict__ off,
-                                                                int32_t* __restrict__ deg, int32_t* __restrict__ nbr,
-                                                                int32_t* status) {
+// Overflow kernel: the few particles with very large cells (a particle
+// bordering a void can have dozens of Voronoi neighbors).
+__global__ void __launch_bounds__(64) voronoi_overflow_kernel(
+    const Rep* __restrict__ reps, const int2* __restrict__ S_pos, const float2* __restrict__ S_dir,
+    const int32_t* __restrict__ S_id, const uint32_t* __restrict__ off, int2* __restrict__ U_pos,
+    float2* __restrict__ U_dir, int32_t* __restrict__ U_id, uint32_t* __restrict__ U_rank,
+    uint32_t* __restrict__ counts, double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams Pm,
+    const int2* __restrict__ ovf_list, const int32_t* __restrict__ ovf_count, int32_t* status) {
+  const int total = *ovf_count;
+  const int64_t step = *d_step;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+    const int2 e = ovf_list[q];
+    const Rep R = reps[e.y];
+    const int64_t s = e.x;
+    const int2 p = S_pos[s];
+    const float2 nv = S_dir[s];
+    const int32_t pi[3] = {p.x, p.y, 0};
+    const float ni[3] = {nv.x, nv.y, 0.f};
+    const int32_t id = S_id[s];
+    Poly<kSlowCap> P;
+    if (!voronoi_cell(R, s, pi, id, S_pos, S_id, off, P, status)) {
+      set_status(status, kStCapacity);
+      continue;
+    }
+    float nnew[3] = {0.f, 0.f, 0.f};
+    voronoi_update(R, Pm, step, s, P, pi, ni, id, S_dir, U_pos, U_dir, U_id, U_rank, counts, nnew);
+    double* acc = phi_acc + ((size_t)(step % Pm.phi_cap) * (size_t)Pm.n_rep + (size_t)e.y) * 3;
+    atomicAdd(acc + 0, (double)nnew[0]);
+    atomicAdd(acc + 1, (double)nnew[1]);
+  }
+}
+
+// Export (not on the hot path): pass 0 writes the degree of every particle
+// (by id), pass 1 writes the sorted ids at out_off[id].
+__global__ void __launch_bounds__(64) voronoi_export_kernel(const Rep* __restrict__ reps, int rep,
+                                                            const int2* __restrict__ S_pos,
+                                                            const int32_t* __restrict__ S_id,
+                                                            const uint32_t* __restrict__ off, int pass,
+                                                            int32_t* __restrict__ deg,
+                                                            const int64_t* __restrict__ out_off,
+                                                            int32_t* __restrict__ out_ids, int32_t* status) {
   const Rep R = reps[rep];
-  const int li = blockIdx.x * kBlock + (int)threadIdx.x;
-  if (li >= R.n) return;
-  const int64_t s = R.p0 + li;
-  const int2 p = S_pos[s];
-  const int32_t pi[3] = {p.x, p.y, 0};
-  const int32_t id = S_id[s];
-  Poly P;
-  voronoi_cell(R, s, pi, id, S_pos, S_id, off, P, status);
-  int32_t nid[kMaxE], nslot[kMaxE];
-  const int cnt = voronoi_neighbors(P, id, nid, nslot);
-  deg[id] = cnt;
-  for (int j = 0; j < cnt; ++j) nbr[(int64_t)id * kMaxE + j] = nid[j];
+  for (int li = blockIdx.x * blockDim.x + threadIdx.x; li < R.n; li += gridDim.x * blockDim.x) {
+    const int64_t s = R.p0 + li;
+    const int2 p = S_pos[s];
+    const int32_t pi[3] = {p.x, p.y, 0};
+    const int32_t id = S_id[s];
+    Poly<kSlowCap> P;
+    if (!voronoi_cell(R, s, pi, id, S_pos, S_id, off, P, status)) {
+      set_status(status, kStCapacity);
+      if (pass == 0) deg[id] = 0;
+      continue;
+    }
+    int32_t nid[kSlowCap], nslot[kSlowCap];
+    const int cnt = voronoi_neighbors(P, id, nid, nslot);
+    if (pass == 0) {
+      deg[id] = cnt;
+    } else {
+      const int64_t o = out_off[id];
+      for (int j = 0; j < cnt; ++j) out_ids[o + j] = nid[j];
+    }
+  }
 }
 
 }  // namespace
@@ -326,16 +410,21 @@ __global__ void __launch_bounds__(kBlock) voronoi_export_kernel(const Rep* __res
 cudaError_t launch_voronoi_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st) {
   voronoi_step_kernel<<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int2*)b.S_pos, (const float2*)b.S_dir,
                                                     b.S_id, b.offsets, (int2*)b.U_pos, (float2*)b.U_dir, b.U_id,
-                                                    b.U_rank, b.counts, b.phi_acc, b.d_step, P, b.d_status);
+                                                    b.U_rank, b.counts, b.phi_acc, b.d_step, P, b.ovf_list,
+                                                    b.ovf_count, b.d_status);
+  voronoi_overflow_kernel<<<152, 64, 0, st>>>(g.reps, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id,
+                                              b.offsets, (int2*)b.U_pos, (float2*)b.U_dir, b.U_id, b.U_rank,
+                                              b.counts, b.phi_acc, b.d_step, P, b.ovf_list, b.ovf_count,
+                                              b.d_status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_voronoi_export(const Geometry& g, const Buffers& b, int rep, int n, int32_t* deg, int32_t* nbr,
-                                  cudaStream_t st) {
-  const int nb = (n + kBlock - 1) / kBlock;
-  if (nb == 0) return cudaSuccess;
-  voronoi_export_kernel<<<nb, kBlock, 0, st>>>(g.reps, rep, (const int2*)b.S_pos, b.S_id, b.offsets, deg, nbr,
-                                               b.d_status);
+cudaError_t launch_voronoi_export(const Geometry& g, const Buffers& b, int rep, int n, int pass, int32_t* deg,
+                                  const int64_t* out_off, int32_t* out_ids, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int nb = std::min((n + 63) / 64, 152 * 8);
+  voronoi_export_kernel<<<nb, 64, 0, st>>>(g.reps, rep, (const int2*)b.S_pos, b.S_id, b.offsets, pass, deg,
+                                           out_off, out_ids, b.d_status);
   return cudaGetLastError();
 }
 

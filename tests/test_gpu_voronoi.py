@@ -86,3 +86,27 @@ def test_coincident_points_are_reported():
         with pytest.raises(vk.VKError) as e:
             sim.neighbors()
         assert e.value.status == vk.VK_ERR_DEGENERATE
+
+
+def test_huge_cell_takes_the_overflow_path():
+    """A particle alone in a void ringed by 60 others has a 60-edge Voronoi
+    cell: more than the main kernel's polygon capacity, so it is finished by
+    the overflow kernel; lists and the update must still match the oracle."""
+    rng = np.random.default_rng(4)
+    L = 1 << 16
+    F = 8
+    ring_r = 20000.0
+    ang = np.sort(rng.uniform(0, 2 * np.pi, 60))
+    rad = ring_r * (1 + rng.uniform(-0.01, 0.01, 60))
+    c = L / 2
+    ring = np.stack([c + rad * np.cos(ang), c + rad * np.sin(ang)], 1)
+    outer = rng.uniform(0, L, size=(600, 2))
+    outer = outer[np.hypot(outer[:, 0] - c, outer[:, 1] - c) > 1.3 * ring_r]
+    pos = np.concatenate([[[c + 17, c - 31]], ring, outer]).astype(np.int64).astype(np.int32)
+    w = W.Workload(name="void", dim=2, pos_q=pos, dir=W.random_dirs(pos.shape[0]), theta=None,
+                   box_q=(L, L), frac_bits=F, rule="voronoi", k=0, v0=0.2, eta=0.3)
+    with vk.from_workload(w) as sim:
+        off, _ = _same(sim, pos, w.box_q)
+        assert off[1] - off[0] == 60
+        for _ in range(2):
+            check_step(sim, w, "voronoi")

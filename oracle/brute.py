@@ -57,6 +57,9 @@ def _tiled_sites(pos, Lx: int, Ly: int, rx: int, ry: int):
 def voronoi_brute(pos, box) -> List[List[int]]:
     """Voronoi neighbors by clipping bisectors (exact; O(N^3) on 25 N sites).
 
+    Coincident particles form one site: they are each other's neighbors, and
+    a coincident copy of a site clips nothing (its half-plane is the site's).
+
     Every site that can shape the cell of i lies within twice the cell's
     circumradius, which is at most half the box diagonal because the cell of
     i fits in the box-sized rectangle centred on i; the tiling below reaches
@@ -78,7 +81,9 @@ def voronoi_brute(pos, box) -> List[List[int]]:
         for c in range(X.shape[0]):
             j = int(ID[c])
             if int(ex[c]) == 0 and int(ey[c]) == 0:
-                continue  # the site itself
+                if j != i:
+                    nbrs.add(j)  # a coincident particle: same site, a neighbor
+                continue
             # bisector of i and site c: points m + t*d with m=(p_i+p_c)/2,
             # d = perp(p_c - p_i); keep-side of site e:
             #   2 x.(p_e - p_i) <= |p_e|^2 - |p_i|^2

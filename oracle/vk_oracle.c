@@ -17,7 +17,8 @@
  *     Voronoi neighbor lists"): a Delaunay triangulation built by incremental
  *     Bowyer-Watson insertion with exact integer orient/incircle predicates
  *     (empty-circumcircle definition), from which an edge is kept iff its dual
- *     Voronoi edge has positive length;
+ *     Voronoi edge has positive length; coincident particles form one site,
+ *     are each other's neighbors and share the site's neighbors;
  *   - one Vicsek update: the position step of Eq. (1) and the alignment rule of
  *     Eq. (2), in FP64, with the noise drawn from Philox4x32-10 (Salmon, Moraes,
  *     Dror & Shaw, SC'11) keyed by (seed) and countered by (id, step, replica);
@@ -570,10 +571,21 @@ static int vtess_build_auto(vtess_t* V, int64_t n, const int32_t* pos, const int
   }
 }
 
-/* Voronoi neighbors of every particle in a periodic rectangular box.  On success
- * offsets[0..n] is a CSR index into ids (sorted by id within a row).  If
- * `cap` is too small, *nnz receives the size needed and ORC_ERR_ARG is
- * returned with nothing written to ids. */
+typedef struct { int32_t x, y, id; } pidx_t;
+static int cmp_pidx(const void* a, const void* b) {
+  const pidx_t* p = (const pidx_t*)a;
+  const pidx_t* q = (const pidx_t*)b;
+  if (p->x != q->x) return p->x < q->x ? -1 : 1;
+  if (p->y != q->y) return p->y < q->y ? -1 : 1;
+  return p->id < q->id ? -1 : (p->id > q->id);
+}
+
+/* Voronoi neighbors of every particle in a periodic rectangular box.
+ * Coincident particles are one site: they are each other's neighbors and
+ * share the neighbors of their site (the Voronoi cell of the site).  On
+ * success offsets[0..n] is a CSR index into ids (sorted by id within a row).
+ * With ids == NULL only *nnz is computed; if `cap` is too small, *nnz
+ * receives the size needed and ORC_ERR_ARG is returned. */
 int orc_voronoi(int64_t n, const int32_t* pos, const int64_t* box, int64_t* offsets,
                 int32_t* ids, int64_t cap, int64_t* nnz) {
   if (n < 1 || box[0] < 2 || box[1] < 2 || box[0] > ((int64_t)1 << 31) || box[1] > ((int64_t)1 << 31))
@@ -581,44 +593,106 @@ int orc_voronoi(int64_t n, const int32_t* pos, const int64_t* box, int64_t* offs
   for (int64_t i = 0; i < n; ++i)
     if (pos[2 * i] < 0 || pos[2 * i] >= box[0] || pos[2 * i + 1] < 0 || pos[2 * i + 1] >= box[1])
       return ORC_ERR_ARG;
-  vtess_t V;
-  int rc = vtess_build_auto(&V, n, pos, box);
-  if (rc) return rc;
-  dt_t* D = &V.D;
-  int64_t pcap = 8 * n + 64, np = 0;
-  pair_t* pr = (pair_t*)malloc(sizeof(pair_t) * (size_t)pcap);
-  if (!pr) { vtess_free(&V); return ORC_ERR_OOM; }
-  for (int32_t t = 0; t < D->nt; ++t) {
-    tri_t* T = &D->t[t];
-    if (!T->alive) continue;
-    for (int e = 0; e < 3; ++e) {
-      int32_t a = T->v[(e + 1) % 3], b = T->v[(e + 2) % 3];
-      if (a >= n) continue; /* only edges leaving an original point */
-      int32_t u = T->nb[e];
-      if (u < 0) { free(pr); vtess_free(&V); return ORC_ERR_INTERNAL; }
-      int32_t w = -1;
-      for (int f = 0; f < 3; ++f)
-        if (D->t[u].v[f] != a && D->t[u].v[f] != b) w = D->t[u].v[f];
-      /* the dual Voronoi edge has zero length iff the four points are cocircular */
-      if (incircle(P(D, T->v[0]), P(D, T->v[1]), P(D, T->v[2]), P(D, w)) == 0) continue;
-      int32_t jb = V.orig[b];
-      if (jb == a) continue; /* an image of the particle itself */
-      if (np == pcap) {
-        pcap *= 2;
-        pair_t* q = (pair_t*)realloc(pr, sizeof(pair_t) * (size_t)pcap);
-        if (!q) { free(pr); vtess_free(&V); return ORC_ERR_OOM; }
-        pr = q;
+  /* distinct sites: site_of[i], members of each site in id order */
+  pidx_t* srt = (pidx_t*)malloc(sizeof(pidx_t) * (size_t)n);
+  int32_t* site_of = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t* site_pos = (int32_t*)malloc(sizeof(int32_t) * 2 * (size_t)n);
+  int64_t* site_beg = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int32_t* members = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  if (!srt || !site_of || !site_pos || !site_beg || !members) {
+    free(srt); free(site_of); free(site_pos); free(site_beg); free(members);
+    return ORC_ERR_OOM;
+  }
+  for (int64_t i = 0; i < n; ++i) { srt[i].x = pos[2 * i]; srt[i].y = pos[2 * i + 1]; srt[i].id = (int32_t)i; }
+  qsort(srt, (size_t)n, sizeof(pidx_t), cmp_pidx);
+  int64_t ns = 0;
+  for (int64_t r = 0; r < n; ++r) {
+    if (r == 0 || srt[r].x != srt[r - 1].x || srt[r].y != srt[r - 1].y) {
+      site_beg[ns] = r;
+      site_pos[2 * ns] = srt[r].x;
+      site_pos[2 * ns + 1] = srt[r].y;
+      ++ns;
+    }
+    site_of[srt[r].id] = (int32_t)(ns - 1);
+    members[r] = srt[r].id;
+  }
+  site_beg[ns] = n;
+  free(srt);
+  int64_t npair = 0;
+  pair_t* pr = NULL;
+  int rc = ORC_OK;
+  if (ns >= 1) {
+    vtess_t V;
+    rc = vtess_build_auto(&V, ns, site_pos, box);
+    if (rc == ORC_OK) {
+      dt_t* D = &V.D;
+      int64_t pcap = 8 * ns + 64;
+      pair_t* sp = (pair_t*)malloc(sizeof(pair_t) * (size_t)pcap);
+      int64_t nsp = 0;
+      if (!sp) rc = ORC_ERR_OOM;
+      for (int32_t t = 0; t < D->nt && rc == ORC_OK; ++t) {
+        tri_t* T = &D->t[t];
+        if (!T->alive) continue;
+        for (int e = 0; e < 3; ++e) {
+          int32_t a = T->v[(e + 1) % 3], b = T->v[(e + 2) % 3];
+          if (a >= ns) continue; /* only edges leaving an original site */
+          int32_t u = T->nb[e];
+          if (u < 0) { rc = ORC_ERR_INTERNAL; break; }
+          int32_t w = -1;
+          for (int f = 0; f < 3; ++f)
+            if (D->t[u].v[f] != a && D->t[u].v[f] != b) w = D->t[u].v[f];
+          /* the dual Voronoi edge has zero length iff the four points are cocircular */
+          if (incircle(P(D, T->v[0]), P(D, T->v[1]), P(D, T->v[2]), P(D, w)) == 0) continue;
+          int32_t jb = V.orig[b];
+          if (jb == a) continue; /* an image of the site itself */
+          if (nsp == pcap) {
+            pcap *= 2;
+            pair_t* q = (pair_t*)realloc(sp, sizeof(pair_t) * (size_t)pcap);
+            if (!q) { rc = ORC_ERR_OOM; break; }
+            sp = q;
+          }
+          sp[nsp].a = a;
+          sp[nsp].b = jb;
+          ++nsp;
+        }
       }
-      pr[np].a = a;
-      pr[np].b = jb;
-      ++np;
+      vtess_free(&V);
+      /* expand site pairs to particle pairs, plus the coincident partners */
+      int64_t tot = 0;
+      for (int64_t q = 0; q < nsp && rc == ORC_OK; ++q)
+        tot += (site_beg[sp[q].a + 1] - site_beg[sp[q].a]) * (site_beg[sp[q].b + 1] - site_beg[sp[q].b]);
+      for (int64_t c = 0; c < ns; ++c) {
+        int64_t m = site_beg[c + 1] - site_beg[c];
+        tot += m * (m - 1);
+      }
+      if (rc == ORC_OK) {
+        pr = (pair_t*)malloc(sizeof(pair_t) * (size_t)(tot > 0 ? tot : 1));
+        if (!pr) rc = ORC_ERR_OOM;
+      }
+      for (int64_t q = 0; q < nsp && rc == ORC_OK; ++q)
+        for (int64_t x = site_beg[sp[q].a]; x < site_beg[sp[q].a + 1]; ++x)
+          for (int64_t y = site_beg[sp[q].b]; y < site_beg[sp[q].b + 1]; ++y) {
+            pr[npair].a = members[x];
+            pr[npair].b = members[y];
+            ++npair;
+          }
+      for (int64_t c = 0; c < ns && rc == ORC_OK; ++c)
+        for (int64_t x = site_beg[c]; x < site_beg[c + 1]; ++x)
+          for (int64_t y = site_beg[c]; y < site_beg[c + 1]; ++y)
+            if (x != y) {
+              pr[npair].a = members[x];
+              pr[npair].b = members[y];
+              ++npair;
+            }
+      free(sp);
     }
   }
-  vtess_free(&V);
-  qsort(pr, (size_t)np, sizeof(pair_t), cmp_pair);
+  free(site_of); free(site_pos); free(site_beg); free(members);
+  if (rc != ORC_OK) { free(pr); return rc; }
+  qsort(pr, (size_t)npair, sizeof(pair_t), cmp_pair);
   int64_t u = 0;
-  for (int64_t s = 0; s < np; ++s)
-    if (s == 0 || pr[s].a != pr[s - 1].a || pr[s].b != pr[s - 1].b) pr[u++] = pr[s];
+  for (int64_t s2 = 0; s2 < npair; ++s2)
+    if (s2 == 0 || pr[s2].a != pr[s2 - 1].a || pr[s2].b != pr[s2 - 1].b) pr[u++] = pr[s2];
   *nnz = u;
   if (ids == NULL) { free(pr); return ORC_OK; } /* size query */
   if (u > cap) { free(pr); return ORC_ERR_ARG; }

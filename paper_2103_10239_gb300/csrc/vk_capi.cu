@@ -4,8 +4,9 @@
 // optional CUDA graph of a multi-step sequence and the tracing events.  A
 // time step (Alg. 1 of the paper: build the neighbor relation, then update) is
 //   search+update kernel (kNN or Voronoi; writes the next state and the
-//   histogram of the new cells) -> 3-kernel exclusive scan -> scatter into
-//   cell-sorted order (also advances the device step counter).
+//   histogram of the new coarse cells) -> build of the two-level grid (coarse
+//   scan with sub-grid sides, sub-cell histogram, sub-cell scan) -> scatter
+//   into (coarse, sub-cell) order (also advances the device step counter).
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -20,7 +21,7 @@ using namespace vk;
 namespace {
 
 constexpr int kPhases = 5;
-const char* kPhaseNames[kPhases] = {"search_update", "scan", "scatter", "load_sort", "export"};
+const char* kPhaseNames[kPhases] = {"search_update", "build", "scatter", "load_sort", "export"};
 
 thread_local std::string g_init_error;
 
@@ -148,19 +149,28 @@ vk_status record_end(vk_sim* s, int phase, cudaEvent_t e0, int launches) {
   return VK_OK;
 }
 
+int64_t sub_cells_bound(const vk_sim* s) { return s->n_cells + s->n_total / kSubTarget + 1; }
+
 vk_status ensure_cells_capacity(vk_sim* s) {
   if (s->n_cells <= s->cells_cap) return VK_OK;
-  cudaFree(s->b.counts);
-  cudaFree(s->b.offsets);
-  cudaFree(s->b.bsum);
-  s->b.counts = nullptr;
-  s->b.offsets = nullptr;
-  s->b.bsum = nullptr;
+  void* old[] = {s->b.counts, s->b.offsets, s->b.bsum, s->b.sub_s, s->b.sub_base,
+                 s->b.sub_count, s->b.sub_off, s->b.bsum2};
+  for (void* p : old)
+    if (p) cudaFree(p);
+  s->b.counts = s->b.offsets = s->b.bsum = s->b.sub_base = s->b.sub_count = s->b.sub_off = s->b.bsum2 = nullptr;
+  s->b.sub_s = nullptr;
   const int64_t cap = s->n_cells;
+  const int64_t scap = sub_cells_bound(s);
   VK_CUDA(s, dalloc(&s->b.counts, cap));
   VK_CUDA(s, dalloc(&s->b.offsets, cap + 1));
-  VK_CUDA(s, dalloc(&s->b.bsum, (cap + 2047) / 2048 + 1));
+  VK_CUDA(s, dalloc(&s->b.bsum, 2 * ((cap + 2047) / 2048 + 1)));
+  VK_CUDA(s, dalloc(&s->b.sub_s, cap));
+  VK_CUDA(s, dalloc(&s->b.sub_base, cap + 1));
+  VK_CUDA(s, dalloc(&s->b.sub_count, scap));
+  VK_CUDA(s, dalloc(&s->b.sub_off, scap + 1));
+  VK_CUDA(s, dalloc(&s->b.bsum2, (scap + 2047) / 2048 + 1));
   VK_CUDA(s, cudaMemsetAsync(s->b.counts, 0, sizeof(uint32_t) * cap, s->stream));
+  VK_CUDA(s, cudaMemsetAsync(s->b.sub_count, 0, sizeof(uint32_t) * scap, s->stream));
   s->cells_cap = cap;
   return VK_OK;
 }
@@ -171,6 +181,7 @@ void refresh_geometry(vk_sim* s) {
   s->g.n_rep = s->n_rep;
   s->g.n_total = s->n_total;
   s->g.n_cells = s->n_cells;
+  s->g.n_sub_max = sub_cells_bound(s);
   s->g.n_tasks = (int)s->tasks_h.size();
   s->g.reps = s->reps_d;
   s->g.tasks = s->tasks_d;
@@ -190,9 +201,9 @@ vk_status sort_from_U(vk_sim* s) {
   vk_status st = record_begin(s, 3, &e0);
   if (st) return st;
   VK_CUDA(s, launch_count(s->g, s->b, s->stream));
-  VK_CUDA(s, launch_scan(s->g, s->b, s->stream));
+  VK_CUDA(s, launch_build(s->g, s->b, s->stream));
   VK_CUDA(s, launch_scatter(s->g, s->b, step_params(s), 0, s->stream));
-  return record_end(s, 3, e0, 5);
+  return record_end(s, 3, e0, 9);
 }
 
 vk_status read_status(vk_sim* s) {
@@ -222,8 +233,8 @@ vk_status enqueue_step(vk_sim* s) {
   else VK_CUDA(s, launch_voronoi_step(s->g, s->b, P, s->stream));
   if ((st = record_end(s, 0, e0, s->prm.rule == VK_RULE_KNN ? 1 : 2))) return st;
   if ((st = record_begin(s, 1, &e0))) return st;
-  VK_CUDA(s, launch_scan(s->g, s->b, s->stream));
-  if ((st = record_end(s, 1, e0, 3))) return st;
+  VK_CUDA(s, launch_build(s->g, s->b, s->stream));
+  if ((st = record_end(s, 1, e0, 7))) return st;
   if ((st = record_begin(s, 2, &e0))) return st;
   VK_CUDA(s, launch_scatter(s->g, s->b, P, 1, s->stream));
   return record_end(s, 2, e0, 1);
@@ -630,7 +641,8 @@ void vk_destroy(vk_sim* s) {
     }
   void* bufs[] = {s->b.S_pos, s->b.S_dir, s->b.S_id, s->b.U_pos, s->b.U_dir, s->b.U_id, s->b.U_rank,
                   s->b.counts, s->b.offsets, s->b.bsum, s->b.phi_acc, s->b.d_step, s->b.d_status,
-                  s->b.ovf_list, s->b.ovf_count, s->reps_d, s->tasks_d};
+                  s->b.ovf_list, s->b.ovf_count, s->reps_d, s->tasks_d, s->b.sub_s, s->b.sub_base,
+                  s->b.sub_count, s->b.sub_off, s->b.bsum2};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -696,7 +708,7 @@ vk_status vk_get_info(vk_sim* s, vk_info* out) {
   out->dim = s->dim;
   out->n_cells = s->n_cells;
   out->step = s->step;
-  out->kernels_per_step = s->prm.rule == VK_RULE_KNN ? 5 : 6;
+  out->kernels_per_step = s->prm.rule == VK_RULE_KNN ? 9 : 10;
   out->rule = s->prm.rule;
   out->k = s->prm.k;
   return VK_OK;

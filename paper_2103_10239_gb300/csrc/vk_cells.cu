@@ -1,8 +1,11 @@
 // vk_cells.cu -- the cell-list build of the search grid (Sec. "Introduction":
-// partition the domain into cells so that only nearby cells are searched):
-// an atomic histogram of particles per cell, an exclusive scan of the counts,
-// and a scatter of the state into cell-sorted order.  Also the import/export
-// of user arrays (id order) to and from the sorted layout.
+// partition the domain into cells so that only nearby cells are searched;
+// stenciled or hierarchical structures for large density disparities):
+//   coarse histogram (atomic, fused into the search+update kernel) ->
+//   coarse scan, which also picks every coarse cell's sub-grid side ->
+//   sub-cell histogram (atomic; the particle's rank in its sub-cell) ->
+//   sub-cell scan -> scatter of the state into (coarse, sub-cell) order.
+// Also the import/export of user arrays (id order) to and from that layout.
 #include "vk_internal.cuh"
 
 namespace vk {
@@ -48,12 +51,12 @@ __global__ void __launch_bounds__(kBlock) load_kernel(const Rep* __restrict__ re
   U_id[s] = li;
 }
 
+// coarse histogram of U (the search+update kernel does this for every step)
 template <int DIM>
 __global__ void __launch_bounds__(kBlock) count_kernel(const Rep* __restrict__ reps,
                                                        const BlockTask* __restrict__ tasks,
                                                        const typename Vec<DIM>::P* __restrict__ U_pos,
-                                                       uint32_t* __restrict__ counts,
-                                                       uint32_t* __restrict__ U_rank) {
+                                                       uint32_t* __restrict__ counts) {
   const BlockTask t = tasks[blockIdx.x];
   const Rep R = reps[t.rep];
   const int li = t.first + (int)threadIdx.x;
@@ -61,7 +64,25 @@ __global__ void __launch_bounds__(kBlock) count_kernel(const Rep* __restrict__ r
   const int64_t s = R.p0 + li;
   int32_t p[3];
   unpack(U_pos[s], p);
-  U_rank[s] = atomicAdd(counts + linear_cell<DIM>(R, p), 1u);
+  atomicAdd(counts + linear_cell<DIM>(R, p), 1u);
+}
+
+// sub-cell histogram of U: the rank of every particle inside its sub-cell
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) sub_count_kernel(const Rep* __restrict__ reps,
+                                                           const BlockTask* __restrict__ tasks,
+                                                           const typename Vec<DIM>::P* __restrict__ U_pos,
+                                                           GridView G, uint32_t* __restrict__ sub_count,
+                                                           uint32_t* __restrict__ U_rank) {
+  const BlockTask t = tasks[blockIdx.x];
+  const Rep R = reps[t.rep];
+  const int li = t.first + (int)threadIdx.x;
+  if (li >= R.n) return;
+  const int64_t s = R.p0 + li;
+  int32_t p[3];
+  unpack(U_pos[s], p);
+  const int64_t g = sub_cell_of<DIM>(R, G, p, linear_cell<DIM>(R, p));
+  U_rank[s] = atomicAdd(sub_count + g, 1u);
 }
 
 constexpr int kScanItems = 8;
@@ -156,14 +177,103 @@ __global__ void __launch_bounds__(kBlock) scan_apply_kernel(uint32_t* __restrict
   }
 }
 
+// ---- coarse scan: (count, s^2) pairs -> offsets, sub-grid sides, sub bases
+__device__ __forceinline__ uint32_t sub_cells(uint32_t count, int dim) {
+  const int s = dim == 2 ? sub_side(count) : 1;
+  return (uint32_t)(s * s);
+}
+
+__global__ void __launch_bounds__(kBlock) pair_reduce_kernel(const uint32_t* __restrict__ counts, int64_t n,
+                                                             int dim, uint2* __restrict__ bsum) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  uint32_t v = 0, w = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    const int64_t c = base + (int64_t)j * kBlock + threadIdx.x;
+    if (c < n) {
+      const uint32_t m = counts[c];
+      v += m;
+      w += sub_cells(m, dim);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v += __shfl_xor_sync(0xffffffffu, v, o);
+    w += __shfl_xor_sync(0xffffffffu, w, o);
+  }
+  __shared__ uint2 sw[kBlock / 32];
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = make_uint2(v, w);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint2 t = make_uint2(0, 0);
+    for (int i = 0; i < kBlock / 32; ++i) {
+      t.x += sw[i].x;
+      t.y += sw[i].y;
+    }
+    bsum[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) pair_bsum_kernel(uint2* __restrict__ bsum, int nb,
+                                                           uint32_t* __restrict__ offsets,
+                                                           uint32_t* __restrict__ sub_base, int64_t n) {
+  uint32_t cv = 0, cw = 0;
+  for (int base = 0; base < nb; base += kBlock) {
+    const int i = base + (int)threadIdx.x;
+    const uint2 v = i < nb ? bsum[i] : make_uint2(0, 0);
+    uint32_t tv, tw;
+    const uint32_t ev = block_exclusive_scan(v.x, &tv);
+    const uint32_t ew = block_exclusive_scan(v.y, &tw);
+    if (i < nb) bsum[i] = make_uint2(cv + ev, cw + ew);
+    cv += tv;
+    cw += tw;
+  }
+  if (threadIdx.x == 0) {
+    offsets[n] = cv;
+    sub_base[n] = cw;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) pair_apply_kernel(uint32_t* __restrict__ counts, int64_t n, int dim,
+                                                            const uint2* __restrict__ bsum,
+                                                            uint32_t* __restrict__ offsets,
+                                                            uint8_t* __restrict__ sub_s,
+                                                            uint32_t* __restrict__ sub_base) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems], w[kScanItems];
+  uint32_t tv = 0, tw = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    const int64_t c = base + j;
+    v[j] = c < n ? counts[c] : 0u;
+    w[j] = c < n ? sub_cells(v[j], dim) : 0u;
+    tv += v[j];
+    tw += w[j];
+  }
+  uint32_t totv, totw;
+  uint32_t rv = bsum[blockIdx.x].x + block_exclusive_scan(tv, &totv);
+  uint32_t rw = bsum[blockIdx.x].y + block_exclusive_scan(tw, &totw);
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    const int64_t c = base + j;
+    if (c < n) {
+      offsets[c] = rv;
+      sub_base[c] = rw;
+      sub_s[c] = (uint8_t)(dim == 2 ? sub_side(v[j]) : 1);
+      counts[c] = 0u;
+    }
+    rv += v[j];
+    rw += w[j];
+  }
+}
+
 template <int DIM>
 __global__ void __launch_bounds__(kBlock) scatter_kernel(const Rep* __restrict__ reps,
                                                          const BlockTask* __restrict__ tasks,
                                                          const typename Vec<DIM>::P* __restrict__ U_pos,
                                                          const typename Vec<DIM>::F* __restrict__ U_dir,
                                                          const int32_t* __restrict__ U_id,
-                                                         const uint32_t* __restrict__ U_rank,
-                                                         const uint32_t* __restrict__ offsets,
+                                                         const uint32_t* __restrict__ U_rank, GridView G,
                                                          typename Vec<DIM>::P* __restrict__ S_pos,
                                                          typename Vec<DIM>::F* __restrict__ S_dir,
                                                          int32_t* __restrict__ S_id, int advance_step,
@@ -188,7 +298,7 @@ __global__ void __launch_bounds__(kBlock) scatter_kernel(const Rep* __restrict__
   const typename Vec<DIM>::P pv = U_pos[s];
   int32_t p[3];
   unpack(pv, p);
-  const uint32_t dst = offsets[linear_cell<DIM>(R, p)] + U_rank[s];
+  const uint32_t dst = G.sub_off[sub_cell_of<DIM>(R, G, p, linear_cell<DIM>(R, p))] + U_rank[s];
   S_pos[dst] = pv;
   S_dir[dst] = U_dir[s];
   S_id[dst] = U_id[s];
@@ -258,32 +368,54 @@ cudaError_t launch_load(const Geometry& g, const Buffers& b, const int32_t* pos_
   return cudaGetLastError();
 }
 
+static GridView grid_view(const Buffers& b) {
+  GridView G;
+  G.off = b.offsets;
+  G.sub_s = b.sub_s;
+  G.sub_base = b.sub_base;
+  G.sub_off = b.sub_off;
+  return G;
+}
+
 cudaError_t launch_count(const Geometry& g, const Buffers& b, cudaStream_t st) {
   if (g.dim == 2)
-    count_kernel<2><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int2*)b.U_pos, b.counts, b.U_rank);
+    count_kernel<2><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int2*)b.U_pos, b.counts);
   else
-    count_kernel<3><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int4*)b.U_pos, b.counts, b.U_rank);
+    count_kernel<3><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int4*)b.U_pos, b.counts);
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan(const Geometry& g, const Buffers& b, cudaStream_t st) {
+cudaError_t launch_build(const Geometry& g, const Buffers& b, cudaStream_t st) {
   const int nb = (int)((g.n_cells + kScanTile - 1) / kScanTile);
-  scan_reduce_kernel<<<nb, kBlock, 0, st>>>(b.counts, g.n_cells, b.bsum);
-  scan_bsum_kernel<<<1, kBlock, 0, st>>>(b.bsum, nb, b.offsets, g.n_cells);
-  scan_apply_kernel<<<nb, kBlock, 0, st>>>(b.counts, g.n_cells, b.bsum, b.offsets);
+  pair_reduce_kernel<<<nb, kBlock, 0, st>>>(b.counts, g.n_cells, g.dim, (uint2*)b.bsum);
+  pair_bsum_kernel<<<1, kBlock, 0, st>>>((uint2*)b.bsum, nb, b.offsets, b.sub_base, g.n_cells);
+  pair_apply_kernel<<<nb, kBlock, 0, st>>>(b.counts, g.n_cells, g.dim, (const uint2*)b.bsum, b.offsets, b.sub_s,
+                                           b.sub_base);
+  const GridView G = grid_view(b);
+  if (g.dim == 2)
+    sub_count_kernel<2><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int2*)b.U_pos, G, b.sub_count,
+                                                       b.U_rank);
+  else
+    sub_count_kernel<3><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int4*)b.U_pos, G, b.sub_count,
+                                                       b.U_rank);
+  const int nb2 = (int)((g.n_sub_max + kScanTile - 1) / kScanTile);
+  scan_reduce_kernel<<<nb2, kBlock, 0, st>>>(b.sub_count, g.n_sub_max, b.bsum2);
+  scan_bsum_kernel<<<1, kBlock, 0, st>>>(b.bsum2, nb2, b.sub_off, g.n_sub_max);
+  scan_apply_kernel<<<nb2, kBlock, 0, st>>>(b.sub_count, g.n_sub_max, b.bsum2, b.sub_off);
   return cudaGetLastError();
 }
 
 cudaError_t launch_scatter(const Geometry& g, const Buffers& b, const StepParams& P, int advance_step,
                            cudaStream_t st) {
+  const GridView G = grid_view(b);
   if (g.dim == 2)
     scatter_kernel<2><<<g.n_tasks, kBlock, 0, st>>>(
-        g.reps, g.tasks, (const int2*)b.U_pos, (const float2*)b.U_dir, b.U_id, b.U_rank, b.offsets,
+        g.reps, g.tasks, (const int2*)b.U_pos, (const float2*)b.U_dir, b.U_id, b.U_rank, G,
         (int2*)b.S_pos, (float2*)b.S_dir, b.S_id, advance_step, b.d_step, b.phi_acc, P.n_rep, P.phi_cap,
         b.ovf_count);
   else
     scatter_kernel<3><<<g.n_tasks, kBlock, 0, st>>>(
-        g.reps, g.tasks, (const int4*)b.U_pos, (const float4*)b.U_dir, b.U_id, b.U_rank, b.offsets,
+        g.reps, g.tasks, (const int4*)b.U_pos, (const float4*)b.U_dir, b.U_id, b.U_rank, G,
         (int4*)b.S_pos, (float4*)b.S_dir, b.S_id, advance_step, b.d_step, b.phi_acc, P.n_rep, P.phi_cap,
         b.ovf_count);
   return cudaGetLastError();

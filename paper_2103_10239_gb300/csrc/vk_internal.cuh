@@ -12,6 +12,7 @@
 //     256-thread block never straddles two replicas.
 #pragma once
 #include <cstdint>
+#include <climits>
 #include <cuda_runtime.h>
 
 namespace vk {
@@ -158,33 +159,160 @@ __device__ __forceinline__ int32_t wrap_add(int32_t p, int32_t d, uint32_t L) {
 }
 
 // --------------------------------------------------------------------------
-// Ring walk over the cells around a particle.  Ring r is the (2r+1)^DIM block
-// of cells minus the (2r-1)^DIM block, clamped per axis so that no cell is
-// visited twice in small boxes.  Each row segment of a ring is one contiguous
-// run [qb, qe) of the cell-sorted arrays and is handed to run(qb, qe).  After
-// ring r, stop(B2) is asked whether to stop, where B2 is the exact squared
-// distance from the particle to the nearest point outside the scanned block
-// (over the axes the block does not yet cover).  Returns true iff the whole
-// box was scanned.
+// Two-level search grid.  The coarse grid is uniform per replica; coarse
+// cell c holding m particles is split into s x s sub-cells, s = sub_side(m)
+// (2D; 3D keeps s = 1).  Particles are sorted by (coarse cell, sub-cell
+// row-major), so every row of sub-cells, and every row of coarse cells, is a
+// contiguous run of the sorted arrays.
 // --------------------------------------------------------------------------
-template <class RunFn>
-__device__ __forceinline__ void walk_row(const Rep& R, int cx, int a, int b, int64_t rowbase,
-                                         const uint32_t* __restrict__ off, RunFn& run) {
-  if (a > b) return;
-  const int nx = R.nc[0];
-  const int start = wrap_index(cx + a, nx);
-  const int len = b - a + 1;
-  const int end1 = min(start + len, nx);
-  run(off[rowbase + start], off[rowbase + end1]);
-  if (start + len > nx) run(off[rowbase], off[rowbase + start + len - nx]);
+constexpr int kSubMax = 32;      // largest sub-grid side
+constexpr int kSubTarget = 2;    // target particles per sub-cell
+
+__device__ __host__ __forceinline__ int sub_side(uint32_t m) {
+  int s = 1;
+  while (s < kSubMax && (uint32_t)((s + 1) * (s + 1) * kSubTarget) <= m) ++s;
+  return s;
 }
 
-template <int DIM, class RunFn, class StopFn>
-__device__ __forceinline__ bool ring_walk(const Rep& R, const int32_t* pi, const uint32_t* __restrict__ off,
-                                          RunFn& run, StopFn& stop) {
+struct GridView {
+  const uint32_t* __restrict__ off;       // coarse cell -> first slot (n_cells + 1)
+  const uint8_t* __restrict__ sub_s;      // coarse cell -> s
+  const uint32_t* __restrict__ sub_base;  // coarse cell -> first sub-cell (n_cells + 1)
+  const uint32_t* __restrict__ sub_off;   // sub-cell -> first slot
+};
+
+// sub-cell (sx, sy) of a point at in-cell offset u in a cell of width w
+__device__ __forceinline__ int sub_index(int64_t u, int64_t w, int s) {
+  return (int)((u * s) / w);
+}
+
+// global sub-cell index of a position (2D), given its coarse cell
+template <int DIM>
+__device__ __forceinline__ int64_t sub_cell_of(const Rep& R, const GridView& G, const int32_t* p, int64_t gcell) {
+  const int s = G.sub_s[gcell];
+  int64_t j = 0;
+  if (DIM == 2 && s > 1) {
+    const int cx = cell_of(p[0], R.nc[0], R.L[0]), cy = cell_of(p[1], R.nc[1], R.L[1]);
+    const int64_t x0 = cell_lo(cx, R.nc[0], R.L[0]), y0 = cell_lo(cy, R.nc[1], R.L[1]);
+    const int64_t wx = cell_lo(cx + 1, R.nc[0], R.L[0]) - x0, wy = cell_lo(cy + 1, R.nc[1], R.L[1]) - y0;
+    j = (int64_t)sub_index(p[1] - y0, wy, s) * s + sub_index(p[0] - x0, wx, s);
+  }
+  return (int64_t)G.sub_base[gcell] + j;
+}
+
+// upper bound (integer) of the square root of r2; r2 may be ~0ull (infinite)
+__device__ __forceinline__ int64_t radius_upper(uint64_t r2) {
+  if (r2 >= (1ull << 62)) return INT64_MAX / 4;
+  const float f = sqrtf((float)r2) * 1.0000005f;
+  int64_t r = (int64_t)f + 1;
+  while ((uint64_t)r * (uint64_t)r < r2) ++r;
+  return r;
+}
+
+// Walk the grid around the particle at pi.  run(qb, qe) receives runs of
+// sorted slots; radius2() is an upper bound of the squared distance beyond
+// which candidates no longer matter (~0ull while unknown; never increasing);
+// stop(B2) is asked after each coarse ring, B2 being the exact squared
+// distance from the particle to the nearest point outside the scanned block
+// of coarse cells.  Returns true iff the whole box was scanned.
+//
+// Phase 1 (own coarse cell split in sub-cells): rings of sub-cells around
+// the particle's sub-cell, until the remaining sub-cells are provably farther
+// than radius2 or the cell is exhausted.  Phase 2: rings of coarse cells
+// (clamped so that no cell is visited twice); in a split cell only the
+// sub-cells meeting the box [p - r, p + r], r^2 >= radius2(), are scanned.
+template <int DIM, class RunFn, class R2Fn, class StopFn>
+__device__ __forceinline__ bool grid_walk(const Rep& R, const int32_t* pi, const GridView& G, RunFn& run,
+                                          R2Fn& radius2, StopFn& stop) {
   int c[3] = {0, 0, 0};
 #pragma unroll
   for (int a = 0; a < DIM; ++a) c[a] = cell_of(pi[a], R.nc[a], R.L[a]);
+  int64_t own = 0;
+#pragma unroll
+  for (int a = DIM - 1; a >= 0; --a) own = own * R.nc[a] + c[a];
+  own += R.c0;
+  const int s_own = G.sub_s[own];
+  bool own_done = false;
+  if (DIM == 2 && s_own > 1) {
+    // ---- phase 1: sub-cell rings inside the own coarse cell
+    const int s = s_own;
+    const int64_t x0 = cell_lo(c[0], R.nc[0], R.L[0]), y0 = cell_lo(c[1], R.nc[1], R.L[1]);
+    const int64_t wx = cell_lo(c[0] + 1, R.nc[0], R.L[0]) - x0, wy = cell_lo(c[1] + 1, R.nc[1], R.L[1]) - y0;
+    const int sx = sub_index(pi[0] - x0, wx, s), sy = sub_index(pi[1] - y0, wy, s);
+    const uint32_t base = G.sub_base[own];
+    for (int r = 0;; ++r) {
+      const int bx0 = max(sx - r, 0), bx1 = min(sx + r, s - 1), by0 = max(sy - r, 0), by1 = min(sy + r, s - 1);
+      const int px0 = r ? max(sx - r + 1, 0) : 1, px1 = r ? min(sx + r - 1, s - 1) : 0;
+      const int py0 = r ? max(sy - r + 1, 0) : 1, py1 = r ? min(sy + r - 1, s - 1) : 0;
+      for (int yy = by0; yy <= by1; ++yy) {
+        const uint32_t rb = base + (uint32_t)yy * s;
+        if (yy < py0 || yy > py1 || px0 > px1) {
+          run(G.sub_off[rb + bx0], G.sub_off[rb + bx1 + 1]);
+        } else {
+          if (bx0 < px0) run(G.sub_off[rb + bx0], G.sub_off[rb + px0]);
+          if (bx1 > px1) run(G.sub_off[rb + px1 + 1], G.sub_off[rb + bx1 + 1]);
+        }
+      }
+      if (bx0 == 0 && by0 == 0 && bx1 == s - 1 && by1 == s - 1) break;
+      int64_t B = INT64_MAX;
+      if (bx0 > 0) B = min(B, (int64_t)pi[0] - (x0 + (bx0 * wx + s - 1) / s) + 1);
+      if (bx1 < s - 1) B = min(B, x0 + ((bx1 + 1) * wx + s - 1) / s - (int64_t)pi[0]);
+      if (by0 > 0) B = min(B, (int64_t)pi[1] - (y0 + (by0 * wy + s - 1) / s) + 1);
+      if (by1 < s - 1) B = min(B, y0 + ((by1 + 1) * wy + s - 1) / s - (int64_t)pi[1]);
+      if (radius2() < (uint64_t)B * (uint64_t)B) break;
+    }
+    own_done = true;
+  }
+  // ---- phase 2: coarse rings
+  // visit coarse cells x-offsets [a, b] of the row at unwrapped y offset uy
+  auto visit_row = [&](int a, int b, int64_t rowbase, int64_t ucy, int64_t ucz) {
+    if (a > b) return;
+    const int nx = R.nc[0];
+    uint32_t pend_b = 0, pend_e = 0;
+    bool pend = false;
+    for (int ox = a; ox <= b; ++ox) {
+      const int xc = wrap_index(c[0] + ox, nx);
+      const int64_t g = rowbase + xc;
+      const int s = G.sub_s[g];
+      if ((g == own && own_done) || s > 1) {
+        if (pend) run(pend_b, pend_e);
+        pend = false;
+        if (g == own && own_done) continue;
+        // split cell: only the sub-cells meeting the box [p - rad, p + rad]
+        const uint64_t r2 = radius2();
+        if (r2 == ~0ull) {
+          run(G.off[g], G.off[g + 1]);
+          continue;
+        }
+        const int64_t rad = radius_upper(r2);
+        const int64_t ucx = (int64_t)c[0] + ox;
+        const int64_t x0 = cell_lo(ucx, R.nc[0], R.L[0]), y0 = cell_lo(ucy, R.nc[1], R.L[1]);
+        const int64_t wx = cell_lo(ucx + 1, R.nc[0], R.L[0]) - x0, wy = cell_lo(ucy + 1, R.nc[1], R.L[1]) - y0;
+        const int64_t lx = (int64_t)pi[0] - rad - x0, hx = (int64_t)pi[0] + rad - x0;
+        const int64_t ly = (int64_t)pi[1] - rad - y0, hy = (int64_t)pi[1] + rad - y0;
+        if (hx < 0 || lx >= wx || hy < 0 || ly >= wy) continue;
+        const int sx0 = lx <= 0 ? 0 : sub_index(lx, wx, s), sx1 = hx >= wx ? s - 1 : sub_index(hx, wx, s);
+        const int sy0 = ly <= 0 ? 0 : sub_index(ly, wy, s), sy1 = hy >= wy ? s - 1 : sub_index(hy, wy, s);
+        const uint32_t base = G.sub_base[g];
+        for (int yy = sy0; yy <= sy1; ++yy) {
+          const uint32_t rb = base + (uint32_t)yy * s;
+          run(G.sub_off[rb + sx0], G.sub_off[rb + sx1 + 1]);
+        }
+      } else {
+        const uint32_t qb = G.off[g], qe = G.off[g + 1];
+        if (pend && qb == pend_e) {
+          pend_e = qe;
+        } else {
+          if (pend) run(pend_b, pend_e);
+          pend = true;
+          pend_b = qb;
+          pend_e = qe;
+        }
+      }
+    }
+    if (pend) run(pend_b, pend_e);
+    (void)ucz;
+  };
   for (int r = 0;; ++r) {
     int lo[3], hi[3], plo[3], phi[3];
     bool full_all = true, any_new = (r == 0);
@@ -201,11 +329,12 @@ __device__ __forceinline__ bool ring_walk(const Rep& R, const int32_t* pi, const
     if (DIM == 2) {
       for (int oy = lo[1]; oy <= hi[1]; ++oy) {
         const int64_t rowbase = R.c0 + (int64_t)wrap_index(c[1] + oy, R.nc[1]) * R.nc[0];
+        const int64_t ucy = (int64_t)c[1] + oy;
         if (oy < plo[1] || oy > phi[1]) {
-          walk_row(R, c[0], lo[0], hi[0], rowbase, off, run);
+          visit_row(lo[0], hi[0], rowbase, ucy, 0);
         } else {
-          walk_row(R, c[0], lo[0], plo[0] - 1, rowbase, off, run);
-          walk_row(R, c[0], phi[0] + 1, hi[0], rowbase, off, run);
+          visit_row(lo[0], plo[0] - 1, rowbase, ucy, 0);
+          visit_row(phi[0] + 1, hi[0], rowbase, ucy, 0);
         }
       }
     } else {
@@ -214,11 +343,12 @@ __device__ __forceinline__ bool ring_walk(const Rep& R, const int32_t* pi, const
         const bool oldz = !(oz < plo[2] || oz > phi[2]);
         for (int oy = lo[1]; oy <= hi[1]; ++oy) {
           const int64_t rowbase = R.c0 + (zb + wrap_index(c[1] + oy, R.nc[1])) * R.nc[0];
+          const int64_t ucy = (int64_t)c[1] + oy;
           if (!oldz || oy < plo[1] || oy > phi[1]) {
-            walk_row(R, c[0], lo[0], hi[0], rowbase, off, run);
+            visit_row(lo[0], hi[0], rowbase, ucy, 0);
           } else {
-            walk_row(R, c[0], lo[0], plo[0] - 1, rowbase, off, run);
-            walk_row(R, c[0], phi[0] + 1, hi[0], rowbase, off, run);
+            visit_row(lo[0], plo[0] - 1, rowbase, ucy, 0);
+            visit_row(phi[0] + 1, hi[0], rowbase, ucy, 0);
           }
         }
       }
@@ -420,7 +550,12 @@ struct Buffers {
   uint32_t* U_rank;
   uint32_t* counts;   // n_cells
   uint32_t* offsets;  // n_cells + 1
-  uint32_t* bsum;     // scan block sums
+  uint32_t* bsum;     // scan block sums (coarse)
+  uint8_t* sub_s;     // n_cells: sub-grid side per coarse cell
+  uint32_t* sub_base; // n_cells + 1: first sub-cell of every coarse cell
+  uint32_t* sub_count;  // n_sub_max
+  uint32_t* sub_off;    // n_sub_max + 1
+  uint32_t* bsum2;      // scan block sums (sub-cells)
   double* phi_acc;    // phi_cap * n_rep * 3
   int64_t* d_step;
   int32_t* d_status;
@@ -434,6 +569,7 @@ struct Geometry {
   int n_rep;
   int64_t n_total;
   int64_t n_cells;
+  int64_t n_sub_max;  // bound of the number of sub-cells: n_cells + n_total / kSubTarget
   int n_tasks;
   const Rep* reps;
   const BlockTask* tasks;
@@ -443,7 +579,9 @@ struct Geometry {
 cudaError_t launch_load(const Geometry& g, const Buffers& b, const int32_t* pos_in, const float* head_in,
                         int heading_kind, cudaStream_t st);
 cudaError_t launch_count(const Geometry& g, const Buffers& b, cudaStream_t st);
-cudaError_t launch_scan(const Geometry& g, const Buffers& b, cudaStream_t st);
+// coarse counts -> offsets, sub-grid sides and sub-cell bases; sub-cell
+// histogram of U (ranks); sub-cell scan
+cudaError_t launch_build(const Geometry& g, const Buffers& b, cudaStream_t st);
 cudaError_t launch_scatter(const Geometry& g, const Buffers& b, const StepParams& P, int advance_step,
                            cudaStream_t st);
 cudaError_t launch_export_state(const Geometry& g, const Buffers& b, int rep, int64_t p0, int32_t n,

@@ -67,8 +67,7 @@ __device__ __forceinline__ void topk_insert(TopK<KC>& T, uint64_t D, int32_t idj
 template <int DIM, int KC>
 __device__ __forceinline__ void knn_search(const Rep& R, int64_t self, const int32_t* pi,
                                            const typename Vec<DIM>::P* __restrict__ pos,
-                                           const int32_t* __restrict__ ids, const uint32_t* __restrict__ off,
-                                           TopK<KC>& T) {
+                                           const int32_t* __restrict__ ids, const GridView& G, TopK<KC>& T) {
   auto run = [&](uint32_t qb, uint32_t qe) {
     for (uint32_t q = qb; q < qe; ++q) {
       if ((int64_t)q == self) continue;
@@ -89,15 +88,17 @@ __device__ __forceinline__ void knn_search(const Rep& R, int64_t self, const int
   // every unscanned particle is at squared distance >= B2: stop once the
   // k-th best is strictly closer (an equal distance could still win on id)
   auto stop = [&](uint64_t B2) { return T.d[KC - 1] < B2; };
-  ring_walk<DIM>(R, pi, off, run, stop);
+  // candidates beyond the k-th best (ties included) cannot enter
+  auto radius2 = [&]() { return T.d[KC - 1]; };
+  grid_walk<DIM>(R, pi, G, run, radius2, stop);
 }
 
 template <int DIM, int KC>
 __global__ void __launch_bounds__(kBlock) knn_step_kernel(
     const Rep* __restrict__ reps, const BlockTask* __restrict__ tasks,
     const typename Vec<DIM>::P* __restrict__ S_pos, const typename Vec<DIM>::F* __restrict__ S_dir,
-    const int32_t* __restrict__ S_id, const uint32_t* __restrict__ off, typename Vec<DIM>::P* __restrict__ U_pos,
-    typename Vec<DIM>::F* __restrict__ U_dir, int32_t* __restrict__ U_id, uint32_t* __restrict__ U_rank,
+    const int32_t* __restrict__ S_id, GridView G, typename Vec<DIM>::P* __restrict__ U_pos,
+    typename Vec<DIM>::F* __restrict__ U_dir, int32_t* __restrict__ U_id,
     uint32_t* __restrict__ counts, double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P) {
   using PV = typename Vec<DIM>::P;
   using FV = typename Vec<DIM>::F;
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(kBlock) knn_step_kernel(
     const int32_t id = S_id[s];
     TopK<KC> T;
     topk_init<KC>(T, P.k);
-    knn_search<DIM, KC>(R, s, pi, S_pos, S_id, off, T);
+    knn_search<DIM, KC>(R, s, pi, S_pos, S_id, G, T);
     HeadSum<DIM> H;
     H.init();
     if (P.include_self) H.add(ni, P.sum_mode);
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(kBlock) knn_step_kernel(
     U_pos[s] = make_p(pout, (PV*)nullptr);
     U_dir[s] = make_f(nnew, (FV*)nullptr);
     U_id[s] = id;
-    U_rank[s] = atomicAdd(counts + linear_cell<DIM>(R, pout), 1u);
+    atomicAdd(counts + linear_cell<DIM>(R, pout), 1u);
   }
   block_phi_accumulate<DIM>(nnew, phi_acc + ((size_t)(step % P.phi_cap) * (size_t)P.n_rep + (size_t)t.rep) * 3);
 }
@@ -141,9 +142,8 @@ __global__ void __launch_bounds__(kBlock) knn_step_kernel(
 template <int DIM, int KC>
 __global__ void __launch_bounds__(kBlock) knn_export_kernel(const Rep* __restrict__ reps, int rep,
                                                             const typename Vec<DIM>::P* __restrict__ S_pos,
-                                                            const int32_t* __restrict__ S_id,
-                                                            const uint32_t* __restrict__ off, int k,
-                                                            int32_t* __restrict__ out) {
+                                                            const int32_t* __restrict__ S_id, GridView G,
+                                                            int k, int32_t* __restrict__ out) {
   const Rep R = reps[rep];
   const int li = blockIdx.x * kBlock + (int)threadIdx.x;
   if (li >= R.n) return;
@@ -153,10 +153,19 @@ __global__ void __launch_bounds__(kBlock) knn_export_kernel(const Rep* __restric
   const int32_t id = S_id[s];
   TopK<KC> T;
   topk_init<KC>(T, k);
-  knn_search<DIM, KC>(R, s, pi, S_pos, S_id, off, T);
+  knn_search<DIM, KC>(R, s, pi, S_pos, S_id, G, T);
 #pragma unroll
   for (int j = 0; j < KC; ++j)
     if (j >= KC - k) out[(int64_t)id * k + (j - (KC - k))] = T.id[j];
+}
+
+GridView grid_view(const Buffers& b) {
+  GridView G;
+  G.off = b.offsets;
+  G.sub_s = b.sub_s;
+  G.sub_base = b.sub_base;
+  G.sub_off = b.sub_off;
+  return G;
 }
 
 template <int DIM, int KC>
@@ -164,8 +173,8 @@ cudaError_t step_dispatch(const Geometry& g, const Buffers& b, const StepParams&
   using PV = typename Vec<DIM>::P;
   using FV = typename Vec<DIM>::F;
   knn_step_kernel<DIM, KC><<<g.n_tasks, kBlock, 0, st>>>(
-      g.reps, g.tasks, (const PV*)b.S_pos, (const FV*)b.S_dir, b.S_id, b.offsets, (PV*)b.U_pos, (FV*)b.U_dir,
-      b.U_id, b.U_rank, b.counts, b.phi_acc, b.d_step, P);
+      g.reps, g.tasks, (const PV*)b.S_pos, (const FV*)b.S_dir, b.S_id, grid_view(b), (PV*)b.U_pos,
+      (FV*)b.U_dir, b.U_id, b.counts, b.phi_acc, b.d_step, P);
   return cudaGetLastError();
 }
 
@@ -175,7 +184,7 @@ cudaError_t export_dispatch(const Geometry& g, const Buffers& b, int k, int rep,
   using PV = typename Vec<DIM>::P;
   const int nb = (n + kBlock - 1) / kBlock;
   if (nb == 0) return cudaSuccess;
-  knn_export_kernel<DIM, KC><<<nb, kBlock, 0, st>>>(g.reps, rep, (const PV*)b.S_pos, b.S_id, b.offsets, k, out);
+  knn_export_kernel<DIM, KC><<<nb, kBlock, 0, st>>>(g.reps, rep, (const PV*)b.S_pos, b.S_id, grid_view(b), k, out);
   return cudaGetLastError();
 }
 

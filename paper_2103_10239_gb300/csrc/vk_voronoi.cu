@@ -17,7 +17,8 @@
 //     largest vertex distance (the security radius), using a rigorous FP32
 //     upper bound of the vertex distances;
 //   * neighbors are the sites of edges with positive length (an edge between
-//     two coincident vertices, i.e. four cocircular points, is dropped).
+//     two coincident vertices, i.e. four cocircular points, is dropped);
+//   * coincident particles form one site (see Poly).
 // Exact predicates need |relative coordinates| < 1.5 * 2^30, hence L_q <= 2^30.
 #include <algorithm>
 #include <climits>
@@ -77,13 +78,22 @@ __device__ __forceinline__ float vertex_r2_upper(int32_t ax, int32_t ay, int32_t
   return isfinite(r2) ? r2 : 3.0e38f;
 }
 
+// Coincident particles form one Voronoi site: they are each other's
+// neighbors and share the site's neighbors.  A candidate at exactly the
+// position of an edge site (or of the particle itself) clips nothing; it is
+// kept in the twin list and joins the neighbors if that edge survives.
 template <int CAP>
 struct Poly {
+  static constexpr int TW = CAP / 4;
   int32_t qx[CAP], qy[CAP];  // relative coordinates of the edge sites
   int32_t id[CAP];           // replica-local id of the site
   int32_t slot[CAP];         // sorted slot of the site (-1: an image of the particle itself)
   float vr2[CAP];            // vertex a (between edges a and a+1): upper bound of |V|^2
+  int32_t tw_slot[TW];       // coincident twins: their sorted slot ...
+  int32_t tw_id[TW];         // ... their id ...
+  int32_t tw_of[TW];         // ... and the slot of the site they sit on (-2: the particle itself)
   int m;
+  int nt;
   float max_r2;
 };
 
@@ -99,6 +109,7 @@ __device__ __forceinline__ void poly_init(Poly<CAP>& P, int32_t self_id, uint32_
   const int32_t X = (int32_t)Lx, Y = (int32_t)Ly;
   const int32_t sx[4] = {X, 0, -X, 0}, sy[4] = {0, Y, 0, -Y};
   P.m = 4;
+  P.nt = 0;
   for (int a = 0; a < 4; ++a) {
     P.qx[a] = sx[a];
     P.qy[a] = sy[a];
@@ -113,16 +124,19 @@ __device__ __forceinline__ void poly_init(Poly<CAP>& P, int32_t self_id, uint32_
 // clip the cell by the bisector of site (mx, my); returns false on overflow
 template <int CAP>
 __device__ __forceinline__ bool poly_clip(Poly<CAP>& P, int32_t mx, int32_t my, int32_t mid, int32_t mslot,
-                                          float Dm, bool* bad) {
+                                          float Dm, bool* bad, bool* touch) {
   const int m = P.m;
   // the vertices strictly beyond the bisector form one cyclic run [s, s+c)
   int c = 0, s = -1;
   bool first_cut = false, prev_cut = false;
+  *touch = false;
   for (int a = 0; a < m; ++a) {
     bool cut = false;
     if (!(Dm > 4.0f * P.vr2[a])) {  // a vertex closer than |m|/2 cannot be cut
       const int b = (a + 1 == m) ? 0 : a + 1;
-      cut = vertex_cut_sign(P.qx[a], P.qy[a], P.qx[b], P.qy[b], mx, my) > 0;
+      const int sg = vertex_cut_sign(P.qx[a], P.qy[a], P.qx[b], P.qy[b], mx, my);
+      cut = sg > 0;
+      *touch = *touch || sg == 0;
     }
     if (a == 0) first_cut = cut;
     if (cut) {
@@ -137,7 +151,8 @@ __device__ __forceinline__ bool poly_clip(Poly<CAP>& P, int32_t mx, int32_t my, 
     }
     prev_cut = cut;
   }
-  if (c == 0) return true;
+  if (c == 0) return true;  // *touch: some vertex lies exactly on the bisector
+  *touch = false;
   if (first_cut) {
     if (!prev_cut) {
       if (s >= 0) {
@@ -197,25 +212,48 @@ __device__ __forceinline__ bool poly_clip(Poly<CAP>& P, int32_t mx, int32_t my, 
 }
 
 // Voronoi cell of the particle at slot `self`.  Status codes are latched on
-// capacity overflow (kStCapacity), coincident points (kStDegenerate) and
-// internal inconsistencies (kStRange).
-// Returns false (and leaves the cell unusable) if the polygon outgrew CAP.
+// internal inconsistencies (kStRange); capacity overflow is returned.
+// Returns false (and leaves the cell unusable) if the polygon or the twin list
+// outgrew its capacity.
 template <int CAP>
 __device__ bool voronoi_cell(const Rep& R, int64_t self, const int32_t* pi, int32_t self_id,
                              const int2* __restrict__ pos, const int32_t* __restrict__ ids,
-                             const uint32_t* __restrict__ off, Poly<CAP>& P, int32_t* status) {
-  bool bad = false, overflow = false, degenerate = false;
+                             const GridView& G, Poly<CAP>& P, int32_t* status) {
+  bool bad = false, overflow = false;
   poly_init(P, self_id, R.L[0], R.L[1], &bad);
   const int64_t Lx = R.L[0], Ly = R.L[1];
+  auto add_twin = [&](int32_t slot, int32_t jid, int32_t of) {
+    if (P.nt == Poly<CAP>::TW) {
+      overflow = true;
+      return;
+    }
+    P.tw_slot[P.nt] = slot;
+    P.tw_id[P.nt] = jid;
+    P.tw_of[P.nt] = of;
+    ++P.nt;
+  };
   auto visit = [&](int32_t qx, int32_t qy, int32_t jid, int32_t slot) {
+    if (overflow) return;
     const uint64_t D = (uint64_t)((int64_t)qx * qx) + (uint64_t)((int64_t)qy * qy);
     if (D == 0) {
-      degenerate = true;
+      add_twin(slot, jid, -2);  // coincident with the particle itself
       return;
     }
     const float Df = (float)D * (1.0f - 2.384185791015625e-07f);  // rounded down
-    if (overflow || Df > 4.0f * P.max_r2) return;
-    if (!poly_clip(P, qx, qy, jid, slot, Df, &bad)) overflow = true;
+    if (Df > 4.0f * P.max_r2) return;
+    bool touch = false;
+    if (!poly_clip(P, qx, qy, jid, slot, Df, &bad, &touch)) {
+      overflow = true;
+      return;
+    }
+    if (touch) {
+      // no vertex cut but some vertex on the bisector: a twin of an edge site?
+      for (int a = 0; a < P.m; ++a)
+        if (P.qx[a] == qx && P.qy[a] == qy && P.slot[a] >= 0) {
+          add_twin(slot, jid, P.slot[a]);
+          break;
+        }
+    }
   };
   auto run = [&](uint32_t qb, uint32_t qe) {
     for (uint32_t q = qb; q < qe; ++q) {
@@ -230,7 +268,12 @@ __device__ bool voronoi_cell(const Rep& R, int64_t self, const int32_t* pi, int3
     const float b2 = (float)B2 * (1.0f - 2.384185791015625e-07f);
     return b2 > 4.0f * P.max_r2;
   };
-  const bool all = ring_walk<2>(R, pi, off, run, stop);
+  // sites farther than twice the largest vertex distance cannot clip
+  auto radius2 = [&]() -> uint64_t {
+    const float r = 4.0f * P.max_r2 * 1.0000005f;
+    return r >= 1.8e19f ? ~0ull : (uint64_t)r + 1ull;
+  };
+  const bool all = grid_walk<2>(R, pi, G, run, radius2, stop);
   if (all) {
     // tiny boxes: other periodic images than the minimum one can still shape
     // the cell when the security radius exceeds half the box
@@ -250,37 +293,41 @@ __device__ bool voronoi_cell(const Rep& R, int64_t self, const int32_t* pi, int3
       }
     }
   }
-  if (degenerate) set_status(status, kStDegenerate);
   if (bad) set_status(status, kStRange);
   return !overflow;
 }
 
-// neighbors of positive edge length, excluding the particle's own images,
+// neighbors: sites of edges with positive length (never the particle's own
+// images) plus the coincident twins of the particle and of those sites;
 // sorted by id and de-duplicated; returns the count
 template <int CAP>
 __device__ __forceinline__ int voronoi_neighbors(const Poly<CAP>& P, int32_t self_id, int32_t* nid,
                                                  int32_t* nslot) {
   int cnt = 0;
   const int m = P.m;
-  for (int a = 0; a < m; ++a) {
-    if (P.slot[a] < 0) continue;  // an image of the particle itself
-    const int pa = (a == 0) ? m - 1 : a - 1, na = (a + 1 == m) ? 0 : a + 1;
-    if (vertex_cut_sign(P.qx[pa], P.qy[pa], P.qx[a], P.qy[a], P.qx[na], P.qy[na]) == 0) continue;
-    // insertion by id
-    const int32_t v = P.id[a];
+  auto push = [&](int32_t v, int32_t sl) {
+    for (int q = 0; q < cnt; ++q)
+      if (nid[q] == v) return;
     int j = cnt;
-    bool dup = false;
-    for (int q = 0; q < cnt; ++q) dup = dup || (nid[q] == v);
-    if (dup) continue;
     while (j > 0 && nid[j - 1] > v) {
       nid[j] = nid[j - 1];
       nslot[j] = nslot[j - 1];
       --j;
     }
     nid[j] = v;
-    nslot[j] = P.slot[a];
+    nslot[j] = sl;
     ++cnt;
+  };
+  for (int a = 0; a < m; ++a) {
+    if (P.slot[a] < 0) continue;  // an image of the particle itself
+    const int pa = (a == 0) ? m - 1 : a - 1, na = (a + 1 == m) ? 0 : a + 1;
+    if (vertex_cut_sign(P.qx[pa], P.qy[pa], P.qx[a], P.qy[a], P.qx[na], P.qy[na]) == 0) continue;
+    push(P.id[a], P.slot[a]);
+    for (int t = 0; t < P.nt; ++t)
+      if (P.tw_of[t] == P.slot[a]) push(P.tw_id[t], P.tw_slot[t]);
   }
+  for (int t = 0; t < P.nt; ++t)
+    if (P.tw_of[t] == -2 && P.tw_id[t] != self_id) push(P.tw_id[t], P.tw_slot[t]);
   return cnt;
 }
 
@@ -290,9 +337,9 @@ __device__ __forceinline__ void voronoi_update(const Rep& R, const StepParams& P
                                                const Poly<CAP>& P, const int32_t* pi, const float* ni,
                                                int32_t id, const float2* __restrict__ S_dir,
                                                int2* __restrict__ U_pos, float2* __restrict__ U_dir,
-                                               int32_t* __restrict__ U_id, uint32_t* __restrict__ U_rank,
-                                               uint32_t* __restrict__ counts, float* nnew) {
-  int32_t nid[CAP], nslot[CAP];
+                                               int32_t* __restrict__ U_id, uint32_t* __restrict__ counts,
+                                               float* nnew) {
+  int32_t nid[CAP + Poly<CAP>::TW], nslot[CAP + Poly<CAP>::TW];
   const int cnt = voronoi_neighbors(P, id, nid, nslot);
   HeadSum<2> H;
   H.init();
@@ -307,15 +354,15 @@ __device__ __forceinline__ void voronoi_update(const Rep& R, const StepParams& P
   U_pos[s] = make_int2(pout[0], pout[1]);
   U_dir[s] = make_float2(nnew[0], nnew[1]);
   U_id[s] = id;
-  U_rank[s] = atomicAdd(counts + linear_cell<2>(R, pout), 1u);
+  atomicAdd(counts + linear_cell<2>(R, pout), 1u);
 }
 
 // Main kernel: cells of up to kFastCap edges.  Particles whose cell outgrows
 // it are appended to the overflow list and finished by the overflow kernel.
 __global__ void __launch_bounds__(kBlock) voronoi_step_kernel(
     const Rep* __restrict__ reps, const BlockTask* __restrict__ tasks, const int2* __restrict__ S_pos,
-    const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, const uint32_t* __restrict__ off,
-    int2* __restrict__ U_pos, float2* __restrict__ U_dir, int32_t* __restrict__ U_id, uint32_t* __restrict__ U_rank,
+    const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G,
+    int2* __restrict__ U_pos, float2* __restrict__ U_dir, int32_t* __restrict__ U_id,
     uint32_t* __restrict__ counts, double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams Pm,
     int2* __restrict__ ovf_list, int32_t* __restrict__ ovf_count, int32_t* status) {
   const BlockTask t = tasks[blockIdx.x];
@@ -331,8 +378,8 @@ __global__ void __launch_bounds__(kBlock) voronoi_step_kernel(
     const float ni[3] = {nv.x, nv.y, 0.f};
     const int32_t id = S_id[s];
     Poly<kFastCap> P;
-    if (voronoi_cell(R, s, pi, id, S_pos, S_id, off, P, status)) {
-      voronoi_update(R, Pm, step, s, P, pi, ni, id, S_dir, U_pos, U_dir, U_id, U_rank, counts, nnew);
+    if (voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status)) {
+      voronoi_update(R, Pm, step, s, P, pi, ni, id, S_dir, U_pos, U_dir, U_id, counts, nnew);
     } else {
       const int q = atomicAdd(ovf_count, 1);
       ovf_list[q] = make_int2((int)s, t.rep);
@@ -345,8 +392,8 @@ __global__ void __launch_bounds__(kBlock) voronoi_step_kernel(
 // bordering a void can have dozens of Voronoi neighbors).
 __global__ void __launch_bounds__(64) voronoi_overflow_kernel(
     const Rep* __restrict__ reps, const int2* __restrict__ S_pos, const float2* __restrict__ S_dir,
-    const int32_t* __restrict__ S_id, const uint32_t* __restrict__ off, int2* __restrict__ U_pos,
-    float2* __restrict__ U_dir, int32_t* __restrict__ U_id, uint32_t* __restrict__ U_rank,
+    const int32_t* __restrict__ S_id, GridView G, int2* __restrict__ U_pos,
+    float2* __restrict__ U_dir, int32_t* __restrict__ U_id,
     uint32_t* __restrict__ counts, double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams Pm,
     const int2* __restrict__ ovf_list, const int32_t* __restrict__ ovf_count, int32_t* status) {
   const int total = *ovf_count;
@@ -361,12 +408,12 @@ __global__ void __launch_bounds__(64) voronoi_overflow_kernel(
     const float ni[3] = {nv.x, nv.y, 0.f};
     const int32_t id = S_id[s];
     Poly<kSlowCap> P;
-    if (!voronoi_cell(R, s, pi, id, S_pos, S_id, off, P, status)) {
+    if (!voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status)) {
       set_status(status, kStCapacity);
       continue;
     }
     float nnew[3] = {0.f, 0.f, 0.f};
-    voronoi_update(R, Pm, step, s, P, pi, ni, id, S_dir, U_pos, U_dir, U_id, U_rank, counts, nnew);
+    voronoi_update(R, Pm, step, s, P, pi, ni, id, S_dir, U_pos, U_dir, U_id, counts, nnew);
     double* acc = phi_acc + ((size_t)(step % Pm.phi_cap) * (size_t)Pm.n_rep + (size_t)e.y) * 3;
     atomicAdd(acc + 0, (double)nnew[0]);
     atomicAdd(acc + 1, (double)nnew[1]);
@@ -378,7 +425,7 @@ __global__ void __launch_bounds__(64) voronoi_overflow_kernel(
 __global__ void __launch_bounds__(64) voronoi_export_kernel(const Rep* __restrict__ reps, int rep,
                                                             const int2* __restrict__ S_pos,
                                                             const int32_t* __restrict__ S_id,
-                                                            const uint32_t* __restrict__ off, int pass,
+                                                            GridView G, int pass,
                                                             int32_t* __restrict__ deg,
                                                             const int64_t* __restrict__ out_off,
                                                             int32_t* __restrict__ out_ids, int32_t* status) {
@@ -389,12 +436,12 @@ __global__ void __launch_bounds__(64) voronoi_export_kernel(const Rep* __restric
     const int32_t pi[3] = {p.x, p.y, 0};
     const int32_t id = S_id[s];
     Poly<kSlowCap> P;
-    if (!voronoi_cell(R, s, pi, id, S_pos, S_id, off, P, status)) {
+    if (!voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status)) {
       set_status(status, kStCapacity);
       if (pass == 0) deg[id] = 0;
       continue;
     }
-    int32_t nid[kSlowCap], nslot[kSlowCap];
+    int32_t nid[kSlowCap + Poly<kSlowCap>::TW], nslot[kSlowCap + Poly<kSlowCap>::TW];
     const int cnt = voronoi_neighbors(P, id, nid, nslot);
     if (pass == 0) {
       deg[id] = cnt;
@@ -407,13 +454,23 @@ __global__ void __launch_bounds__(64) voronoi_export_kernel(const Rep* __restric
 
 }  // namespace
 
+static GridView grid_view(const Buffers& b) {
+  GridView G;
+  G.off = b.offsets;
+  G.sub_s = b.sub_s;
+  G.sub_base = b.sub_base;
+  G.sub_off = b.sub_off;
+  return G;
+}
+
 cudaError_t launch_voronoi_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st) {
+  const GridView G = grid_view(b);
   voronoi_step_kernel<<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int2*)b.S_pos, (const float2*)b.S_dir,
-                                                    b.S_id, b.offsets, (int2*)b.U_pos, (float2*)b.U_dir, b.U_id,
-                                                    b.U_rank, b.counts, b.phi_acc, b.d_step, P, b.ovf_list,
+                                                    b.S_id, G, (int2*)b.U_pos, (float2*)b.U_dir, b.U_id,
+                                                    b.counts, b.phi_acc, b.d_step, P, b.ovf_list,
                                                     b.ovf_count, b.d_status);
   voronoi_overflow_kernel<<<152, 64, 0, st>>>(g.reps, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id,
-                                              b.offsets, (int2*)b.U_pos, (float2*)b.U_dir, b.U_id, b.U_rank,
+                                              G, (int2*)b.U_pos, (float2*)b.U_dir, b.U_id,
                                               b.counts, b.phi_acc, b.d_step, P, b.ovf_list, b.ovf_count,
                                               b.d_status);
   return cudaGetLastError();
@@ -423,7 +480,7 @@ cudaError_t launch_voronoi_export(const Geometry& g, const Buffers& b, int rep, 
                                   const int64_t* out_off, int32_t* out_ids, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const int nb = std::min((n + 63) / 64, 152 * 8);
-  voronoi_export_kernel<<<nb, 64, 0, st>>>(g.reps, rep, (const int2*)b.S_pos, b.S_id, b.offsets, pass, deg,
+  voronoi_export_kernel<<<nb, 64, 0, st>>>(g.reps, rep, (const int2*)b.S_pos, b.S_id, grid_view(b), pass, deg,
                                            out_off, out_ids, b.d_status);
   return cudaGetLastError();
 }

@@ -73,6 +73,18 @@ def test_translation_invariance_on_gpu():
             assert np.array_equal(_knn_lists(sim, 7), base)
 
 
+@pytest.mark.parametrize("occ", [0.5, 2.0, 8.0, 40.0])
+def test_clustered_lists_for_any_coarse_occupancy(occ):
+    """Dense coarse cells are split into sub-grids; the lists must not
+    depend on how the two-level grid is cut."""
+    w = W.clustered_large(n=1 << 15)
+    want = oracle.knn(w.pos_q, w.box_q, 7)
+    with vk.from_workload(w, cell_occupancy=occ) as sim:
+        assert np.array_equal(_knn_lists(sim, 7), want)
+        sim.step(1)
+        check_step(sim, w, "knn")
+
+
 def test_clustered_density_contrast():
     w = W.clustered_large(n=1 << 15)
     with vk.from_workload(w) as sim:

@@ -71,6 +71,22 @@ def test_reciprocity_and_euler_after_steps():
     assert ids.size == 6 * w.n
 
 
+@pytest.mark.parametrize("occ", [1.0, 2.0, 16.0])
+def test_clustered_voronoi_split_cells(occ):
+    """Voronoi cells in dense clusters (split coarse cells) and sparse
+    background, F=16 so that L_q stays below 2^30."""
+    base = W.clustered_large(n=1 << 14)
+    rng = np.random.default_rng(7)
+    pos = (base.pos_q.astype(np.int64) >> 4).astype(np.int32)  # F=20 -> F=16
+    pos = np.unique(pos, axis=0)[rng.permutation(np.unique(pos, axis=0).shape[0])]
+    box = (base.box_q[0] >> 4, base.box_q[1] >> 4)
+    w = W.Workload(name="clustered_vor", dim=2, pos_q=pos, dir=W.random_dirs(pos.shape[0]), theta=None,
+                   box_q=box, frac_bits=16, rule="voronoi", k=0, v0=0.3, eta=0.2)
+    with vk.from_workload(w, cell_occupancy=occ) as sim:
+        _same(sim, w.pos_q, w.box_q)
+        check_step(sim, w, "voronoi")
+
+
 def test_density_two_large_sampled():
     w = W.precision_study("voronoi", n=1 << 18)
     with vk.from_workload(w) as sim:
@@ -78,14 +94,20 @@ def test_density_two_large_sampled():
         _same(sim, pos, w.box_q)
 
 
-def test_coincident_points_are_reported():
-    w = W.uniform_system(200, 14.0, 16, 2, input_seed=2, rule="voronoi", k=0)
+def test_coincident_particles_share_a_site():
+    """Reading: coincident particles form one Voronoi site, are each other's
+    neighbors and share the site's neighbors (the oracle applies the same
+    rule to an exact triangulation of the distinct sites)."""
+    w = W.uniform_system(200, 14.0, 16, 2, input_seed=2, rule="voronoi", k=0, v0=0.3, eta=0.3)
     pos = w.pos_q.copy()
     pos[7] = pos[3]
-    with vk.Sim.create(pos, w.dir, w.box_q, 16, rule="voronoi") as sim:
-        with pytest.raises(vk.VKError) as e:
-            sim.neighbors()
-        assert e.value.status == vk.VK_ERR_DEGENERATE
+    pos[11] = pos[3]
+    pos[40] = pos[41]
+    w.pos_q = pos
+    with vk.from_workload(w) as sim:
+        off, ids = _same(sim, pos, w.box_q)
+        assert 7 in ids[off[3]:off[4]] and 3 in ids[off[11]:off[12]]
+        check_step(sim, w, "voronoi")
 
 
 def test_huge_cell_takes_the_overflow_path():
@@ -96,8 +118,10 @@ def test_huge_cell_takes_the_overflow_path():
     L = 1 << 16
     F = 8
     ring_r = 20000.0
-    ang = np.sort(rng.uniform(0, 2 * np.pi, 60))
-    rad = ring_r * (1 + rng.uniform(-0.01, 0.01, 60))
+    # evenly spaced: a ring member keeps its edge while its radial offset
+    # stays below 1/cos(3 deg) - 1 = 0.14 % of the radius
+    ang = np.arange(60) * (2 * np.pi / 60) + rng.uniform(-1e-4, 1e-4, 60)
+    rad = ring_r * (1 + rng.uniform(-3e-4, 3e-4, 60))
     c = L / 2
     ring = np.stack([c + rad * np.cos(ang), c + rad * np.sin(ang)], 1)
     outer = rng.uniform(0, L, size=(600, 2))

@@ -124,10 +124,24 @@ def test_against_qhull_on_generic_input(orc):
     del center
 
 
-def test_coincident_points_are_rejected(orc):
-    pos = np.array([[10, 10], [500, 400], [10, 10], [900, 30]], dtype=np.int32)
-    with pytest.raises(orc.OracleError):
-        orc.voronoi(pos, (1000, 1000))
+def test_coincident_points_share_a_site(orc):
+    """Coincident particles (reading: one Voronoi site) are each other's
+    neighbors and share the site's neighbors; checked against the bisector
+    brute force, which handles coincident sites without any triangulation."""
+    pos = np.array([[10, 10], [500, 400], [10, 10], [900, 30], [700, 800], [10, 10], [500, 400]],
+                   dtype=np.int32)
+    off, ids = orc.voronoi(pos, (1000, 1000))
+    rows = _rows(off, ids)
+    assert rows == brute.voronoi_brute(pos, (1000, 1000))
+    assert {2, 5} <= set(rows[0]) and {0, 2} <= set(rows[5]) and 6 in rows[1]
+    rng = np.random.default_rng(3)
+    for _ in range(30):
+        n = int(rng.integers(2, 25))
+        L = int(rng.integers(20, 3000))
+        base = rng.integers(0, L, size=(max(1, n // 2), 2))
+        pos = base[rng.integers(0, base.shape[0], size=n)].astype(np.int32)
+        off, ids = orc.voronoi(pos, (L, L))
+        assert _rows(off, ids) == brute.voronoi_brute(pos, (L, L))
 
 
 def test_predicates(orc):

@@ -174,6 +174,13 @@ vk_status vk_get_profile(vk_sim* sim, double* ms, int64_t* launches, int32_t max
                          int32_t* n_phases);
 const char* vk_phase_name(int32_t phase);
 
+/* Search counters of the neighbor search, summed over
+ * the particle updates run while tracing was on: mean candidates examined per
+ * particle, mean contiguous slot runs visited per particle, and the largest
+ * candidate count of one particle. */
+vk_status vk_get_search_stats(vk_sim* sim, double* mean_candidates, double* mean_runs,
+                              int64_t* max_candidates);
+
 /* Sizes chosen at init: total particles, replicas, cells of the search grid. */
 typedef struct {
   int64_t n_total;

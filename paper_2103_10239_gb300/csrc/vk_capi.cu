@@ -36,6 +36,7 @@ struct vk_sim {
   int64_t cells_cap = 0;
   std::vector<Rep> reps_h;
   std::vector<BlockTask> tasks_h;
+  std::vector<uint32_t> bounds_h;  // cell boundary tables of all replicas
   std::vector<int64_t> n_r;
   std::vector<vk_box> boxes;
   std::vector<float> eta_r;
@@ -58,6 +59,7 @@ struct vk_sim {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[kPhases];
   double prof_ms[kPhases] = {0, 0, 0, 0, 0};
   int64_t prof_launches[kPhases] = {0, 0, 0, 0, 0};
+  unsigned long long* d_stats = nullptr;  // search counters, collected while tracing
   std::string err;
 };
 
@@ -97,6 +99,7 @@ StepParams step_params(const vk_sim* s) {
   P.seed_hi = (uint32_t)(s->prm.seed >> 32);
   P.n_rep = s->n_rep;
   P.phi_cap = s->phi_cap;
+  P.stats = s->prof ? s->d_stats : nullptr;
   return P;
 }
 
@@ -106,9 +109,11 @@ float default_occupancy(const vk_params& p, int dim) {
   return dim == 2 ? 2.0f : 3.0f;
 }
 
-// per-replica search grid for a target occupancy; fills nc and c0
+// per-replica search grid for a target occupancy; fills nc, c0 and the cell
+// boundary tables (bnd[b] = ceil(b * L / nc), the first coordinate of cell b)
 void plan_cells(vk_sim* s, float occ) {
   int64_t c0 = 0;
+  s->bounds_h.clear();
   for (int r = 0; r < s->n_rep; ++r) {
     Rep& R = s->reps_h[r];
     double vol = 1.0;
@@ -124,6 +129,12 @@ void plan_cells(vk_sim* s, float occ) {
       ncd = std::max(1.0, std::min(ncd, std::min((double)R.L[a], 65536.0)));
       R.nc[a] = (int32_t)ncd;
       cells *= R.nc[a];
+    }
+    for (int a = 0; a < 3; ++a) {
+      R.bnd[a] = (int32_t)s->bounds_h.size();
+      R.inv_w[a] = (float)R.nc[a] / (float)R.L[a];
+      for (int64_t b = 0; b <= R.nc[a]; ++b)
+        s->bounds_h.push_back((uint32_t)((b * (int64_t)R.L[a] + R.nc[a] - 1) / R.nc[a]));
     }
     R.c0 = c0;
     c0 += cells;
@@ -190,6 +201,11 @@ void refresh_geometry(vk_sim* s) {
 vk_status upload_reps(vk_sim* s) {
   VK_CUDA(s, cudaMemcpyAsync(s->reps_d, s->reps_h.data(), sizeof(Rep) * s->n_rep, cudaMemcpyHostToDevice,
                              s->stream));
+  if (s->b.bounds) cudaFree(s->b.bounds);
+  s->b.bounds = nullptr;
+  VK_CUDA(s, dalloc(&s->b.bounds, s->bounds_h.size()));
+  VK_CUDA(s, cudaMemcpyAsync(s->b.bounds, s->bounds_h.data(), sizeof(uint32_t) * s->bounds_h.size(),
+                             cudaMemcpyHostToDevice, s->stream));
   VK_CUDA(s, cudaStreamSynchronize(s->stream));
   refresh_geometry(s);
   return VK_OK;
@@ -229,7 +245,8 @@ vk_status enqueue_step(vk_sim* s) {
   cudaEvent_t e0 = nullptr;
   vk_status st = record_begin(s, 0, &e0);
   if (st) return st;
-  if (s->prm.rule == VK_RULE_KNN) VK_CUDA(s, launch_knn_step(s->g, s->b, P, s->stream));
+  if (s->prm.rule == VK_RULE_KNN && s->dim == 2) VK_CUDA(s, launch_knn2_step(s->g, s->b, P, s->stream));
+  else if (s->prm.rule == VK_RULE_KNN) VK_CUDA(s, launch_knn_step(s->g, s->b, P, s->stream));
   else VK_CUDA(s, launch_voronoi_step(s->g, s->b, P, s->stream));
   if ((st = record_end(s, 0, e0, s->prm.rule == VK_RULE_KNN ? 1 : 2))) return st;
   if ((st = record_begin(s, 1, &e0))) return st;
@@ -370,6 +387,7 @@ vk_status build_sim(int32_t n_rep, const int64_t* n_r, const int32_t* pos_q, con
       (e = dalloc(&s->b.phi_acc, 3 * (size_t)s->phi_cap * n_rep)) || (e = dalloc(&s->b.d_step, 1)) ||
       (e = dalloc(&s->b.d_status, 1)) || (e = dalloc(&s->reps_d, n_rep)) ||
       (e = dalloc(&s->b.ovf_list, params->rule == VK_RULE_VORONOI ? N : 1)) || (e = dalloc(&s->b.ovf_count, 1)) ||
+      (e = dalloc(&s->d_stats, 4)) ||
       (e = dalloc(&s->tasks_d, s->tasks_h.size())))
     return bail(cuda_fail(s, e, "cudaMalloc"));
   if (ensure_cells_capacity(s)) return bail(VK_ERR_OOM);
@@ -479,7 +497,8 @@ vk_status vk_get_neighbors(vk_sim* s, int32_t replica, int64_t* offsets, int32_t
     const int k = s->prm.k;
     int32_t* out_d = nullptr;
     VK_CUDA(s, dalloc(&out_d, (size_t)n * k));
-    cudaError_t e = launch_knn_export(s->g, s->b, k, replica, (int)n, out_d, s->stream);
+    cudaError_t e = s->dim == 2 ? launch_knn2_export(s->g, s->b, k, replica, (int)n, out_d, s->stream)
+                                : launch_knn_export(s->g, s->b, k, replica, (int)n, out_d, s->stream);
     if (e == cudaSuccess) {
       ids_h.resize((size_t)n * k);
       e = cudaMemcpyAsync(ids_h.data(), out_d, sizeof(int32_t) * n * k, cudaMemcpyDeviceToHost, s->stream);
@@ -642,7 +661,7 @@ void vk_destroy(vk_sim* s) {
   void* bufs[] = {s->b.S_pos, s->b.S_dir, s->b.S_id, s->b.U_pos, s->b.U_dir, s->b.U_id, s->b.U_rank,
                   s->b.counts, s->b.offsets, s->b.bsum, s->b.phi_acc, s->b.d_step, s->b.d_status,
                   s->b.ovf_list, s->b.ovf_count, s->reps_d, s->tasks_d, s->b.sub_s, s->b.sub_base,
-                  s->b.sub_count, s->b.sub_off, s->b.bsum2};
+                  s->b.sub_count, s->b.sub_off, s->b.bsum2, s->d_stats, s->b.bounds};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -659,8 +678,10 @@ vk_status vk_set_graph_steps(vk_sim* s, int32_t steps_per_graph) {
 vk_status vk_set_profiling(vk_sim* s, int32_t enable) {
   if (!s) return fail(s, VK_ERR_ARG, "sim is NULL");
   s->prof = enable != 0;
+  drop_graph(s);  // the captured launches carry the tracing switch
   if (s->prof) {
     cudaStreamSynchronize(s->stream);
+    VK_CUDA(s, cudaMemsetAsync(s->d_stats, 0, 4 * sizeof(unsigned long long), s->stream));
     for (int p = 0; p < kPhases; ++p) {
       for (auto& pr : s->ev[p]) {
         cudaEventDestroy(pr.first);
@@ -693,6 +714,18 @@ vk_status vk_get_profile(vk_sim* s, double* ms, int64_t* launches, int32_t max_p
     if (launches) launches[p] = s->prof_launches[p];
   }
   if (n_phases) *n_phases = kPhases;
+  return VK_OK;
+}
+
+vk_status vk_get_search_stats(vk_sim* s, double* mean_candidates, double* mean_runs, int64_t* max_candidates) {
+  if (!s) return fail(s, VK_ERR_ARG, "sim is NULL");
+  unsigned long long h[4] = {0, 0, 0, 0};
+  VK_CUDA(s, cudaMemcpyAsync(h, s->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+  VK_CUDA(s, cudaStreamSynchronize(s->stream));
+  const double n = h[3] ? (double)h[3] : 1.0;
+  if (mean_candidates) *mean_candidates = (double)h[0] / n;
+  if (mean_runs) *mean_runs = (double)h[1] / n;
+  if (max_candidates) *max_candidates = (int64_t)h[2];
   return VK_OK;
 }
 

@@ -38,6 +38,8 @@ struct Rep {
   float eta;       // noise strength
   float s;         // grid units per unit heading and step: fl32(v0*dt) * 2^F
   uint32_t replica;
+  int32_t bnd[3];  // offset of the axis' cell-boundary table in the bounds array
+  float inv_w[3];  // nc / L (estimate of the cell index; corrected exactly)
 };
 
 struct BlockTask {
@@ -54,7 +56,29 @@ struct StepParams {
   uint32_t seed_lo, seed_hi;
   int32_t n_rep;
   int32_t phi_cap;
+  unsigned long long* stats;  // tracing only: [candidates, runs, max candidates, particles]; NULL = off
 };
+
+// Tracing: add one particle's search counters to the global totals.
+__device__ __forceinline__ void record_search_stats(unsigned long long* stats, bool valid, uint32_t cand,
+                                                    uint32_t runs) {
+  if (!stats) return;
+  unsigned long long c = valid ? cand : 0, r = valid ? runs : 0, n = valid ? 1 : 0;
+  unsigned long long mx = c;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+    r += __shfl_xor_sync(0xffffffffu, r, o);
+    n += __shfl_xor_sync(0xffffffffu, n, o);
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0 && n) {
+    atomicAdd(stats + 0, c);
+    atomicAdd(stats + 1, r);
+    atomicMax(stats + 2, mx);
+    atomicAdd(stats + 3, n);
+  }
+}
 
 template <int DIM> struct Vec;
 template <> struct Vec<2> { using P = int2; using F = float2; };
@@ -136,6 +160,22 @@ __device__ __forceinline__ int32_t grid_step(float s, float h) {
     else if (e < 0.f) r = __fsub_rn(p, 0.5f);
   }
   return (int32_t)r;
+}
+
+// Cell geometry from the per-replica boundary tables: bnd[b] is the first
+// grid coordinate of cell b (b = 0..n), so no division is needed.
+__device__ __forceinline__ int cell_of_tab(uint32_t p, int n, const uint32_t* __restrict__ bnd, float inv_w) {
+  int c = min((int)((float)p * inv_w), n - 1);
+  while (c > 0 && p < __ldg(bnd + c)) --c;
+  while (c < n - 1 && p >= __ldg(bnd + c + 1)) ++c;
+  return c;
+}
+
+// first (unwrapped) coordinate of unwrapped cell b, -n <= b < 2n
+__device__ __forceinline__ int64_t cell_lo_tab(int b, int n, const uint32_t* __restrict__ bnd, int64_t L) {
+  if (b < 0) return (int64_t)__ldg(bnd + b + n) - L;
+  if (b >= n) return (int64_t)__ldg(bnd + b - n) + L;
+  return (int64_t)__ldg(bnd + b);
 }
 
 // global cell index of a position in replica R (x fastest)
@@ -492,12 +532,23 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Block-wide compensated sum of v[0..DIM) over the block; thread 0 adds the
-// result into acc[0..DIM) with FP64 atomics.  All threads must call it.
+// Block-wide compensated sum of v[0..DIM) without a block barrier at the end:
+// every warp reduces its lanes and parks the partial in shared memory; the
+// last warp of the block to arrive adds the block total into acc[0..DIM) with
+// FP64 atomics.  phi_block_begin() must be called by all threads first.
+struct PhiShared {
+  float s[kBlock / 32][3];
+  float c[kBlock / 32][3];
+  unsigned int arrived;
+};
+
+__device__ __forceinline__ void phi_block_begin(PhiShared& sh) {
+  if (threadIdx.x == 0) sh.arrived = 0;
+  __syncthreads();
+}
+
 template <int DIM>
-__device__ __forceinline__ void block_phi_accumulate(const float* v, double* acc) {
-  __shared__ float sh_s[kBlock / 32][3];
-  __shared__ float sh_c[kBlock / 32][3];
+__device__ __forceinline__ void phi_block_end(PhiShared& sh, const float* v, double* acc) {
   float s[DIM], c[DIM];
 #pragma unroll
   for (int a = 0; a < DIM; ++a) { s[a] = v[a]; c[a] = 0.f; }
@@ -516,17 +567,31 @@ __device__ __forceinline__ void block_phi_accumulate(const float* v, double* acc
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) { sh_s[wid][a] = s[a]; sh_c[wid][a] = c[a]; }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
     for (int a = 0; a < DIM; ++a) {
-      double t = 0.0;
-      for (int w2 = 0; w2 < kBlock / 32; ++w2) t += (double)sh_s[w2][a] + (double)sh_c[w2][a];
-      atomicAdd(acc + a, t);
+      ((volatile float*)sh.s[wid])[a] = s[a];
+      ((volatile float*)sh.c[wid])[a] = c[a];
+    }
+    __threadfence_block();
+    const unsigned int before = atomicAdd(&sh.arrived, 1u);
+    if (before == blockDim.x / 32 - 1) {
+      __threadfence_block();
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        double t = 0.0;
+        for (int w2 = 0; w2 < (int)(blockDim.x / 32); ++w2)
+          t += (double)((volatile float*)sh.s[w2])[a] + (double)((volatile float*)sh.c[w2])[a];
+        atomicAdd(acc + a, t);
+      }
     }
   }
+}
+
+// (kept for kernels whose warps finish together)
+template <int DIM>
+__device__ __forceinline__ void block_phi_accumulate(const float* v, double* acc) {
+  __shared__ PhiShared sh;
+  phi_block_begin(sh);
+  phi_block_end<DIM>(sh, v, acc);
 }
 
 __device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
@@ -556,6 +621,7 @@ struct Buffers {
   uint32_t* sub_count;  // n_sub_max
   uint32_t* sub_off;    // n_sub_max + 1
   uint32_t* bsum2;      // scan block sums (sub-cells)
+  uint32_t* bounds;     // per replica and axis: first coordinate of every cell (nc + 1 entries)
   double* phi_acc;    // phi_cap * n_rep * 3
   int64_t* d_step;
   int32_t* d_status;
@@ -593,6 +659,11 @@ cudaError_t launch_import_state(const Geometry& g, const Buffers& b, int rep, in
 cudaError_t launch_knn_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st);
 cudaError_t launch_knn_export(const Geometry& g, const Buffers& b, int k, int rep, int n, int32_t* out,
                               cudaStream_t st);
+
+// vk_knn2d.cu (the 2D kNN hot path)
+cudaError_t launch_knn2_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st);
+cudaError_t launch_knn2_export(const Geometry& g, const Buffers& b, int k, int rep, int n, int32_t* out,
+                               cudaStream_t st);
 
 // vk_voronoi.cu
 cudaError_t launch_voronoi_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st);

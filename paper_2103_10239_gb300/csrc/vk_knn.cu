@@ -67,8 +67,13 @@ __device__ __forceinline__ void topk_insert(TopK<KC>& T, uint64_t D, int32_t idj
 template <int DIM, int KC>
 __device__ __forceinline__ void knn_search(const Rep& R, int64_t self, const int32_t* pi,
                                            const typename Vec<DIM>::P* __restrict__ pos,
-                                           const int32_t* __restrict__ ids, const GridView& G, TopK<KC>& T) {
+                                           const int32_t* __restrict__ ids, const GridView& G, TopK<KC>& T,
+                                           uint32_t* n_cand = nullptr, uint32_t* n_runs = nullptr) {
   auto run = [&](uint32_t qb, uint32_t qe) {
+    if (n_cand) {
+      *n_cand += qe - qb;
+      *n_runs += 1;
+    }
     for (uint32_t q = qb; q < qe; ++q) {
       if ((int64_t)q == self) continue;
       int32_t pj[3];
@@ -107,6 +112,7 @@ __global__ void __launch_bounds__(kBlock) knn_step_kernel(
   const int li = t.first + (int)threadIdx.x;
   const int64_t step = *d_step;
   float nnew[3] = {0.f, 0.f, 0.f};
+  uint32_t n_cand = 0, n_runs = 0;
   if (li < R.n) {
     const int64_t s = R.p0 + li;
     int32_t pi[3] = {0, 0, 0};
@@ -116,7 +122,8 @@ __global__ void __launch_bounds__(kBlock) knn_step_kernel(
     const int32_t id = S_id[s];
     TopK<KC> T;
     topk_init<KC>(T, P.k);
-    knn_search<DIM, KC>(R, s, pi, S_pos, S_id, G, T);
+    if (P.stats) knn_search<DIM, KC>(R, s, pi, S_pos, S_id, G, T, &n_cand, &n_runs);
+    else knn_search<DIM, KC>(R, s, pi, S_pos, S_id, G, T);
     HeadSum<DIM> H;
     H.init();
     if (P.include_self) H.add(ni, P.sum_mode);
@@ -135,6 +142,7 @@ __global__ void __launch_bounds__(kBlock) knn_step_kernel(
     U_id[s] = id;
     atomicAdd(counts + linear_cell<DIM>(R, pout), 1u);
   }
+  record_search_stats(P.stats, li < R.n, n_cand, n_runs);
   block_phi_accumulate<DIM>(nnew, phi_acc + ((size_t)(step % P.phi_cap) * (size_t)P.n_rep + (size_t)t.rep) * 3);
 }
 

@@ -218,7 +218,8 @@ __device__ __forceinline__ bool poly_clip(Poly<CAP>& P, int32_t mx, int32_t my, 
 template <int CAP>
 __device__ bool voronoi_cell(const Rep& R, int64_t self, const int32_t* pi, int32_t self_id,
                              const int2* __restrict__ pos, const int32_t* __restrict__ ids,
-                             const GridView& G, Poly<CAP>& P, int32_t* status) {
+                             const GridView& G, Poly<CAP>& P, int32_t* status, uint32_t* n_cand = nullptr,
+                             uint32_t* n_runs = nullptr) {
   bool bad = false, overflow = false;
   poly_init(P, self_id, R.L[0], R.L[1], &bad);
   const int64_t Lx = R.L[0], Ly = R.L[1];
@@ -256,6 +257,10 @@ __device__ bool voronoi_cell(const Rep& R, int64_t self, const int32_t* pi, int3
     }
   };
   auto run = [&](uint32_t qb, uint32_t qe) {
+    if (n_cand) {
+      *n_cand += qe - qb;
+      *n_runs += 1;
+    }
     for (uint32_t q = qb; q < qe; ++q) {
       if ((int64_t)q == self) continue;
       const int2 pj = pos[q];
@@ -370,6 +375,7 @@ __global__ void __launch_bounds__(kBlock) voronoi_step_kernel(
   const int li = t.first + (int)threadIdx.x;
   const int64_t step = *d_step;
   float nnew[3] = {0.f, 0.f, 0.f};
+  uint32_t n_cand = 0, n_runs = 0;
   if (li < R.n) {
     const int64_t s = R.p0 + li;
     const int2 p = S_pos[s];
@@ -378,13 +384,16 @@ __global__ void __launch_bounds__(kBlock) voronoi_step_kernel(
     const float ni[3] = {nv.x, nv.y, 0.f};
     const int32_t id = S_id[s];
     Poly<kFastCap> P;
-    if (voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status)) {
+    const bool ok = Pm.stats ? voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status, &n_cand, &n_runs)
+                             : voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status);
+    if (ok) {
       voronoi_update(R, Pm, step, s, P, pi, ni, id, S_dir, U_pos, U_dir, U_id, counts, nnew);
     } else {
       const int q = atomicAdd(ovf_count, 1);
       ovf_list[q] = make_int2((int)s, t.rep);
     }
   }
+  record_search_stats(Pm.stats, li < R.n, n_cand, n_runs);
   block_phi_accumulate<2>(nnew, phi_acc + ((size_t)(step % Pm.phi_cap) * (size_t)Pm.n_rep + (size_t)t.rep) * 3);
 }
 

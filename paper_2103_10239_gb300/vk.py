@@ -80,6 +80,8 @@ _SIGS = {
     "vk_get_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                       ctypes.POINTER(ctypes.c_int32)]),
     "vk_phase_name": (ctypes.c_char_p, [ctypes.c_int32]),
+    "vk_get_search_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     "vk_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(vk_info)]),
     "vk_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.POINTER(ctypes.c_float)]),
@@ -272,6 +274,14 @@ class Sim:
         nph = ctypes.c_int32(0)
         _check(lib.vk_get_profile(self._h, _ptr(ms), _ptr(la), 8, ctypes.byref(nph)), self._h)
         return {lib.vk_phase_name(p).decode(): (float(ms[p]), int(la[p])) for p in range(nph.value)}
+
+    def search_stats(self) -> dict:
+        """Mean candidates / runs per particle update while tracing was on."""
+        c = ctypes.c_double(0.0)
+        r = ctypes.c_double(0.0)
+        m = ctypes.c_int64(0)
+        _check(load().vk_get_search_stats(self._h, ctypes.byref(c), ctypes.byref(r), ctypes.byref(m)), self._h)
+        return {"mean_candidates": c.value, "mean_runs": r.value, "max_candidates": m.value}
 
     def autotune(self, candidates: Sequence[float], trial_steps: int = 3) -> float:
         c = np.ascontiguousarray(candidates, dtype=np.float32)

@@ -111,89 +111,310 @@ __device__ __forceinline__ int64_t sub_lo(int b, int64_t w, int s) {
   return q;
 }
 
-struct Walk {
+// Resumable generator of the slot runs of the two-level walk, so that the
+// candidate loop exists once in the kernel (instruction-cache footprint).
+// Phase 1: rings of sub-cells in the own coarse cell (when it is split).
+// Phase 2: rings of coarse cells; a row segment without sub-grids is one run,
+// a split cell contributes the rows of its sub-cells that meet the box
+// [p - rad, p + rad], rad^2 >= the current k-th best distance.
+struct RunGen {
+  // fixed
   const Rep* R;
   const uint32_t* __restrict__ bx;
   const uint32_t* __restrict__ by;
   GridView G;
+  int64_t px, py;
+  int nx, ny, cx, cy;
   int64_t own;
+  // phase 1 geometry
+  int s1, sx, sy;
+  uint32_t ob0;
+  int64_t cx0, wx1, cy0, wy1;
+  // cursor
+  int phase, r;
+  int bx0, bx1, by0, by1, px0, px1, py0, py1;  // phase 1 block (current and previous ring)
+  int yy, seg;                                  // phase 1 row / segment
+  int lox, hix, loy, hiy, plox, phix, ploy, phiy;
+  int oy;                                       // phase 2 row offset
+  int part, nparts;                             // phase 2 parts of the row
+  int pa[4], pb[4], pu[4];                      // part x0, x1, unwrapped x of x0
+  int64_t rowbase;
+  int ucy;
+  int x;                                        // current cell in a per-cell part (-1: part not started)
+  bool fast;
+  int sr, sr1, sx0r, sx1r;                      // rows of the current split-cell rectangle
+  uint32_t sbase;
+  int sstride;
+  bool in_rect;
   bool own_done;
+  // split cells met while the search radius was still unknown, revisited at
+  // the end of the ring (when it usually is known)
+  int ndef;
+  int64_t def_g[4];
+  int def_ucx[4], def_ucy[4];
 };
 
-// coarse cells x0..x1 (actual indices, contiguous) of one row; ux0 is the
-// unwrapped x index of cell x0 and ucy the unwrapped y index of the row
-template <int KC>
-__device__ __forceinline__ void visit_cells(Ctx& C, const Walk& W, const int2* __restrict__ pos,
-                                            const int32_t* __restrict__ ids, int x0, int x1, int ux0, int ucy,
-                                            int64_t rowbase, Top<KC>& T) {
-  const GridView& G = W.G;
-  const uint32_t sb0 = __ldg(G.sub_base + rowbase + x0), sb1 = __ldg(G.sub_base + rowbase + x1 + 1);
-  if (sb1 - sb0 == (uint32_t)(x1 - x0 + 1)) {  // no sub-grid in the segment: one run
-    scan_run<KC>(C, pos, ids, __ldg(G.off + rowbase + x0), __ldg(G.off + rowbase + x1 + 1), T);
-    return;
+enum { kRun = 0, kRingEnd = 1, kDone = 2 };
+
+__device__ __forceinline__ void gen_row_parts(RunGen& g) {
+  // parts of row offset g.oy of ring g.r: up to 2 segments, each split by the wrap
+  g.nparts = 0;
+  const int ay = g.ucy < 0 ? g.ucy + g.ny : (g.ucy >= g.ny ? g.ucy - g.ny : g.ucy);
+  g.rowbase = g.R->c0 + (int64_t)ay * g.nx;
+  int sa[2], sb[2], ns = 0;
+  if (g.oy < g.ploy || g.oy > g.phiy) {
+    sa[0] = g.lox; sb[0] = g.hix; ns = 1;
+  } else {
+    if (g.lox <= g.plox - 1) { sa[ns] = g.lox; sb[ns] = g.plox - 1; ++ns; }
+    if (g.phix + 1 <= g.hix) { sa[ns] = g.phix + 1; sb[ns] = g.hix; ++ns; }
   }
-  const Rep& R = *W.R;
-  uint32_t pb = 0, pe = 0;
-  bool pend = false;
-  for (int x = x0; x <= x1; ++x) {
-    const int64_t g = rowbase + x;
-    const uint32_t b0 = __ldg(G.sub_base + g), b1 = __ldg(G.sub_base + g + 1);
-    if (b1 - b0 == 1) {
-      const uint32_t qb = __ldg(G.off + g), qe = __ldg(G.off + g + 1);
-      if (pend && qb == pe) {
-        pe = qe;
-      } else {
-        if (pend) scan_run<KC>(C, pos, ids, pb, pe, T);
-        pend = true;
-        pb = qb;
-        pe = qe;
-      }
-      continue;
-    }
-    if (pend) scan_run<KC>(C, pos, ids, pb, pe, T);
-    pend = false;
-    if (g == W.own && W.own_done) continue;
-    const uint64_t r2 = T.d[KC - 1];
-    if (r2 == ~0ull) {
-      scan_run<KC>(C, pos, ids, __ldg(G.off + g), __ldg(G.off + g + 1), T);
-      continue;
-    }
-    // only the sub-cells meeting the box [p - rad, p + rad]
-    const int64_t rad = radius_upper(r2);
-    const int ucx = ux0 + (x - x0);
-    const int64_t cx0 = cell_lo_tab(ucx, R.nc[0], W.bx, R.L[0]);
-    const int64_t wx = cell_lo_tab(ucx + 1, R.nc[0], W.bx, R.L[0]) - cx0;
-    const int64_t cy0 = cell_lo_tab(ucy, R.nc[1], W.by, R.L[1]);
-    const int64_t wy = cell_lo_tab(ucy + 1, R.nc[1], W.by, R.L[1]) - cy0;
-    const int64_t lx = (int64_t)C.px - rad - cx0, hx = (int64_t)C.px + rad - cx0;
-    const int64_t ly = (int64_t)C.py - rad - cy0, hy = (int64_t)C.py + rad - cy0;
-    if (hx < 0 || lx >= wx || hy < 0 || ly >= wy) continue;
-    const int s = __ldg(G.sub_s + g);
-    const int sx0 = lx <= 0 ? 0 : sub_idx(lx, wx, s), sx1 = hx >= wx ? s - 1 : sub_idx(hx, wx, s);
-    const int sy0 = ly <= 0 ? 0 : sub_idx(ly, wy, s), sy1 = hy >= wy ? s - 1 : sub_idx(hy, wy, s);
-    for (int yy = sy0; yy <= sy1; ++yy) {
-      const uint32_t rb = b0 + (uint32_t)yy * s;
-      scan_run<KC>(C, pos, ids, __ldg(G.sub_off + rb + sx0), __ldg(G.sub_off + rb + sx1 + 1), T);
+  for (int q = 0; q < ns; ++q) {
+    const int ua = g.cx + sa[q];
+    const int start = ua < 0 ? ua + g.nx : (ua >= g.nx ? ua - g.nx : ua);
+    const int len = sb[q] - sa[q] + 1;
+    if (start + len <= g.nx) {
+      g.pa[g.nparts] = start; g.pb[g.nparts] = start + len - 1; g.pu[g.nparts] = ua; ++g.nparts;
+    } else {
+      g.pa[g.nparts] = start; g.pb[g.nparts] = g.nx - 1; g.pu[g.nparts] = ua; ++g.nparts;
+      g.pa[g.nparts] = 0; g.pb[g.nparts] = start + len - g.nx - 1; g.pu[g.nparts] = ua + (g.nx - start);
+      ++g.nparts;
     }
   }
-  if (pend) scan_run<KC>(C, pos, ids, pb, pe, T);
+  g.part = 0;
+  g.x = -1;
 }
 
-// row segment of x offsets [a, b] around the particle's cell cx
-template <int KC>
-__device__ __forceinline__ void visit_segment(Ctx& C, const Walk& W, const int2* __restrict__ pos,
-                                              const int32_t* __restrict__ ids, int cx, int a, int b, int ucy,
-                                              int64_t rowbase, Top<KC>& T) {
-  if (a > b) return;
-  const int nx = W.R->nc[0];
-  const int ua = cx + a;
-  const int start = ua < 0 ? ua + nx : (ua >= nx ? ua - nx : ua);
-  const int len = b - a + 1;
-  if (start + len <= nx) {
-    visit_cells<KC>(C, W, pos, ids, start, start + len - 1, ua, ucy, rowbase, T);
+// sub-cell rectangle of split cell gc (unwrapped indices ucx, ucy) meeting
+// the box [p - rad, p + rad]; false if it misses the cell
+__device__ __forceinline__ bool gen_rect(RunGen& g, int64_t gc, int ucx, int ucy, uint64_t r2) {
+  const GridView& G = g.G;
+  const Rep& R = *g.R;
+  const int s = __ldg(G.sub_s + gc);
+  g.sbase = __ldg(G.sub_base + gc);
+  g.sstride = s;
+  if (r2 == ~0ull) {
+    g.sx0r = 0; g.sx1r = s - 1; g.sr = 0; g.sr1 = s - 1;
+    g.in_rect = true;
+    return true;
+  }
+  const int64_t rad = radius_upper(r2);
+  const int64_t cx0 = cell_lo_tab(ucx, g.nx, g.bx, R.L[0]);
+  const int64_t wx = cell_lo_tab(ucx + 1, g.nx, g.bx, R.L[0]) - cx0;
+  const int64_t cy0 = cell_lo_tab(ucy, g.ny, g.by, R.L[1]);
+  const int64_t wy = cell_lo_tab(ucy + 1, g.ny, g.by, R.L[1]) - cy0;
+  const int64_t lx = g.px - rad - cx0, hx = g.px + rad - cx0;
+  const int64_t ly = g.py - rad - cy0, hy = g.py + rad - cy0;
+  if (hx < 0 || lx >= wx || hy < 0 || ly >= wy) return false;
+  g.sx0r = lx <= 0 ? 0 : sub_idx(lx, wx, s);
+  g.sx1r = hx >= wx ? s - 1 : sub_idx(hx, wx, s);
+  g.sr = ly <= 0 ? 0 : sub_idx(ly, wy, s);
+  g.sr1 = hy >= wy ? s - 1 : sub_idx(hy, wy, s);
+  g.in_rect = true;
+  return true;
+}
+
+__device__ __forceinline__ void gen_ring2(RunGen& g) {
+  const int r = g.r;
+  g.lox = -min(r, (g.nx - 1) / 2); g.hix = min(r, g.nx / 2);
+  g.loy = -min(r, (g.ny - 1) / 2); g.hiy = min(r, g.ny / 2);
+  g.plox = r ? -min(r - 1, (g.nx - 1) / 2) : 1; g.phix = r ? min(r - 1, g.nx / 2) : 0;
+  g.ploy = r ? -min(r - 1, (g.ny - 1) / 2) : 1; g.phiy = r ? min(r - 1, g.ny / 2) : 0;
+  g.oy = g.loy;
+  g.ucy = g.cy + g.oy;
+  gen_row_parts(g);
+}
+
+__device__ __forceinline__ void gen_ring1(RunGen& g) {
+  const int r = g.r, s = g.s1;
+  g.bx0 = max(g.sx - r, 0); g.bx1 = min(g.sx + r, s - 1);
+  g.by0 = max(g.sy - r, 0); g.by1 = min(g.sy + r, s - 1);
+  g.px0 = r ? max(g.sx - r + 1, 0) : 1; g.px1 = r ? min(g.sx + r - 1, s - 1) : 0;
+  g.py0 = r ? max(g.sy - r + 1, 0) : 1; g.py1 = r ? min(g.sy + r - 1, s - 1) : 0;
+  g.yy = g.by0;
+  g.seg = 0;
+}
+
+__device__ __forceinline__ void gen_init(RunGen& g, const Rep& R, const uint32_t* __restrict__ bounds,
+                                         const GridView& G, uint32_t px, uint32_t py) {
+  g.R = &R;
+  g.bx = bounds + R.bnd[0];
+  g.by = bounds + R.bnd[1];
+  g.G = G;
+  g.px = px;
+  g.py = py;
+  g.nx = R.nc[0];
+  g.ny = R.nc[1];
+  g.cx = cell_of_tab(px, g.nx, g.bx, R.inv_w[0]);
+  g.cy = cell_of_tab(py, g.ny, g.by, R.inv_w[1]);
+  g.own = R.c0 + (int64_t)g.cy * g.nx + g.cx;
+  g.own_done = false;
+  g.in_rect = false;
+  g.ndef = 0;
+  g.ob0 = __ldg(G.sub_base + g.own);
+  const uint32_t ob1 = __ldg(G.sub_base + g.own + 1);
+  g.r = 0;
+  if (ob1 - g.ob0 > 1) {
+    g.phase = 1;
+    g.s1 = __ldg(G.sub_s + g.own);
+    g.cx0 = __ldg(g.bx + g.cx);
+    g.wx1 = (int64_t)__ldg(g.bx + g.cx + 1) - g.cx0;
+    g.cy0 = __ldg(g.by + g.cy);
+    g.wy1 = (int64_t)__ldg(g.by + g.cy + 1) - g.cy0;
+    g.sx = sub_idx(px - g.cx0, g.wx1, g.s1);
+    g.sy = sub_idx(py - g.cy0, g.wy1, g.s1);
+    gen_ring1(g);
   } else {
-    visit_cells<KC>(C, W, pos, ids, start, nx - 1, ua, ucy, rowbase, T);
-    visit_cells<KC>(C, W, pos, ids, 0, start + len - nx - 1, ua + (nx - start), ucy, rowbase, T);
+    g.phase = 2;
+    gen_ring2(g);
+  }
+}
+
+// squared distance bound of the current ring's block (call at kRingEnd);
+// returns ~0ull when the phase has covered everything it can
+__device__ __forceinline__ uint64_t gen_ring_bound(const RunGen& g) {
+  int64_t B = INT64_MAX;
+  if (g.phase == 1) {
+    const int s = g.s1;
+    if (g.bx0 == 0 && g.by0 == 0 && g.bx1 == s - 1 && g.by1 == s - 1) return ~0ull;
+    if (g.bx0 > 0) B = min(B, g.px - (g.cx0 + sub_lo(g.bx0, g.wx1, s)) + 1);
+    if (g.bx1 < s - 1) B = min(B, g.cx0 + sub_lo(g.bx1 + 1, g.wx1, s) - g.px);
+    if (g.by0 > 0) B = min(B, g.py - (g.cy0 + sub_lo(g.by0, g.wy1, s)) + 1);
+    if (g.by1 < s - 1) B = min(B, g.cy0 + sub_lo(g.by1 + 1, g.wy1, s) - g.py);
+  } else {
+    const bool fullx = g.hix - g.lox + 1 == g.nx, fully = g.hiy - g.loy + 1 == g.ny;
+    if (fullx && fully) return ~0ull;
+    const int r = g.r;
+    if (!fullx) {
+      B = min(B, g.px - cell_lo_tab(g.cx - r, g.nx, g.bx, g.R->L[0]) + 1);
+      B = min(B, cell_lo_tab(g.cx + r + 1, g.nx, g.bx, g.R->L[0]) - g.px);
+    }
+    if (!fully) {
+      B = min(B, g.py - cell_lo_tab(g.cy - r, g.ny, g.by, g.R->L[1]) + 1);
+      B = min(B, cell_lo_tab(g.cy + r + 1, g.ny, g.by, g.R->L[1]) - g.py);
+    }
+  }
+  return (uint64_t)B * (uint64_t)B;
+}
+
+// after kRingEnd: move to the next ring (stop=false) or end the phase (stop=true)
+__device__ __forceinline__ bool gen_advance(RunGen& g, bool stop) {
+  if (g.phase == 1) {
+    g.own_done = true;
+    if (!stop) {
+      ++g.r;
+      gen_ring1(g);
+      return true;
+    }
+    g.phase = 2;
+    g.r = 0;
+    gen_ring2(g);
+    return true;
+  }
+  if (stop) return false;
+  ++g.r;
+  const int lox = -min(g.r, (g.nx - 1) / 2), hix = min(g.r, g.nx / 2);
+  const int loy = -min(g.r, (g.ny - 1) / 2), hiy = min(g.r, g.ny / 2);
+  if (lox == g.lox && hix == g.hix && loy == g.loy && hiy == g.hiy) return false;  // nothing new
+  gen_ring2(g);
+  return true;
+}
+
+// next run [qb, qe) of the current ring, or kRingEnd
+__device__ __forceinline__ int gen_next(RunGen& g, uint64_t r2, uint32_t& qb, uint32_t& qe) {
+  const GridView& G = g.G;
+  if (g.phase == 1) {
+    for (;;) {
+      if (g.yy > g.by1) return kRingEnd;
+      const uint32_t rb = g.ob0 + (uint32_t)g.yy * g.s1;
+      const bool oldrow = !(g.yy < g.py0 || g.yy > g.py1 || g.px0 > g.px1);
+      int a, b;
+      if (!oldrow) {
+        a = g.bx0; b = g.bx1;
+        ++g.yy;
+      } else if (g.seg == 0) {
+        a = g.bx0; b = g.px0 - 1;
+        g.seg = 1;
+      } else {
+        a = g.px1 + 1; b = g.bx1;
+        g.seg = 0;
+        ++g.yy;
+      }
+      if (a > b) continue;
+      qb = __ldg(G.sub_off + rb + a);
+      qe = __ldg(G.sub_off + rb + b + 1);
+      return kRun;
+    }
+  }
+  for (;;) {
+    if (g.in_rect) {  // rows of a split cell's rectangle
+      if (g.sr > g.sr1) {
+        g.in_rect = false;
+        continue;
+      }
+      const uint32_t rb = g.sbase + (uint32_t)g.sr * g.sstride;
+      ++g.sr;
+      qb = __ldg(G.sub_off + rb + g.sx0r);
+      qe = __ldg(G.sub_off + rb + g.sx1r + 1);
+      return kRun;
+    }
+    if (g.part >= g.nparts) {  // next row
+      if (g.oy + 1 > g.hiy) {
+        if (g.ndef > 0) {  // deferred split cells, now with the current radius
+          --g.ndef;
+          gen_rect(g, g.def_g[g.ndef], g.def_ucx[g.ndef], g.def_ucy[g.ndef], r2);
+          continue;
+        }
+        return kRingEnd;
+      }
+      ++g.oy;
+      g.ucy = g.cy + g.oy;
+      gen_row_parts(g);
+      continue;
+    }
+    const int x0 = g.pa[g.part], x1 = g.pb[g.part];
+    if (g.x < 0) {  // start of a part: one run when no cell in it is split
+      const uint32_t sb0 = __ldg(G.sub_base + g.rowbase + x0), sb1 = __ldg(G.sub_base + g.rowbase + x1 + 1);
+      if (sb1 - sb0 == (uint32_t)(x1 - x0 + 1)) {
+        ++g.part;
+        qb = __ldg(G.off + g.rowbase + x0);
+        qe = __ldg(G.off + g.rowbase + x1 + 1);
+        return kRun;
+      }
+      g.x = x0;
+    }
+    if (g.x > x1) {
+      ++g.part;
+      g.x = -1;
+      continue;
+    }
+    // per cell: a maximal run of unsplit cells, or one split cell
+    const int64_t gc = g.rowbase + g.x;
+    uint32_t b0 = __ldg(G.sub_base + gc), b1 = __ldg(G.sub_base + gc + 1);
+    if (b1 - b0 == 1) {
+      const int xs = g.x;
+      while (g.x + 1 <= x1) {
+        const uint32_t c1 = __ldg(G.sub_base + gc + (g.x - xs) + 2);
+        if (c1 - b1 != 1) break;
+        b1 = c1;
+        ++g.x;
+      }
+      qb = __ldg(G.off + g.rowbase + xs);
+      qe = __ldg(G.off + g.rowbase + g.x + 1);
+      ++g.x;
+      return kRun;
+    }
+    const int xc = g.x;
+    ++g.x;
+    if (gc == g.own && g.own_done) continue;
+    const int ucx = g.pu[g.part] + (xc - x0);
+    if (r2 == ~0ull && g.ndef < 4) {
+      g.def_g[g.ndef] = gc;
+      g.def_ucx[g.ndef] = ucx;
+      g.def_ucy[g.ndef] = g.ucy;
+      ++g.ndef;
+      continue;
+    }
+    gen_rect(g, gc, ucx, g.ucy, r2);
   }
 }
 
@@ -201,79 +422,20 @@ template <int KC>
 __device__ __forceinline__ void knn2_search(Ctx& C, const Rep& R, const uint32_t* __restrict__ bounds,
                                             const GridView& G, const int2* __restrict__ pos,
                                             const int32_t* __restrict__ ids, Top<KC>& T) {
-  Walk W;
-  W.R = &R;
-  W.bx = bounds + R.bnd[0];
-  W.by = bounds + R.bnd[1];
-  W.G = G;
-  const int nx = R.nc[0], ny = R.nc[1];
-  const int cx = cell_of_tab(C.px, nx, W.bx, R.inv_w[0]);
-  const int cy = cell_of_tab(C.py, ny, W.by, R.inv_w[1]);
-  W.own = R.c0 + (int64_t)cy * nx + cx;
-  W.own_done = false;
-  const uint32_t ob0 = __ldg(G.sub_base + W.own), ob1 = __ldg(G.sub_base + W.own + 1);
-  if (ob1 - ob0 > 1) {
-    // phase 1: rings of sub-cells in the own coarse cell
-    const int s = __ldg(G.sub_s + W.own);
-    const int64_t cx0 = __ldg(W.bx + cx), wx = (int64_t)__ldg(W.bx + cx + 1) - cx0;
-    const int64_t cy0 = __ldg(W.by + cy), wy = (int64_t)__ldg(W.by + cy + 1) - cy0;
-    const int sx = sub_idx((int64_t)C.px - cx0, wx, s), sy = sub_idx((int64_t)C.py - cy0, wy, s);
-    for (int r = 0;; ++r) {
-      const int bx0 = max(sx - r, 0), bx1 = min(sx + r, s - 1), by0 = max(sy - r, 0), by1 = min(sy + r, s - 1);
-      const int px0 = r ? max(sx - r + 1, 0) : 1, px1 = r ? min(sx + r - 1, s - 1) : 0;
-      const int py0 = r ? max(sy - r + 1, 0) : 1, py1 = r ? min(sy + r - 1, s - 1) : 0;
-      for (int yy = by0; yy <= by1; ++yy) {
-        const uint32_t rb = ob0 + (uint32_t)yy * s;
-        if (yy < py0 || yy > py1 || px0 > px1) {
-          scan_run<KC>(C, pos, ids, __ldg(G.sub_off + rb + bx0), __ldg(G.sub_off + rb + bx1 + 1), T);
-        } else {
-          if (bx0 < px0) scan_run<KC>(C, pos, ids, __ldg(G.sub_off + rb + bx0), __ldg(G.sub_off + rb + px0), T);
-          if (bx1 > px1)
-            scan_run<KC>(C, pos, ids, __ldg(G.sub_off + rb + px1 + 1), __ldg(G.sub_off + rb + bx1 + 1), T);
-        }
-      }
-      if (bx0 == 0 && by0 == 0 && bx1 == s - 1 && by1 == s - 1) break;
-      int64_t B = INT64_MAX;
-      if (bx0 > 0) B = min(B, (int64_t)C.px - (cx0 + sub_lo(bx0, wx, s)) + 1);
-      if (bx1 < s - 1) B = min(B, cx0 + sub_lo(bx1 + 1, wx, s) - (int64_t)C.px);
-      if (by0 > 0) B = min(B, (int64_t)C.py - (cy0 + sub_lo(by0, wy, s)) + 1);
-      if (by1 < s - 1) B = min(B, cy0 + sub_lo(by1 + 1, wy, s) - (int64_t)C.py);
-      if (T.d[KC - 1] < (uint64_t)B * (uint64_t)B) break;
+  RunGen g;
+  gen_init(g, R, bounds, G, C.px, C.py);
+  for (;;) {
+    uint32_t qb = 0, qe = 0;
+    const int ev = gen_next(g, T.d[KC - 1], qb, qe);
+    if (ev == kRun) {
+      scan_run<KC>(C, pos, ids, qb, qe, T);  // the only copy of the candidate loop
+      continue;
     }
-    W.own_done = true;
-  }
-  // phase 2: rings of coarse cells
-  for (int r = 0;; ++r) {
-    const int lox = -min(r, (nx - 1) / 2), hix = min(r, nx / 2);
-    const int loy = -min(r, (ny - 1) / 2), hiy = min(r, ny / 2);
-    const int plox = r ? -min(r - 1, (nx - 1) / 2) : 1, phix = r ? min(r - 1, nx / 2) : 0;
-    const int ploy = r ? -min(r - 1, (ny - 1) / 2) : 1, phiy = r ? min(r - 1, ny / 2) : 0;
-    const bool fullx = hix - lox + 1 == nx, fully = hiy - loy + 1 == ny;
-    if (r > 0 && lox == plox && hix == phix && loy == ploy && hiy == phiy) break;  // nothing new
-    for (int oy = loy; oy <= hiy; ++oy) {
-      const int ucy = cy + oy;
-      const int ay = ucy < 0 ? ucy + ny : (ucy >= ny ? ucy - ny : ucy);
-      const int64_t rowbase = R.c0 + (int64_t)ay * nx;
-      if (oy < ploy || oy > phiy) {
-        visit_segment<KC>(C, W, pos, ids, cx, lox, hix, ucy, rowbase, T);
-      } else {
-        visit_segment<KC>(C, W, pos, ids, cx, lox, plox - 1, ucy, rowbase, T);
-        visit_segment<KC>(C, W, pos, ids, cx, phix + 1, hix, ucy, rowbase, T);
-      }
-    }
-    if (fullx && fully) break;
-    int64_t B = INT64_MAX;
-    if (!fullx) {
-      B = min(B, (int64_t)C.px - cell_lo_tab(cx - r, nx, W.bx, R.L[0]) + 1);
-      B = min(B, cell_lo_tab(cx + r + 1, nx, W.bx, R.L[0]) - (int64_t)C.px);
-    }
-    if (!fully) {
-      B = min(B, (int64_t)C.py - cell_lo_tab(cy - r, ny, W.by, R.L[1]) + 1);
-      B = min(B, cell_lo_tab(cy + r + 1, ny, W.by, R.L[1]) - (int64_t)C.py);
-    }
-    // every unscanned particle is at squared distance >= B^2; an equal
-    // distance could still win on id, hence the strict test
-    if (T.d[KC - 1] < (uint64_t)B * (uint64_t)B) break;
+    // ring end: every unscanned particle (of the phase's region) is at
+    // squared distance >= B2; an equal distance could still win on id
+    const uint64_t B2 = gen_ring_bound(g);
+    const bool stop = (B2 == ~0ull) || (T.d[KC - 1] < B2);
+    if (!gen_advance(g, stop)) break;
   }
 }
 

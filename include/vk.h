@@ -201,6 +201,40 @@ vk_status vk_get_info(vk_sim* sim, vk_info* out);
 vk_status vk_autotune(vk_sim* sim, const float* candidates, int32_t n_candidates,
                       int32_t trial_steps, float* best);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free kNN lists.  (The paper has no counterpart: this is a
+ * deployment entry point.)
+ *
+ * Some callers cannot allocate GPU memory at the moment they need neighbor
+ * lists: code that is recording a CUDA graph (cudaMalloc/cudaFree are not
+ * allowed during stream capture), real-time loops that cannot afford the
+ * blocking and device synchronisation of cudaMalloc/cudaFree, and hosts that
+ * manage the whole device memory budget themselves.  This call allocates
+ * nothing: the caller passes the input and output arrays, and every
+ * intermediate array lives in one fixed static scratch array of about 6 MiB
+ * compiled into the library, which each GPU that loads the library holds
+ * until the process exits.
+ *
+ * Computes, for n <= VK_NOALLOC_MAX_N points of a periodic 2D box, the same
+ * lists as vk_init + vk_get_neighbors with VK_RULE_KNN: out_ids[i*k + j] is
+ * the j-th nearest other point of point i, ordered by (exact squared
+ * minimum-image distance, id).
+ *   pos_q    device pointer, n*2 int32 in [0, L_q) (points outside are
+ *            wrapped into the box and reported through dev_status)
+ *   out_ids  device pointer, n*k int32
+ *   dev_status  optional pointer (device or host-pinned) receiving 0, or
+ *            VK_ERR_RANGE when a point lay outside the box
+ * Asynchronous on cuda_stream (NULL: the legacy default stream).  Returns
+ * VK_ERR_ARG for n > VK_NOALLOC_MAX_N, n < 2, k outside [1, min(32, n-1)] or
+ * a non-2D box.  The first call on each device looks up the device address
+ * of the scratch array, so make that first call outside stream capture.  All
+ * calls share the one scratch array and leave their intermediates in it:
+ * calls that can overlap on the GPU (different streams, different host
+ * threads) race and must be serialised by the caller. */
+#define VK_NOALLOC_MAX_N 65536
+vk_status vk_knn_lists_noalloc(const int32_t* pos_q, int64_t n, const vk_box* box, int32_t k,
+                               int32_t* out_ids, int32_t* dev_status, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

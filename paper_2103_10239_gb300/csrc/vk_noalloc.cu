@@ -1,0 +1,213 @@
+// vk_noalloc.cu -- k-nearest-neighbor lists without any device allocation.
+//
+// Who needs this: callers that must not allocate GPU memory at the point of
+// the call.  Examples: code that records its work into a CUDA graph (plain
+// cudaMalloc/cudaFree are not allowed while a stream is being captured);
+// real-time or tightly scheduled loops, where cudaMalloc/cudaFree can block on
+// or synchronise the device and add unpredictable latency; and hosts that own
+// the device memory budget themselves (a fixed pool, a framework allocator)
+// and forbid a library from taking memory behind their back.  For them this
+// entry point works entirely inside one fixed scratch array that is part of
+// the library image and sized for at most kNoAllocMaxN particles.
+//
+// It runs the same kernels as vk_init + vk_get_neighbors (cell histogram,
+// two-level grid build, scatter, 2D kNN search) on the caller's stream, with
+// every intermediate array carved out of that static array.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/vk.h"
+#include "vk_internal.cuh"
+
+namespace vk {
+
+namespace {
+
+constexpr int64_t kNoAllocMaxN = VK_NOALLOC_MAX_N;
+constexpr float kNoAllocOccupancy = 2.0f;
+// generous bound of the scratch the layout below needs for kNoAllocMaxN
+constexpr size_t kScratchBytes = (size_t)6 << 20;
+
+// The scratch array: every GPU that loads the library keeps these bytes
+// until the process exits.  Host code must not use the symbol as a pointer;
+// its device address comes from cudaGetSymbolAddress (see scratch_ptr).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+std::mutex g_mu;
+void* g_ptr[256] = {nullptr};
+
+// Device address of the scratch on the current device, looked up once per
+// device (the first call on a device does it; that call must not be made
+// while the stream is being captured).
+cudaError_t scratch_ptr(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_ptr[dev] = p;
+  }
+  *out = g_ptr[dev];
+  return cudaSuccess;
+}
+
+struct Carver {
+  unsigned char* base;
+  size_t used;
+  template <class T>
+  T* take(size_t count) {
+    used = (used + 255) & ~(size_t)255;
+    T* p = reinterpret_cast<T*>(base + used);
+    used += sizeof(T) * (count ? count : 1);
+    return p;
+  }
+};
+
+// tables, grid bounds and cleared counters for one call
+__global__ void noalloc_setup_kernel(Rep R, BlockTask* tasks, int n_tasks, Rep* rep_out, uint32_t* bounds,
+                                     uint32_t* counts, int64_t n_cells, uint32_t* sub_count, int64_t n_sub,
+                                     int32_t* status) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (tid == 0) {
+    *rep_out = R;
+    *status = 0;
+  }
+  for (int64_t i = tid; i < n_tasks; i += stride) tasks[i] = BlockTask{0, (int32_t)(i * kBlock)};
+  for (int a = 0; a < 3; ++a)
+    for (int64_t b = tid; b <= R.nc[a]; b += stride)
+      bounds[R.bnd[a] + b] = (uint32_t)((b * (int64_t)R.L[a] + R.nc[a] - 1) / R.nc[a]);
+  for (int64_t i = tid; i < n_cells; i += stride) counts[i] = 0u;
+  for (int64_t i = tid; i < n_sub; i += stride) sub_count[i] = 0u;
+}
+
+// caller positions -> U; positions outside the box are wrapped into it so
+// that every later index stays in bounds, and the status records it
+__global__ void noalloc_load_kernel(const int32_t* __restrict__ pos, int32_t n, uint32_t Lx, uint32_t Ly,
+                                    int2* __restrict__ U_pos, float2* __restrict__ U_dir, int32_t* __restrict__ U_id,
+                                    int32_t* status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t x = pos[2 * (int64_t)i], y = pos[2 * (int64_t)i + 1];
+  if (x < 0 || x >= (int64_t)Lx || y < 0 || y >= (int64_t)Ly) {
+    atomicCAS(status, 0, (int32_t)VK_ERR_RANGE);
+    x %= (int64_t)Lx;
+    if (x < 0) x += Lx;
+    y %= (int64_t)Ly;
+    if (y < 0) y += Ly;
+  }
+  U_pos[i] = make_int2((int32_t)x, (int32_t)y);
+  U_dir[i] = make_float2(0.f, 0.f);
+  U_id[i] = i;
+}
+
+}  // namespace
+
+}  // namespace vk
+
+using namespace vk;
+
+extern "C" vk_status vk_knn_lists_noalloc(const int32_t* pos_q, int64_t n, const vk_box* box, int32_t k,
+                                          int32_t* out_ids, int32_t* dev_status, void* cuda_stream) {
+  if (!pos_q || !box || !out_ids) return VK_ERR_ARG;
+  if (n < 2 || n > kNoAllocMaxN) return VK_ERR_ARG;  // beyond the fixed scratch: see VK_NOALLOC_MAX_N
+  if (k < 1 || k > kMaxK || k > n - 1) return VK_ERR_ARG;
+  if (box->dim != 2) return VK_ERR_ARG;
+  for (int a = 0; a < 2; ++a)
+    if (box->box_q[a] < 1 || box->box_q[a] > (1u << 31)) return VK_ERR_RANGE;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  void* base = nullptr;
+  if (scratch_ptr(&base) != cudaSuccess) {
+    cudaGetLastError();
+    return VK_ERR_CUDA;
+  }
+
+  // grid plan (host arithmetic only)
+  Rep R;
+  std::memset(&R, 0, sizeof(R));
+  R.p0 = 0;
+  R.c0 = 0;
+  R.n = (int32_t)n;
+  R.L[0] = box->box_q[0];
+  R.L[1] = box->box_q[1];
+  R.L[2] = 1;
+  const double side = std::sqrt((double)kNoAllocOccupancy * (double)R.L[0] * (double)R.L[1] / (double)n);
+  int64_t n_cells = 1;
+  for (int a = 0; a < 3; ++a) {
+    double ncd = a < 2 ? std::floor((double)R.L[a] / side) : 1.0;
+    ncd = std::max(1.0, std::min(ncd, std::min((double)R.L[a], 65536.0)));
+    R.nc[a] = (int32_t)ncd;
+    n_cells *= R.nc[a];
+    R.inv_w[a] = (float)R.nc[a] / (float)R.L[a];
+  }
+  R.bnd[0] = 0;
+  R.bnd[1] = R.nc[0] + 1;
+  R.bnd[2] = R.bnd[1] + R.nc[1] + 1;
+  const int64_t n_bounds = (int64_t)R.nc[0] + R.nc[1] + R.nc[2] + 3;
+  const int64_t n_sub = n_cells + n / kSubTarget + 1;
+  const int n_tasks = (int)((n + kBlock - 1) / kBlock);
+
+  // carve the scratch
+  Carver cv{reinterpret_cast<unsigned char*>(base), 0};
+  Buffers b;
+  std::memset(&b, 0, sizeof(b));
+  b.U_pos = cv.take<int2>(n);
+  b.U_dir = cv.take<float2>(n);
+  b.U_id = cv.take<int32_t>(n);
+  b.U_rank = cv.take<uint32_t>(n);
+  b.S_pos = cv.take<int2>(n);
+  b.S_dir = cv.take<float2>(n);
+  b.S_id = cv.take<int32_t>(n);
+  b.counts = cv.take<uint32_t>(n_cells);
+  b.offsets = cv.take<uint32_t>(n_cells + 1);
+  b.bsum = cv.take<uint32_t>(2 * ((n_cells + 2047) / 2048 + 1));
+  b.sub_s = cv.take<uint8_t>(n_cells);
+  b.sub_base = cv.take<uint32_t>(n_cells + 1);
+  b.sub_count = cv.take<uint32_t>(n_sub);
+  b.sub_off = cv.take<uint32_t>(n_sub + 1);
+  b.bsum2 = cv.take<uint32_t>((n_sub + 2047) / 2048 + 1);
+  b.bounds = cv.take<uint32_t>(n_bounds);
+  Rep* rep_d = cv.take<Rep>(1);
+  BlockTask* tasks_d = cv.take<BlockTask>(n_tasks);
+  int32_t* status_d = cv.take<int32_t>(1);
+  if (cv.used > kScratchBytes) return VK_ERR_CAPACITY;  // cannot happen for n <= kNoAllocMaxN
+
+  Geometry g;
+  g.dim = 2;
+  g.rule = VK_RULE_KNN;
+  g.n_rep = 1;
+  g.n_total = n;
+  g.n_cells = n_cells;
+  g.n_sub_max = n_sub;
+  g.n_tasks = n_tasks;
+  g.reps = rep_d;
+  g.tasks = tasks_d;
+  StepParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.k = k;
+  P.n_rep = 1;
+  P.phi_cap = 2;
+
+  noalloc_setup_kernel<<<64, 256, 0, st>>>(R, tasks_d, n_tasks, rep_d, b.bounds, b.counts, n_cells, b.sub_count,
+                                           n_sub, status_d);
+  noalloc_load_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(pos_q, (int32_t)n, R.L[0], R.L[1], (int2*)b.U_pos,
+                                                              (float2*)b.U_dir, b.U_id, status_d);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_count(g, b, st);
+  if (e == cudaSuccess) e = launch_build(g, b, st);
+  if (e == cudaSuccess) e = launch_scatter(g, b, P, 0, st);
+  if (e == cudaSuccess) e = launch_knn2_export(g, b, k, 0, (int)n, out_ids, st);
+  if (e == cudaSuccess && dev_status)
+    e = cudaMemcpyAsync(dev_status, status_d, sizeof(int32_t), cudaMemcpyDefault, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return VK_ERR_CUDA;
+  }
+  return VK_OK;
+}

@@ -85,7 +85,11 @@ _SIGS = {
     "vk_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(vk_info)]),
     "vk_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.POINTER(ctypes.c_float)]),
+    "vk_knn_lists_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(vk_box),
+                                            ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
+
+NOALLOC_MAX_N = 65536
 
 
 def load(path: Optional[str] = None) -> ctypes.CDLL:
@@ -306,6 +310,17 @@ class Sim:
 
     def __exit__(self, *a):
         self.close()
+
+
+def knn_lists_noalloc(pos_q, box_q, frac_bits: int, k: int, out_ids, dev_status=None, stream=None) -> None:
+    """vk_knn_lists_noalloc: kNN lists of device-resident points into a
+    caller-provided device buffer, using only the library's static scratch
+    (no device allocation).  Asynchronous on ``stream``."""
+    box = make_box(box_q, frac_bits)
+    rc = load().vk_knn_lists_noalloc(_ptr(pos_q), int(pos_q.shape[0]), ctypes.byref(box), int(k), _ptr(out_ids),
+                                     _ptr(dev_status), _stream_handle(stream))
+    if rc != VK_OK:
+        raise VKError(rc, load().vk_status_string(rc).decode())
 
 
 def from_workload(w, stream=None, heading_kind: str = "dir", **over) -> Sim:

@@ -163,23 +163,24 @@ def recorded_traffic(workload_name: str):
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (the oracle as it stands, on the host cores)
 # ---------------------------------------------------------------------------
-def oracle_sample_rate(w, budget_s: float, min_q: int = 32):
+def oracle_sample_rate(w, budget_s: float, min_q: int = 32, m_fixed=None, seed: int = 0):
     """Oracle particle-steps/s on a bounded sample: brute-force kNN of a
     random subset of particles over all N plus the FP64 update, scaled to
-    the subset."""
+    the subset.  Without m_fixed the subset grows until the search takes
+    about budget_s."""
     import oracle
     oracle.build()
-    rng = np.random.default_rng(0)
-    # calibrate
-    q = np.sort(rng.choice(w.n, min_q, replace=False)).astype(np.int64)
-    t0 = time.perf_counter()
-    oracle.knn(w.pos_q, w.box_q, w.k, query=q)
-    t_q = (time.perf_counter() - t0) / min_q
-    m = int(max(min_q, min(w.n, budget_s / max(t_q, 1e-9))))
-    q = np.sort(rng.choice(w.n, m, replace=False)).astype(np.int64)
-    t0 = time.perf_counter()
-    nb = oracle.knn(w.pos_q, w.box_q, w.k, query=q)
-    t_knn = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    # grow the sample until the brute-force search takes about the budget
+    m = m_fixed or min_q
+    while True:
+        q = np.sort(rng.choice(w.n, m, replace=False)).astype(np.int64)
+        t0 = time.perf_counter()
+        nb = oracle.knn(w.pos_q, w.box_q, w.k, query=q)
+        t_knn = time.perf_counter() - t0
+        if m_fixed or t_knn >= 0.6 * budget_s or m >= w.n:
+            break
+        m = int(min(w.n, max(2 * m, m * 0.9 * budget_s / max(t_knn, 1e-6))))
     # the update of the sampled particles (run on a system made of them)
     off = np.arange(m + 1, dtype=np.int64) * w.k
     remap = np.full(w.n, -1, dtype=np.int64)
@@ -200,16 +201,15 @@ def run_reference(args, rank, world):
     w = workload(args)
     total_budget = 150.0
     per_step = total_budget / max(1, args.steps + args.warmup)
-    for _ in range(args.warmup):
-        oracle_sample_rate(w, per_step)
+    _, m_used, _, _ = oracle_sample_rate(w, per_step)  # size the per-step sample once
+    for i in range(args.warmup):
+        oracle_sample_rate(w, per_step, m_fixed=m_used, seed=1 + i)
     times, parts = [], 0
-    m_used = 0
     cores = 0
-    for _ in range(args.steps):
-        rate, m, cores, secs = oracle_sample_rate(w, per_step)
+    for i in range(args.steps):
+        rate, m, cores, secs = oracle_sample_rate(w, per_step, m_fixed=m_used, seed=100 + i)
         times.append(secs)
         parts += m
-        m_used = m
     value = parts / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,

@@ -56,6 +56,7 @@ struct vk_sim {
   int gexec_steps = 0;
   // tracing
   bool prof = false;
+  bool prof_counters = false;  // search counters (tracing level 2)
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[kPhases];
   double prof_ms[kPhases] = {0, 0, 0, 0, 0};
   int64_t prof_launches[kPhases] = {0, 0, 0, 0, 0};
@@ -99,7 +100,8 @@ StepParams step_params(const vk_sim* s) {
   P.seed_hi = (uint32_t)(s->prm.seed >> 32);
   P.n_rep = s->n_rep;
   P.phi_cap = s->phi_cap;
-  P.stats = s->prof ? s->d_stats : nullptr;
+  P.stats = (s->prof && s->prof_counters) ? s->d_stats : nullptr;
+  P.tile_stats = s->prof ? s->d_stats : nullptr;
   return P;
 }
 
@@ -240,6 +242,14 @@ vk_status clear_phi(vk_sim* s) {
   return VK_OK;
 }
 
+// kernels of the search+update phase: the 2D kNN warp-tile kernel and its
+// fallback walk; the per-particle walk alone while search counters are on;
+// the Voronoi kernel and its overflow kernel
+int search_launches(const vk_sim* s) {
+  if (s->prm.rule == VK_RULE_KNN) return (s->dim == 2 && !(s->prof && s->prof_counters)) ? 2 : 1;
+  return 2;
+}
+
 vk_status enqueue_step(vk_sim* s) {
   const StepParams P = step_params(s);
   cudaEvent_t e0 = nullptr;
@@ -248,7 +258,7 @@ vk_status enqueue_step(vk_sim* s) {
   if (s->prm.rule == VK_RULE_KNN && s->dim == 2) VK_CUDA(s, launch_knn2_step(s->g, s->b, P, s->stream));
   else if (s->prm.rule == VK_RULE_KNN) VK_CUDA(s, launch_knn_step(s->g, s->b, P, s->stream));
   else VK_CUDA(s, launch_voronoi_step(s->g, s->b, P, s->stream));
-  if ((st = record_end(s, 0, e0, s->prm.rule == VK_RULE_KNN ? 1 : 2))) return st;
+  if ((st = record_end(s, 0, e0, search_launches(s)))) return st;
   if ((st = record_begin(s, 1, &e0))) return st;
   VK_CUDA(s, launch_build(s->g, s->b, s->stream));
   if ((st = record_end(s, 1, e0, 7))) return st;
@@ -386,8 +396,8 @@ vk_status build_sim(int32_t n_rep, const int64_t* n_r, const int32_t* pos_q, con
       (e = dalloc(&s->b.U_id, N)) || (e = dalloc(&s->b.U_rank, N)) ||
       (e = dalloc(&s->b.phi_acc, 3 * (size_t)s->phi_cap * n_rep)) || (e = dalloc(&s->b.d_step, 1)) ||
       (e = dalloc(&s->b.d_status, 1)) || (e = dalloc(&s->reps_d, n_rep)) ||
-      (e = dalloc(&s->b.ovf_list, params->rule == VK_RULE_VORONOI ? N : 1)) || (e = dalloc(&s->b.ovf_count, 1)) ||
-      (e = dalloc(&s->d_stats, 4)) ||
+      (e = dalloc(&s->b.ovf_list, N)) || (e = dalloc(&s->b.ovf_count, 1)) ||
+      (e = dalloc(&s->d_stats, 6)) ||
       (e = dalloc(&s->tasks_d, s->tasks_h.size())))
     return bail(cuda_fail(s, e, "cudaMalloc"));
   if (ensure_cells_capacity(s)) return bail(VK_ERR_OOM);
@@ -678,10 +688,11 @@ vk_status vk_set_graph_steps(vk_sim* s, int32_t steps_per_graph) {
 vk_status vk_set_profiling(vk_sim* s, int32_t enable) {
   if (!s) return fail(s, VK_ERR_ARG, "sim is NULL");
   s->prof = enable != 0;
+  s->prof_counters = enable >= 2;
   drop_graph(s);  // the captured launches carry the tracing switch
   if (s->prof) {
     cudaStreamSynchronize(s->stream);
-    VK_CUDA(s, cudaMemsetAsync(s->d_stats, 0, 4 * sizeof(unsigned long long), s->stream));
+    VK_CUDA(s, cudaMemsetAsync(s->d_stats, 0, 6 * sizeof(unsigned long long), s->stream));
     for (int p = 0; p < kPhases; ++p) {
       for (auto& pr : s->ev[p]) {
         cudaEventDestroy(pr.first);
@@ -717,15 +728,17 @@ vk_status vk_get_profile(vk_sim* s, double* ms, int64_t* launches, int32_t max_p
   return VK_OK;
 }
 
-vk_status vk_get_search_stats(vk_sim* s, double* mean_candidates, double* mean_runs, int64_t* max_candidates) {
+vk_status vk_get_search_stats(vk_sim* s, double* mean_candidates, double* mean_runs, int64_t* max_candidates,
+                              double* fallback_fraction) {
   if (!s) return fail(s, VK_ERR_ARG, "sim is NULL");
-  unsigned long long h[4] = {0, 0, 0, 0};
+  unsigned long long h[6] = {0, 0, 0, 0, 0, 0};
   VK_CUDA(s, cudaMemcpyAsync(h, s->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
   VK_CUDA(s, cudaStreamSynchronize(s->stream));
   const double n = h[3] ? (double)h[3] : 1.0;
   if (mean_candidates) *mean_candidates = (double)h[0] / n;
   if (mean_runs) *mean_runs = (double)h[1] / n;
   if (max_candidates) *max_candidates = (int64_t)h[2];
+  if (fallback_fraction) *fallback_fraction = h[5] ? (double)h[4] / (double)h[5] : 0.0;
   return VK_OK;
 }
 
@@ -741,7 +754,7 @@ vk_status vk_get_info(vk_sim* s, vk_info* out) {
   out->dim = s->dim;
   out->n_cells = s->n_cells;
   out->step = s->step;
-  out->kernels_per_step = s->prm.rule == VK_RULE_KNN ? 9 : 10;
+  out->kernels_per_step = 8 + search_launches(s);
   out->rule = s->prm.rule;
   out->k = s->prm.k;
   return VK_OK;

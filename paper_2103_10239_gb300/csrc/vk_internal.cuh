@@ -57,6 +57,7 @@ struct StepParams {
   int32_t n_rep;
   int32_t phi_cap;
   unsigned long long* stats;  // tracing only: [candidates, runs, max candidates, particles]; NULL = off
+  unsigned long long* tile_stats;  // tracing: [4] particles sent to the fallback walk, [5] particles updated
 };
 
 // Tracing: add one particle's search counters to the global totals.

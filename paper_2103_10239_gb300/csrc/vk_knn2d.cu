@@ -460,6 +460,66 @@ __device__ __noinline__ void align_advect_general(const Rep& R, const StepParams
   align_advect<2>(R, P, step, id, ni, H, m, pi, pout, nout);
 }
 
+// Eq. (2) alignment + noise and Eq. (1) advection of one particle from its
+// finished top-k; writes the next state and counts the new coarse cell.
+template <int KC>
+__device__ __forceinline__ void knn2_update(const Rep& R, const StepParams& P, int64_t step, int64_t s, int2 p,
+                                            float2 nv, int32_t id, const Top<KC>& T,
+                                            const uint32_t* __restrict__ bounds, const float2* __restrict__ S_dir,
+                                            int2* __restrict__ U_pos, float2* __restrict__ U_dir,
+                                            int32_t* __restrict__ U_id, uint32_t* __restrict__ counts, float* nnew) {
+  // Eq. (2): neighbor headings in (D, id) order
+  HeadSum<2> H;
+  H.init();
+  const float ni[3] = {nv.x, nv.y, 0.f};
+  if (P.include_self) H.add(ni, P.sum_mode);
+#pragma unroll
+  for (int j = 0; j < KC; ++j) {
+    if (j >= KC - P.k) {
+      const float2 d = __ldg(S_dir + T.slot[j]);
+      const float v[2] = {d.x, d.y};
+      H.add(v, P.sum_mode);
+    }
+  }
+  const int32_t pi[3] = {p.x, p.y, 0};
+  int32_t pout[3] = {0, 0, 0};
+  const int m = P.k + (P.include_self ? 1 : 0);
+  if (P.noise == 0 && P.sum_mode != 2) {
+    // angular noise, FP32 sums (the default) inline
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)step, R.replica, 0u),
+                                  make_uint2(P.seed_lo, P.seed_hi));
+    const float u = unit24(w.x);
+    const float Sx = P.sum_mode == 1 ? __fadd_rn(H.s[0], H.c[0]) : H.s[0];
+    const float Sy = P.sum_mode == 1 ? __fadd_rn(H.s[1], H.c[1]) : H.s[1];
+    float th = (Sx == 0.f && Sy == 0.f) ? atan2f(nv.y, nv.x) : atan2f(Sy, Sx);
+    th = th + R.eta * (u - 0.5f);
+    sincosf(th, &nnew[1], &nnew[0]);
+    const float hx = P.advect_new ? nnew[0] : nv.x, hy = P.advect_new ? nnew[1] : nv.y;
+    int64_t qx = (int64_t)p.x + grid_step(R.s, hx), qy = (int64_t)p.y + grid_step(R.s, hy);
+    if (qx < 0 || qx >= (int64_t)R.L[0]) {
+      qx %= (int64_t)R.L[0];
+      if (qx < 0) qx += R.L[0];
+    }
+    if (qy < 0 || qy >= (int64_t)R.L[1]) {
+      qy %= (int64_t)R.L[1];
+      if (qy < 0) qy += R.L[1];
+    }
+    pout[0] = (int32_t)qx;
+    pout[1] = (int32_t)qy;
+  } else {
+    align_advect_general(R, P, (uint32_t)step, id, ni, H, m, pi, pout, nnew);
+  }
+  U_pos[s] = make_int2(pout[0], pout[1]);
+  U_dir[s] = make_float2(nnew[0], nnew[1]);
+  U_id[s] = id;
+  const uint32_t* bx = bounds + R.bnd[0];
+  const uint32_t* by = bounds + R.bnd[1];
+  const int ncx = cell_of_tab((uint32_t)pout[0], R.nc[0], bx, R.inv_w[0]);
+  const int ncy = cell_of_tab((uint32_t)pout[1], R.nc[1], by, R.inv_w[1]);
+  atomicAdd(counts + R.c0 + (int64_t)ncy * R.nc[0] + ncx, 1u);
+}
+
+// thread-per-particle search + update (the walk of RunGen for every particle)
 template <int KC>
 __global__ void __launch_bounds__(kBlock, 2) knn2_step_kernel(
     const Rep* __restrict__ reps, const BlockTask* __restrict__ tasks, const uint32_t* __restrict__ bounds,
@@ -485,58 +545,225 @@ __global__ void __launch_bounds__(kBlock, 2) knn2_step_kernel(
     Top<KC> T;
     top_init<KC>(T, P.k);
     knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T);
-    // Eq. (2): neighbor headings in (D, id) order
-    HeadSum<2> H;
-    H.init();
-    const float ni[3] = {nv.x, nv.y, 0.f};
-    if (P.include_self) H.add(ni, P.sum_mode);
-#pragma unroll
-    for (int j = 0; j < KC; ++j) {
-      if (j >= KC - P.k) {
-        const float2 d = __ldg(S_dir + T.slot[j]);
-        const float v[2] = {d.x, d.y};
-        H.add(v, P.sum_mode);
-      }
-    }
-    const int32_t pi[3] = {p.x, p.y, 0};
-    int32_t pout[3] = {0, 0, 0};
-    const int m = P.k + (P.include_self ? 1 : 0);
-    if (P.noise == 0 && P.sum_mode != 2) {
-      // angular noise, FP32 sums (the default) inline
-      const uint4 w = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)step, R.replica, 0u),
-                                    make_uint2(P.seed_lo, P.seed_hi));
-      const float u = unit24(w.x);
-      const float Sx = P.sum_mode == 1 ? __fadd_rn(H.s[0], H.c[0]) : H.s[0];
-      const float Sy = P.sum_mode == 1 ? __fadd_rn(H.s[1], H.c[1]) : H.s[1];
-      float th = (Sx == 0.f && Sy == 0.f) ? atan2f(nv.y, nv.x) : atan2f(Sy, Sx);
-      th = th + R.eta * (u - 0.5f);
-      sincosf(th, &nnew[1], &nnew[0]);
-      const float hx = P.advect_new ? nnew[0] : nv.x, hy = P.advect_new ? nnew[1] : nv.y;
-      int64_t qx = (int64_t)p.x + grid_step(R.s, hx), qy = (int64_t)p.y + grid_step(R.s, hy);
-      if (qx < 0 || qx >= (int64_t)R.L[0]) {
-        qx %= (int64_t)R.L[0];
-        if (qx < 0) qx += R.L[0];
-      }
-      if (qy < 0 || qy >= (int64_t)R.L[1]) {
-        qy %= (int64_t)R.L[1];
-        if (qy < 0) qy += R.L[1];
-      }
-      pout[0] = (int32_t)qx;
-      pout[1] = (int32_t)qy;
-    } else {
-      align_advect_general(R, P, (uint32_t)step, id, ni, H, m, pi, pout, nnew);
-    }
-    U_pos[s] = make_int2(pout[0], pout[1]);
-    U_dir[s] = make_float2(nnew[0], nnew[1]);
-    U_id[s] = id;
-    const uint32_t* bx = bounds + R.bnd[0];
-    const uint32_t* by = bounds + R.bnd[1];
-    const int ncx = cell_of_tab((uint32_t)pout[0], R.nc[0], bx, R.inv_w[0]);
-    const int ncy = cell_of_tab((uint32_t)pout[1], R.nc[1], by, R.inv_w[1]);
-    atomicAdd(counts + R.c0 + (int64_t)ncy * R.nc[0] + ncx, 1u);
+    knn2_update<KC>(R, P, step, s, p, nv, id, T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
   }
   record_search_stats(P.stats, li < R.n, C.n_cand, C.n_runs);
   phi_block_end<2>(phs, nnew, phi_acc + ((size_t)(step % P.phi_cap) * (size_t)P.n_rep + (size_t)t.rep) * 3);
+}
+
+// ---------------------------------------------------------------------------
+// Warp-tile search.  A warp takes 32 consecutive particles of the sorted
+// order (a compact patch of space), gathers every particle inside the box
+// "bounding box of the patch + margin" into shared memory, and every lane
+// scans the same gathered candidates (uniform loop trip counts, no walk
+// divergence).  The margin scales with the local density, 1.6 times the
+// radius that holds k particles.  A lane whose k-th best distance is not
+// provably inside the box (distance to the box boundary) is appended to the
+// fallback list and finished by knn2_fallback_kernel with the exact walk.
+// ---------------------------------------------------------------------------
+constexpr int kTileCap = 704;  // gathered candidates per warp
+
+struct TileShared {
+  int2 pos[kBlock / 32][kTileCap];   // candidate position relative to the warp's frame origin
+  int32_t slot[kBlock / 32][kTileCap];
+};
+
+// gather the slot run [qb, qe) into the warp's shared list; false on overflow
+__device__ __forceinline__ bool tile_take(TileShared& sh, int w, int lane, int& n, uint32_t qb, uint32_t qe,
+                                          const int2* __restrict__ pos, int32_t ox, int32_t oy, const Ctx& F) {
+  const int len = (int)(qe - qb);
+  if (n + len > kTileCap) return false;
+  for (int i = lane; i < len; i += 32) {
+    const int2 pj = __ldg(pos + qb + i);
+    int32_t dx = (int32_t)((uint32_t)pj.x - (uint32_t)ox);
+    int32_t dy = (int32_t)((uint32_t)pj.y - (uint32_t)oy);
+    if (dx > F.hix) dx = (int32_t)((uint32_t)dx - F.Lx);
+    else if (dx <= F.lox) dx = (int32_t)((uint32_t)dx + F.Lx);
+    if (dy > F.hiy) dy = (int32_t)((uint32_t)dy - F.Ly);
+    else if (dy <= F.loy) dy = (int32_t)((uint32_t)dy + F.Ly);
+    sh.pos[w][n + i] = make_int2(dx, dy);
+    sh.slot[w][n + i] = (int32_t)(qb + i);
+  }
+  n += len;
+  return true;
+}
+
+template <int KC>
+__global__ void __launch_bounds__(kBlock, 2) knn2_tile_kernel(
+    const Rep* __restrict__ reps, const BlockTask* __restrict__ tasks, const uint32_t* __restrict__ bounds,
+    const int2* __restrict__ S_pos, const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G,
+    int2* __restrict__ U_pos, float2* __restrict__ U_dir, int32_t* __restrict__ U_id, uint32_t* __restrict__ counts,
+    double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P, int2* __restrict__ fb_list,
+    int32_t* __restrict__ fb_count) {
+  __shared__ PhiShared phs;
+  extern __shared__ __align__(16) unsigned char tile_raw[];
+  TileShared& sh = *reinterpret_cast<TileShared*>(tile_raw);
+  phi_block_begin(phs);
+  const BlockTask t = tasks[blockIdx.x];
+  const Rep R = reps[t.rep];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int li = t.first + (int)threadIdx.x;
+  const bool valid = li < R.n;
+  const int64_t step = *d_step;
+  float nnew[3] = {0.f, 0.f, 0.f};
+  const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+  if (vmask) {
+    const int64_t s = R.p0 + (valid ? li : t.first + (w << 5));
+    const int2 p = S_pos[s];
+    // frame: minimum-image offsets from the first particle of the warp
+    Ctx F;
+    init_ctx(F, R, s, p);
+    const int32_t ox = __shfl_sync(0xffffffffu, p.x, 0), oy = __shfl_sync(0xffffffffu, p.y, 0);
+    int32_t rx = (int32_t)((uint32_t)p.x - (uint32_t)ox), ry = (int32_t)((uint32_t)p.y - (uint32_t)oy);
+    if (rx > F.hix) rx = (int32_t)((uint32_t)rx - F.Lx);
+    else if (rx <= F.lox) rx = (int32_t)((uint32_t)rx + F.Lx);
+    if (ry > F.hiy) ry = (int32_t)((uint32_t)ry - F.Ly);
+    else if (ry <= F.loy) ry = (int32_t)((uint32_t)ry + F.Ly);
+    int32_t bx0 = rx, bx1 = rx, by0 = ry, by1 = ry;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      bx0 = min(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
+      bx1 = max(bx1, __shfl_xor_sync(0xffffffffu, bx1, o));
+      by0 = min(by0, __shfl_xor_sync(0xffffffffu, by0, o));
+      by1 = max(by1, __shfl_xor_sync(0xffffffffu, by1, o));
+    }
+    // margin from the density of the frame origin's coarse cell
+    const uint32_t* bxt = bounds + R.bnd[0];
+    const uint32_t* byt = bounds + R.bnd[1];
+    const int nx = R.nc[0], ny = R.nc[1];
+    const int ocx = cell_of_tab((uint32_t)ox, nx, bxt, R.inv_w[0]);
+    const int ocy = cell_of_tab((uint32_t)oy, ny, byt, R.inv_w[1]);
+    const int64_t og = R.c0 + (int64_t)ocy * nx + ocx;
+    const float m = (float)max(__ldg(G.off + og + 1) - __ldg(G.off + og), 1u);
+    const float area = (float)(__ldg(bxt + ocx + 1) - __ldg(bxt + ocx)) * (float)(__ldg(byt + ocy + 1) - __ldg(byt + ocy));
+    const float marg = 1.6f * sqrtf((float)P.k * area / (3.14159265f * m)) + 1.0f;
+    const int64_t M = (int64_t)marg;
+    const int64_t X0 = (int64_t)bx0 - M, X1 = (int64_t)bx1 + M, Y0 = (int64_t)by0 - M, Y1 = (int64_t)by1 + M;
+    // the frame is only valid while the box plus a cell on each side stays
+    // well inside half the periodic box
+    const int64_t cwx = (int64_t)(R.L[0] / (uint32_t)nx) + 2, cwy = (int64_t)(R.L[1] / (uint32_t)ny) + 2;
+    bool tile_ok = (X1 - X0) < (int64_t)(R.L[0] / 4) && (Y1 - Y0) < (int64_t)(R.L[1] / 4) &&
+                   (X1 - X0) + 2 * cwx < (int64_t)(R.L[0] / 2) && (Y1 - Y0) + 2 * cwy < (int64_t)(R.L[1] / 2);
+    int n = 0;
+    if (tile_ok) {
+      // coarse cells overlapping the box (unwrapped indices)
+      const int64_t AX0 = (int64_t)ox + X0, AX1 = (int64_t)ox + X1, AY0 = (int64_t)oy + Y0, AY1 = (int64_t)oy + Y1;
+      auto ucell = [&](int64_t A, int nc, const uint32_t* tab, float inv, int64_t L) {
+        int64_t q = A >= 0 ? A / L : -((-A + L - 1) / L);
+        return (int)(q * nc) + cell_of_tab((uint32_t)(A - q * L), nc, tab, inv);
+      };
+      const int ux0 = ucell(AX0, nx, bxt, R.inv_w[0], R.L[0]), ux1 = ucell(AX1, nx, bxt, R.inv_w[0], R.L[0]);
+      const int uy0 = ucell(AY0, ny, byt, R.inv_w[1], R.L[1]), uy1 = ucell(AY1, ny, byt, R.inv_w[1], R.L[1]);
+      tile_ok = (ux1 - ux0 + 1 <= nx) && (uy1 - uy0 + 1 <= ny);
+      for (int ucy = uy0; tile_ok && ucy <= uy1; ++ucy) {
+        const int ay = ucy < 0 ? ucy + ny : (ucy >= ny ? ucy - ny : ucy);
+        const int64_t rowbase = R.c0 + (int64_t)ay * nx;
+        const int64_t cy0 = cell_lo_tab(ucy, ny, byt, R.L[1]) - oy;  // cell row bounds in the frame
+        const int64_t cy1 = cell_lo_tab(ucy + 1, ny, byt, R.L[1]) - oy;
+        int ucx = ux0;
+        while (tile_ok && ucx <= ux1) {
+          // contiguous actual cells [ax, ax + len)
+          const int ax = ucx < 0 ? ucx + nx : (ucx >= nx ? ucx - nx : ucx);
+          const int len = min(ux1 - ucx + 1, nx - ax);
+          const uint32_t sb0 = __ldg(G.sub_base + rowbase + ax), sb1 = __ldg(G.sub_base + rowbase + ax + len);
+          if (sb1 - sb0 == (uint32_t)len) {
+            tile_ok = tile_take(sh, w, lane, n, __ldg(G.off + rowbase + ax), __ldg(G.off + rowbase + ax + len),
+                                S_pos, ox, oy, F);
+          } else {
+            for (int j = 0; tile_ok && j < len; ++j) {
+              const int64_t g = rowbase + ax + j;
+              const uint32_t b0 = __ldg(G.sub_base + g), b1 = __ldg(G.sub_base + g + 1);
+              if (b1 - b0 == 1) {
+                tile_ok = tile_take(sh, w, lane, n, __ldg(G.off + g), __ldg(G.off + g + 1), S_pos, ox, oy, F);
+                continue;
+              }
+              const int sdiv = __ldg(G.sub_s + g);
+              const int64_t cx0 = cell_lo_tab(ucx + j, nx, bxt, R.L[0]) - ox;
+              const int64_t cw = cell_lo_tab(ucx + j + 1, nx, bxt, R.L[0]) - ox - cx0;
+              const int64_t ch = cy1 - cy0;
+              const int64_t lx = X0 - cx0, hx = X1 - cx0, ly = Y0 - cy0, hy = Y1 - cy0;
+              if (hx < 0 || lx >= cw || hy < 0 || ly >= ch) continue;
+              const int sx0 = lx <= 0 ? 0 : sub_idx(lx, cw, sdiv), sx1 = hx >= cw ? sdiv - 1 : sub_idx(hx, cw, sdiv);
+              const int sy0 = ly <= 0 ? 0 : sub_idx(ly, ch, sdiv), sy1 = hy >= ch ? sdiv - 1 : sub_idx(hy, ch, sdiv);
+              for (int yy = sy0; tile_ok && yy <= sy1; ++yy) {
+                const uint32_t rb = b0 + (uint32_t)yy * sdiv;
+                tile_ok = tile_take(sh, w, lane, n, __ldg(G.sub_off + rb + sx0), __ldg(G.sub_off + rb + sx1 + 1),
+                                    S_pos, ox, oy, F);
+              }
+            }
+          }
+          ucx += len;
+        }
+      }
+    }
+    __syncwarp();
+    bool done = false;
+    if (valid) {
+      const float2 nv = S_dir[s];
+      const int32_t id = S_id[s];
+      Top<KC> T;
+      if (tile_ok) {
+        top_init<KC>(T, P.k);
+        const int32_t qx = rx, qy = ry;
+        for (int i = 0; i < n; ++i) {
+          const int2 c = sh.pos[w][i];
+          const int32_t dx = c.x - qx, dy = c.y - qy;
+          const uint64_t D = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy);
+          if (D <= T.d[KC - 1]) {
+            const int32_t sl = sh.slot[w][i];
+            if ((int64_t)sl != s) {
+              const int32_t idj = __ldg(S_id + sl);
+              if (D < T.d[KC - 1] || idj < T.id[KC - 1]) top_insert<KC>(T, D, idj, sl);
+            }
+          }
+        }
+        // every particle outside the box is at squared distance >= B^2
+        int64_t B = min(min((int64_t)qx - X0 + 1, X1 - (int64_t)qx + 1), min((int64_t)qy - Y0 + 1, Y1 - (int64_t)qy + 1));
+        done = T.d[KC - 1] < (uint64_t)B * (uint64_t)B;
+      }
+      if (done) {
+        knn2_update<KC>(R, P, step, s, p, nv, id, T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
+      } else {
+        const int q = atomicAdd(fb_count, 1);
+        fb_list[q] = make_int2((int)s, t.rep);
+      }
+    }
+
+  }
+  phi_block_end<2>(phs, nnew, phi_acc + ((size_t)(step % P.phi_cap) * (size_t)P.n_rep + (size_t)t.rep) * 3);
+}
+
+// particles the tiles could not certify: the exact walk, one thread each
+template <int KC>
+__global__ void __launch_bounds__(kBlock, 2) knn2_fallback_kernel(
+    const Rep* __restrict__ reps, const uint32_t* __restrict__ bounds, const int2* __restrict__ S_pos,
+    const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G, int2* __restrict__ U_pos,
+    float2* __restrict__ U_dir, int32_t* __restrict__ U_id, uint32_t* __restrict__ counts,
+    double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P,
+    const int2* __restrict__ fb_list, const int32_t* __restrict__ fb_count) {
+  const int total = *fb_count;
+  const int64_t step = *d_step;
+  for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
+    const int q = base + (int)threadIdx.x;
+    float nnew[3] = {0.f, 0.f, 0.f};
+    int rep = -1;
+    if (q < total) {
+      const int2 e = fb_list[q];
+      rep = e.y;
+      const Rep R = reps[e.y];
+      const int64_t s = e.x;
+      const int2 p = S_pos[s];
+      Ctx C;
+      init_ctx(C, R, s, p);
+      Top<KC> T;
+      top_init<KC>(T, P.k);
+      knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T);
+      knn2_update<KC>(R, P, step, s, p, S_dir[s], S_id[s], T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
+      double* acc = phi_acc + ((size_t)(step % P.phi_cap) * (size_t)P.n_rep + (size_t)rep) * 3;
+      atomicAdd(acc + 0, (double)nnew[0]);
+      atomicAdd(acc + 1, (double)nnew[1]);
+    }
+  }
 }
 
 template <int KC>
@@ -571,9 +798,19 @@ GridView view_of(const Buffers& b) {
 
 template <int KC>
 cudaError_t step2(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st) {
-  knn2_step_kernel<KC><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, b.bounds, (const int2*)b.S_pos,
-                                                     (const float2*)b.S_dir, b.S_id, view_of(b), (int2*)b.U_pos,
-                                                     (float2*)b.U_dir, b.U_id, b.counts, b.phi_acc, b.d_step, P);
+  if (P.stats || !b.ovf_list) {  // tracing counts the walk of every particle
+    knn2_step_kernel<KC><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, b.bounds, (const int2*)b.S_pos,
+                                                       (const float2*)b.S_dir, b.S_id, view_of(b), (int2*)b.U_pos,
+                                                       (float2*)b.U_dir, b.U_id, b.counts, b.phi_acc, b.d_step, P);
+    return cudaGetLastError();
+  }
+  cudaFuncSetAttribute(knn2_tile_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileShared));
+  knn2_tile_kernel<KC><<<g.n_tasks, kBlock, sizeof(TileShared), st>>>(
+      g.reps, g.tasks, b.bounds, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id, view_of(b), (int2*)b.U_pos,
+      (float2*)b.U_dir, b.U_id, b.counts, b.phi_acc, b.d_step, P, b.ovf_list, b.ovf_count);
+  knn2_fallback_kernel<KC><<<152 * 2, kBlock, 0, st>>>(
+      g.reps, b.bounds, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id, view_of(b), (int2*)b.U_pos,
+      (float2*)b.U_dir, b.U_id, b.counts, b.phi_acc, b.d_step, P, b.ovf_list, b.ovf_count);
   return cudaGetLastError();
 }
 

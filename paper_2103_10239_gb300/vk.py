@@ -81,7 +81,8 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_int32)]),
     "vk_phase_name": (ctypes.c_char_p, [ctypes.c_int32]),
     "vk_get_search_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
-                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_double)]),
     "vk_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(vk_info)]),
     "vk_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.POINTER(ctypes.c_float)]),
@@ -268,8 +269,9 @@ class Sim:
     def set_graph_steps(self, n: int):
         _check(load().vk_set_graph_steps(self._h, int(n)), self._h)
 
-    def set_profiling(self, on: bool):
-        _check(load().vk_set_profiling(self._h, 1 if on else 0), self._h)
+    def set_profiling(self, on: bool, counters: bool = False):
+        level = (2 if counters else 1) if on else 0
+        _check(load().vk_set_profiling(self._h, level), self._h)
 
     def profile(self) -> dict:
         lib = load()
@@ -284,8 +286,11 @@ class Sim:
         c = ctypes.c_double(0.0)
         r = ctypes.c_double(0.0)
         m = ctypes.c_int64(0)
-        _check(load().vk_get_search_stats(self._h, ctypes.byref(c), ctypes.byref(r), ctypes.byref(m)), self._h)
-        return {"mean_candidates": c.value, "mean_runs": r.value, "max_candidates": m.value}
+        f = ctypes.c_double(0.0)
+        _check(load().vk_get_search_stats(self._h, ctypes.byref(c), ctypes.byref(r), ctypes.byref(m),
+                                          ctypes.byref(f)), self._h)
+        return {"mean_candidates": c.value, "mean_runs": r.value, "max_candidates": m.value,
+                "fallback_fraction": f.value}
 
     def autotune(self, candidates: Sequence[float], trial_steps: int = 3) -> float:
         c = np.ascontiguousarray(candidates, dtype=np.float32)

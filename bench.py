@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scenario", choices=["headline", "replicas", "voronoi", "knn3d"], default="headline",
+                    help="headline: the benchmark line; the others are secondary measurements")
     return ap.parse_args()
 
 
@@ -337,8 +339,86 @@ def run_ours(args, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# secondary scenarios (not the benchmark line): batched replicas against
+# per-replica launches, the Voronoi rule, the 3D kNN rule
+# ---------------------------------------------------------------------------
+def _timed(stream, fn):
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b)
+
+
+def run_scenario(args):
+    import torch
+    from paper_2103_10239_gb300 import vk, _build
+    from paper_2103_10239_gb300 import workloads as W
+    _build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    out = {"scenario": args.scenario, "steps": args.steps, "warmup": args.warmup, "data": "synthetic"}
+    if args.scenario == "replicas":
+        ws = W.replica_batch()
+        total = sum(w.n for w in ws)
+        sim = vk.batch_from_workloads(ws, stream=stream)
+        sim.set_graph_steps(args.steps)
+        sim.step(args.steps)  # warm-up (and graph capture)
+        ms_b = _timed(stream, lambda: sim.step(args.steps)) / args.steps
+        sim.close()
+        sims = [vk.from_workload(w, stream=stream) for w in ws]
+        for x in sims:
+            x.step(args.warmup)
+
+        def per_rep():
+            for _ in range(args.steps):
+                for x in sims:
+                    x.step(1)
+        ms_p = _timed(stream, per_rep) / args.steps
+        for x in sims:
+            x.set_graph_steps(args.steps)
+            x.step(args.steps)  # capture
+        ms_g = _timed(stream, lambda: [x.step(args.steps) for x in sims]) / args.steps
+        for x in sims:
+            x.close()
+        out.update({"metric": "particle-steps/s, 512 replicas (batched launch + multi-step graph)",
+                    "value": total / (ms_b * 1e-3), "unit": "particle-steps/s", "ms_per_step": ms_b,
+                    "per_replica_launches": {"value": total / (ms_p * 1e-3), "ms_per_step": ms_p},
+                    "per_replica_graphs": {"value": total / (ms_g * 1e-3), "ms_per_step": ms_g},
+                    "speedup_vs_per_replica_launches": ms_p / ms_b,
+                    "speedup_vs_per_replica_graphs": ms_g / ms_b,
+                    "config": {"workload": "512 replicas, N_r log-uniform [1024, 65536], k=7, F=16",
+                               "n_total": total}})
+    else:
+        if args.scenario == "voronoi":
+            w = W.voronoi_mixed(eta=0.1)
+        else:
+            w = W.knn_3d()
+        sim = vk.from_workload(w, stream=stream)
+        sim.step(args.warmup)
+        ms = _timed(stream, lambda: sim.step(args.steps)) / args.steps
+        sim.set_profiling(True)
+        sim.step(3)
+        prof = sim.profile()
+        sim.close()
+        out.update({"metric": f"particle-steps/s ({w.rule}, {w.dim}D)", "value": w.n / (ms * 1e-3),
+                    "unit": "particle-steps/s", "ms_per_step": ms,
+                    "config": {"workload": w.name, "n": w.n, "rule": w.rule, "k": w.k, "dim": w.dim},
+                    "phases_ms_per_step": {k: v[0] / 3 for k, v in prof.items() if v[1]}})
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.scenario != "headline":
+        run_scenario(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -101,7 +101,6 @@ StepParams step_params(const vk_sim* s) {
   P.n_rep = s->n_rep;
   P.phi_cap = s->phi_cap;
   P.stats = (s->prof && s->prof_counters) ? s->d_stats : nullptr;
-  P.tile_stats = s->prof ? s->d_stats : nullptr;
   return P;
 }
 
@@ -242,13 +241,9 @@ vk_status clear_phi(vk_sim* s) {
   return VK_OK;
 }
 
-// kernels of the search+update phase: the 2D kNN warp-tile kernel and its
-// fallback walk; the per-particle walk alone while search counters are on;
-// the Voronoi kernel and its overflow kernel
-int search_launches(const vk_sim* s) {
-  if (s->prm.rule == VK_RULE_KNN) return (s->dim == 2 && !(s->prof && s->prof_counters)) ? 2 : 1;
-  return 2;
-}
+// kernels of the search+update phase: one for kNN; the Voronoi kernel and
+// its overflow kernel
+int search_launches(const vk_sim* s) { return s->prm.rule == VK_RULE_KNN ? 1 : 2; }
 
 vk_status enqueue_step(vk_sim* s) {
   const StepParams P = step_params(s);
@@ -729,7 +724,7 @@ vk_status vk_get_profile(vk_sim* s, double* ms, int64_t* launches, int32_t max_p
 }
 
 vk_status vk_get_search_stats(vk_sim* s, double* mean_candidates, double* mean_runs, int64_t* max_candidates,
-                              double* fallback_fraction) {
+                              double* split_fraction) {
   if (!s) return fail(s, VK_ERR_ARG, "sim is NULL");
   unsigned long long h[6] = {0, 0, 0, 0, 0, 0};
   VK_CUDA(s, cudaMemcpyAsync(h, s->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
@@ -738,7 +733,7 @@ vk_status vk_get_search_stats(vk_sim* s, double* mean_candidates, double* mean_r
   if (mean_candidates) *mean_candidates = (double)h[0] / n;
   if (mean_runs) *mean_runs = (double)h[1] / n;
   if (max_candidates) *max_candidates = (int64_t)h[2];
-  if (fallback_fraction) *fallback_fraction = h[5] ? (double)h[4] / (double)h[5] : 0.0;
+  if (split_fraction) *split_fraction = h[3] ? (double)h[4] / (double)h[3] : 0.0;
   return VK_OK;
 }
 

@@ -56,21 +56,23 @@ struct StepParams {
   uint32_t seed_lo, seed_hi;
   int32_t n_rep;
   int32_t phi_cap;
-  unsigned long long* stats;  // tracing only: [candidates, runs, max candidates, particles]; NULL = off
-  unsigned long long* tile_stats;  // tracing: [4] particles sent to the fallback walk, [5] particles updated
+  // tracing only (NULL = off): [candidates, runs, max candidates, particles,
+  // particles whose own coarse cell is split]
+  unsigned long long* stats;
 };
 
 // Tracing: add one particle's search counters to the global totals.
 __device__ __forceinline__ void record_search_stats(unsigned long long* stats, bool valid, uint32_t cand,
-                                                    uint32_t runs) {
+                                                    uint32_t runs, bool split = false) {
   if (!stats) return;
   unsigned long long c = valid ? cand : 0, r = valid ? runs : 0, n = valid ? 1 : 0;
-  unsigned long long mx = c;
+  unsigned long long mx = c, sp = (valid && split) ? 1 : 0;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     c += __shfl_xor_sync(0xffffffffu, c, o);
     r += __shfl_xor_sync(0xffffffffu, r, o);
     n += __shfl_xor_sync(0xffffffffu, n, o);
+    sp += __shfl_xor_sync(0xffffffffu, sp, o);
     mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   }
   if ((threadIdx.x & 31) == 0 && n) {
@@ -78,6 +80,7 @@ __device__ __forceinline__ void record_search_stats(unsigned long long* stats, b
     atomicAdd(stats + 1, r);
     atomicMax(stats + 2, mx);
     atomicAdd(stats + 3, n);
+    atomicAdd(stats + 4, sp);
   }
 }
 

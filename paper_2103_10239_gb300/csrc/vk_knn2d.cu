@@ -19,10 +19,14 @@ namespace vk {
 
 namespace {
 
+// Top-k in registers: exact squared distances and sorted slots, ordered by
+// (D, id).  For k < KC the first KC-k entries are sentinels (D = 0, slot -1)
+// that order before every real candidate, so the threshold is always entry
+// KC-1 and no register array is indexed dynamically.  Ids are only read to
+// break an exact distance tie.
 template <int KC>
 struct Top {
   uint64_t d[KC];
-  int32_t id[KC];
   int32_t slot[KC];
 };
 
@@ -30,27 +34,27 @@ template <int KC>
 __device__ __forceinline__ void top_init(Top<KC>& T, int k) {
 #pragma unroll
   for (int s = 0; s < KC; ++s) {
-    const bool sentinel = s < KC - k;  // orders before every real candidate
-    T.d[s] = sentinel ? 0ull : ~0ull;
-    T.id[s] = sentinel ? INT_MIN : INT_MAX;
+    T.d[s] = s < KC - k ? 0ull : ~0ull;
     T.slot[s] = -1;
   }
 }
 
+// insert candidate slot q at squared distance D, known to order before the
+// current last entry; an exact distance tie is decided by the ids (a real
+// candidate never orders before a sentinel)
 template <int KC>
-__device__ __forceinline__ void top_insert(Top<KC>& T, uint64_t D, int32_t idj, int32_t q) {
+__device__ __forceinline__ void top_insert(Top<KC>& T, uint64_t D, int32_t q, const int32_t* __restrict__ ids) {
   bool placed = false;
 #pragma unroll
   for (int s = KC - 1; s > 0; --s) {
-    const bool before = (D < T.d[s - 1]) || (D == T.d[s - 1] && idj < T.id[s - 1]);
     if (!placed) {
+      bool before = D < T.d[s - 1];
+      if (D == T.d[s - 1]) before = T.slot[s - 1] >= 0 && __ldg(ids + q) < __ldg(ids + T.slot[s - 1]);
       if (before) {
         T.d[s] = T.d[s - 1];
-        T.id[s] = T.id[s - 1];
         T.slot[s] = T.slot[s - 1];
       } else {
         T.d[s] = D;
-        T.id[s] = idj;
         T.slot[s] = q;
         placed = true;
       }
@@ -58,7 +62,6 @@ __device__ __forceinline__ void top_insert(Top<KC>& T, uint64_t D, int32_t idj, 
   }
   if (!placed) {
     T.d[0] = D;
-    T.id[0] = idj;
     T.slot[0] = q;
   }
 }
@@ -69,6 +72,7 @@ struct Ctx {
   uint32_t Lx, Ly;
   int32_t hix, lox, hiy, loy;  // minimum image: d > hi -> d - L, d <= lo -> d + L
   uint32_t n_cand, n_runs;
+  bool split;  // the particle's own coarse cell is split (tracing)
 };
 
 template <int KC>
@@ -86,8 +90,9 @@ __device__ __forceinline__ void scan_run(Ctx& C, const int2* __restrict__ pos, c
     else if (dy <= C.loy) dy = (int32_t)((uint32_t)dy + C.Ly);
     const uint64_t D = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy);
     if (D <= T.d[KC - 1] && (int64_t)q != C.self) {
-      const int32_t idj = __ldg(ids + q);
-      if (D < T.d[KC - 1] || idj < T.id[KC - 1]) top_insert<KC>(T, D, idj, (int32_t)q);
+      // an exact tie with the current k-th best is decided by the ids
+      if (D < T.d[KC - 1] || (T.slot[KC - 1] >= 0 && __ldg(ids + q) < __ldg(ids + T.slot[KC - 1])))
+        top_insert<KC>(T, D, (int32_t)q, ids);
     }
   }
 }
@@ -424,6 +429,7 @@ __device__ __forceinline__ void knn2_search(Ctx& C, const Rep& R, const uint32_t
                                             const int32_t* __restrict__ ids, Top<KC>& T) {
   RunGen g;
   gen_init(g, R, bounds, G, C.px, C.py);
+  C.split = g.phase == 1;
   for (;;) {
     uint32_t qb = 0, qe = 0;
     const int ev = gen_next(g, T.d[KC - 1], qb, qe);
@@ -451,6 +457,7 @@ __device__ __forceinline__ void init_ctx(Ctx& C, const Rep& R, int64_t self, int
   C.loy = -(int32_t)((R.L[1] + 1) / 2);
   C.n_cand = 0;
   C.n_runs = 0;
+  C.split = false;
 }
 
 // the general update (vectorial noise, FP64 sums), kept out of line
@@ -536,6 +543,7 @@ __global__ void __launch_bounds__(kBlock, 2) knn2_step_kernel(
   Ctx C;
   C.n_cand = 0;
   C.n_runs = 0;
+  C.split = false;
   if (li < R.n) {
     const int64_t s = R.p0 + li;
     const int2 p = S_pos[s];
@@ -547,223 +555,8 @@ __global__ void __launch_bounds__(kBlock, 2) knn2_step_kernel(
     knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T);
     knn2_update<KC>(R, P, step, s, p, nv, id, T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
   }
-  record_search_stats(P.stats, li < R.n, C.n_cand, C.n_runs);
+  record_search_stats(P.stats, li < R.n, C.n_cand, C.n_runs, C.split);
   phi_block_end<2>(phs, nnew, phi_acc + ((size_t)(step % P.phi_cap) * (size_t)P.n_rep + (size_t)t.rep) * 3);
-}
-
-// ---------------------------------------------------------------------------
-// Warp-tile search.  A warp takes 32 consecutive particles of the sorted
-// order (a compact patch of space), gathers every particle inside the box
-// "bounding box of the patch + margin" into shared memory, and every lane
-// scans the same gathered candidates (uniform loop trip counts, no walk
-// divergence).  The margin scales with the local density, 1.6 times the
-// radius that holds k particles.  A lane whose k-th best distance is not
-// provably inside the box (distance to the box boundary) is appended to the
-// fallback list and finished by knn2_fallback_kernel with the exact walk.
-// ---------------------------------------------------------------------------
-constexpr int kTileCap = 704;  // gathered candidates per warp
-
-struct TileShared {
-  int2 pos[kBlock / 32][kTileCap];   // candidate position relative to the warp's frame origin
-  int32_t slot[kBlock / 32][kTileCap];
-};
-
-// gather the slot run [qb, qe) into the warp's shared list; false on overflow
-__device__ __forceinline__ bool tile_take(TileShared& sh, int w, int lane, int& n, uint32_t qb, uint32_t qe,
-                                          const int2* __restrict__ pos, int32_t ox, int32_t oy, const Ctx& F) {
-  const int len = (int)(qe - qb);
-  if (n + len > kTileCap) return false;
-  for (int i = lane; i < len; i += 32) {
-    const int2 pj = __ldg(pos + qb + i);
-    int32_t dx = (int32_t)((uint32_t)pj.x - (uint32_t)ox);
-    int32_t dy = (int32_t)((uint32_t)pj.y - (uint32_t)oy);
-    if (dx > F.hix) dx = (int32_t)((uint32_t)dx - F.Lx);
-    else if (dx <= F.lox) dx = (int32_t)((uint32_t)dx + F.Lx);
-    if (dy > F.hiy) dy = (int32_t)((uint32_t)dy - F.Ly);
-    else if (dy <= F.loy) dy = (int32_t)((uint32_t)dy + F.Ly);
-    sh.pos[w][n + i] = make_int2(dx, dy);
-    sh.slot[w][n + i] = (int32_t)(qb + i);
-  }
-  n += len;
-  return true;
-}
-
-template <int KC>
-__global__ void __launch_bounds__(kBlock, 2) knn2_tile_kernel(
-    const Rep* __restrict__ reps, const BlockTask* __restrict__ tasks, const uint32_t* __restrict__ bounds,
-    const int2* __restrict__ S_pos, const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G,
-    int2* __restrict__ U_pos, float2* __restrict__ U_dir, int32_t* __restrict__ U_id, uint32_t* __restrict__ counts,
-    double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P, int2* __restrict__ fb_list,
-    int32_t* __restrict__ fb_count) {
-  __shared__ PhiShared phs;
-  extern __shared__ __align__(16) unsigned char tile_raw[];
-  TileShared& sh = *reinterpret_cast<TileShared*>(tile_raw);
-  phi_block_begin(phs);
-  const BlockTask t = tasks[blockIdx.x];
-  const Rep R = reps[t.rep];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int li = t.first + (int)threadIdx.x;
-  const bool valid = li < R.n;
-  const int64_t step = *d_step;
-  float nnew[3] = {0.f, 0.f, 0.f};
-  const unsigned vmask = __ballot_sync(0xffffffffu, valid);
-  if (vmask) {
-    const int64_t s = R.p0 + (valid ? li : t.first + (w << 5));
-    const int2 p = S_pos[s];
-    // frame: minimum-image offsets from the first particle of the warp
-    Ctx F;
-    init_ctx(F, R, s, p);
-    const int32_t ox = __shfl_sync(0xffffffffu, p.x, 0), oy = __shfl_sync(0xffffffffu, p.y, 0);
-    int32_t rx = (int32_t)((uint32_t)p.x - (uint32_t)ox), ry = (int32_t)((uint32_t)p.y - (uint32_t)oy);
-    if (rx > F.hix) rx = (int32_t)((uint32_t)rx - F.Lx);
-    else if (rx <= F.lox) rx = (int32_t)((uint32_t)rx + F.Lx);
-    if (ry > F.hiy) ry = (int32_t)((uint32_t)ry - F.Ly);
-    else if (ry <= F.loy) ry = (int32_t)((uint32_t)ry + F.Ly);
-    int32_t bx0 = rx, bx1 = rx, by0 = ry, by1 = ry;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      bx0 = min(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
-      bx1 = max(bx1, __shfl_xor_sync(0xffffffffu, bx1, o));
-      by0 = min(by0, __shfl_xor_sync(0xffffffffu, by0, o));
-      by1 = max(by1, __shfl_xor_sync(0xffffffffu, by1, o));
-    }
-    // margin from the density of the frame origin's coarse cell
-    const uint32_t* bxt = bounds + R.bnd[0];
-    const uint32_t* byt = bounds + R.bnd[1];
-    const int nx = R.nc[0], ny = R.nc[1];
-    const int ocx = cell_of_tab((uint32_t)ox, nx, bxt, R.inv_w[0]);
-    const int ocy = cell_of_tab((uint32_t)oy, ny, byt, R.inv_w[1]);
-    const int64_t og = R.c0 + (int64_t)ocy * nx + ocx;
-    const float m = (float)max(__ldg(G.off + og + 1) - __ldg(G.off + og), 1u);
-    const float area = (float)(__ldg(bxt + ocx + 1) - __ldg(bxt + ocx)) * (float)(__ldg(byt + ocy + 1) - __ldg(byt + ocy));
-    const float marg = 1.6f * sqrtf((float)P.k * area / (3.14159265f * m)) + 1.0f;
-    const int64_t M = (int64_t)marg;
-    const int64_t X0 = (int64_t)bx0 - M, X1 = (int64_t)bx1 + M, Y0 = (int64_t)by0 - M, Y1 = (int64_t)by1 + M;
-    // the frame is only valid while the box plus a cell on each side stays
-    // well inside half the periodic box
-    const int64_t cwx = (int64_t)(R.L[0] / (uint32_t)nx) + 2, cwy = (int64_t)(R.L[1] / (uint32_t)ny) + 2;
-    bool tile_ok = (X1 - X0) < (int64_t)(R.L[0] / 4) && (Y1 - Y0) < (int64_t)(R.L[1] / 4) &&
-                   (X1 - X0) + 2 * cwx < (int64_t)(R.L[0] / 2) && (Y1 - Y0) + 2 * cwy < (int64_t)(R.L[1] / 2);
-    int n = 0;
-    if (tile_ok) {
-      // coarse cells overlapping the box (unwrapped indices)
-      const int64_t AX0 = (int64_t)ox + X0, AX1 = (int64_t)ox + X1, AY0 = (int64_t)oy + Y0, AY1 = (int64_t)oy + Y1;
-      auto ucell = [&](int64_t A, int nc, const uint32_t* tab, float inv, int64_t L) {
-        int64_t q = A >= 0 ? A / L : -((-A + L - 1) / L);
-        return (int)(q * nc) + cell_of_tab((uint32_t)(A - q * L), nc, tab, inv);
-      };
-      const int ux0 = ucell(AX0, nx, bxt, R.inv_w[0], R.L[0]), ux1 = ucell(AX1, nx, bxt, R.inv_w[0], R.L[0]);
-      const int uy0 = ucell(AY0, ny, byt, R.inv_w[1], R.L[1]), uy1 = ucell(AY1, ny, byt, R.inv_w[1], R.L[1]);
-      tile_ok = (ux1 - ux0 + 1 <= nx) && (uy1 - uy0 + 1 <= ny);
-      for (int ucy = uy0; tile_ok && ucy <= uy1; ++ucy) {
-        const int ay = ucy < 0 ? ucy + ny : (ucy >= ny ? ucy - ny : ucy);
-        const int64_t rowbase = R.c0 + (int64_t)ay * nx;
-        const int64_t cy0 = cell_lo_tab(ucy, ny, byt, R.L[1]) - oy;  // cell row bounds in the frame
-        const int64_t cy1 = cell_lo_tab(ucy + 1, ny, byt, R.L[1]) - oy;
-        int ucx = ux0;
-        while (tile_ok && ucx <= ux1) {
-          // contiguous actual cells [ax, ax + len)
-          const int ax = ucx < 0 ? ucx + nx : (ucx >= nx ? ucx - nx : ucx);
-          const int len = min(ux1 - ucx + 1, nx - ax);
-          const uint32_t sb0 = __ldg(G.sub_base + rowbase + ax), sb1 = __ldg(G.sub_base + rowbase + ax + len);
-          if (sb1 - sb0 == (uint32_t)len) {
-            tile_ok = tile_take(sh, w, lane, n, __ldg(G.off + rowbase + ax), __ldg(G.off + rowbase + ax + len),
-                                S_pos, ox, oy, F);
-          } else {
-            for (int j = 0; tile_ok && j < len; ++j) {
-              const int64_t g = rowbase + ax + j;
-              const uint32_t b0 = __ldg(G.sub_base + g), b1 = __ldg(G.sub_base + g + 1);
-              if (b1 - b0 == 1) {
-                tile_ok = tile_take(sh, w, lane, n, __ldg(G.off + g), __ldg(G.off + g + 1), S_pos, ox, oy, F);
-                continue;
-              }
-              const int sdiv = __ldg(G.sub_s + g);
-              const int64_t cx0 = cell_lo_tab(ucx + j, nx, bxt, R.L[0]) - ox;
-              const int64_t cw = cell_lo_tab(ucx + j + 1, nx, bxt, R.L[0]) - ox - cx0;
-              const int64_t ch = cy1 - cy0;
-              const int64_t lx = X0 - cx0, hx = X1 - cx0, ly = Y0 - cy0, hy = Y1 - cy0;
-              if (hx < 0 || lx >= cw || hy < 0 || ly >= ch) continue;
-              const int sx0 = lx <= 0 ? 0 : sub_idx(lx, cw, sdiv), sx1 = hx >= cw ? sdiv - 1 : sub_idx(hx, cw, sdiv);
-              const int sy0 = ly <= 0 ? 0 : sub_idx(ly, ch, sdiv), sy1 = hy >= ch ? sdiv - 1 : sub_idx(hy, ch, sdiv);
-              for (int yy = sy0; tile_ok && yy <= sy1; ++yy) {
-                const uint32_t rb = b0 + (uint32_t)yy * sdiv;
-                tile_ok = tile_take(sh, w, lane, n, __ldg(G.sub_off + rb + sx0), __ldg(G.sub_off + rb + sx1 + 1),
-                                    S_pos, ox, oy, F);
-              }
-            }
-          }
-          ucx += len;
-        }
-      }
-    }
-    __syncwarp();
-    bool done = false;
-    if (valid) {
-      const float2 nv = S_dir[s];
-      const int32_t id = S_id[s];
-      Top<KC> T;
-      if (tile_ok) {
-        top_init<KC>(T, P.k);
-        const int32_t qx = rx, qy = ry;
-        for (int i = 0; i < n; ++i) {
-          const int2 c = sh.pos[w][i];
-          const int32_t dx = c.x - qx, dy = c.y - qy;
-          const uint64_t D = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy);
-          if (D <= T.d[KC - 1]) {
-            const int32_t sl = sh.slot[w][i];
-            if ((int64_t)sl != s) {
-              const int32_t idj = __ldg(S_id + sl);
-              if (D < T.d[KC - 1] || idj < T.id[KC - 1]) top_insert<KC>(T, D, idj, sl);
-            }
-          }
-        }
-        // every particle outside the box is at squared distance >= B^2
-        int64_t B = min(min((int64_t)qx - X0 + 1, X1 - (int64_t)qx + 1), min((int64_t)qy - Y0 + 1, Y1 - (int64_t)qy + 1));
-        done = T.d[KC - 1] < (uint64_t)B * (uint64_t)B;
-      }
-      if (done) {
-        knn2_update<KC>(R, P, step, s, p, nv, id, T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
-      } else {
-        const int q = atomicAdd(fb_count, 1);
-        fb_list[q] = make_int2((int)s, t.rep);
-      }
-    }
-
-  }
-  phi_block_end<2>(phs, nnew, phi_acc + ((size_t)(step % P.phi_cap) * (size_t)P.n_rep + (size_t)t.rep) * 3);
-}
-
-// particles the tiles could not certify: the exact walk, one thread each
-template <int KC>
-__global__ void __launch_bounds__(kBlock, 2) knn2_fallback_kernel(
-    const Rep* __restrict__ reps, const uint32_t* __restrict__ bounds, const int2* __restrict__ S_pos,
-    const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G, int2* __restrict__ U_pos,
-    float2* __restrict__ U_dir, int32_t* __restrict__ U_id, uint32_t* __restrict__ counts,
-    double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P,
-    const int2* __restrict__ fb_list, const int32_t* __restrict__ fb_count) {
-  const int total = *fb_count;
-  const int64_t step = *d_step;
-  for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
-    const int q = base + (int)threadIdx.x;
-    float nnew[3] = {0.f, 0.f, 0.f};
-    int rep = -1;
-    if (q < total) {
-      const int2 e = fb_list[q];
-      rep = e.y;
-      const Rep R = reps[e.y];
-      const int64_t s = e.x;
-      const int2 p = S_pos[s];
-      Ctx C;
-      init_ctx(C, R, s, p);
-      Top<KC> T;
-      top_init<KC>(T, P.k);
-      knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T);
-      knn2_update<KC>(R, P, step, s, p, S_dir[s], S_id[s], T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
-      double* acc = phi_acc + ((size_t)(step % P.phi_cap) * (size_t)P.n_rep + (size_t)rep) * 3;
-      atomicAdd(acc + 0, (double)nnew[0]);
-      atomicAdd(acc + 1, (double)nnew[1]);
-    }
-  }
 }
 
 template <int KC>
@@ -784,7 +577,7 @@ __global__ void __launch_bounds__(kBlock, 2) knn2_export_kernel(const Rep* __res
   const int32_t id = S_id[s];
 #pragma unroll
   for (int j = 0; j < KC; ++j)
-    if (j >= KC - k) out[(int64_t)id * k + (j - (KC - k))] = T.id[j];
+    if (j >= KC - k) out[(int64_t)id * k + (j - (KC - k))] = __ldg(S_id + T.slot[j]);
 }
 
 GridView view_of(const Buffers& b) {
@@ -798,19 +591,9 @@ GridView view_of(const Buffers& b) {
 
 template <int KC>
 cudaError_t step2(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st) {
-  if (P.stats || !b.ovf_list) {  // tracing counts the walk of every particle
-    knn2_step_kernel<KC><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, b.bounds, (const int2*)b.S_pos,
-                                                       (const float2*)b.S_dir, b.S_id, view_of(b), (int2*)b.U_pos,
-                                                       (float2*)b.U_dir, b.U_id, b.counts, b.phi_acc, b.d_step, P);
-    return cudaGetLastError();
-  }
-  cudaFuncSetAttribute(knn2_tile_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileShared));
-  knn2_tile_kernel<KC><<<g.n_tasks, kBlock, sizeof(TileShared), st>>>(
-      g.reps, g.tasks, b.bounds, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id, view_of(b), (int2*)b.U_pos,
-      (float2*)b.U_dir, b.U_id, b.counts, b.phi_acc, b.d_step, P, b.ovf_list, b.ovf_count);
-  knn2_fallback_kernel<KC><<<152 * 2, kBlock, 0, st>>>(
-      g.reps, b.bounds, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id, view_of(b), (int2*)b.U_pos,
-      (float2*)b.U_dir, b.U_id, b.counts, b.phi_acc, b.d_step, P, b.ovf_list, b.ovf_count);
+  knn2_step_kernel<KC><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, b.bounds, (const int2*)b.S_pos,
+                                                     (const float2*)b.S_dir, b.S_id, view_of(b), (int2*)b.U_pos,
+                                                     (float2*)b.U_dir, b.U_id, b.counts, b.phi_acc, b.d_step, P);
   return cudaGetLastError();
 }
 

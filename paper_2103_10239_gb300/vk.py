@@ -290,7 +290,7 @@ class Sim:
         _check(load().vk_get_search_stats(self._h, ctypes.byref(c), ctypes.byref(r), ctypes.byref(m),
                                           ctypes.byref(f)), self._h)
         return {"mean_candidates": c.value, "mean_runs": r.value, "max_candidates": m.value,
-                "fallback_fraction": f.value}
+                "split_fraction": f.value}
 
     def autotune(self, candidates: Sequence[float], trial_steps: int = 3) -> float:
         c = np.ascontiguousarray(candidates, dtype=np.float32)

@@ -110,7 +110,7 @@ def test_profiling_counts_phases():
         sim.set_profiling(True)
         sim.step(5)
         prof = sim.profile()
-    assert prof["search_update"][1] == 10 and prof["build"][1] == 35 and prof["scatter"][1] == 5
+    assert prof["search_update"][1] == 5 and prof["build"][1] == 35 and prof["scatter"][1] == 5
     assert prof["search_update"][0] > 0
 
 

@@ -15,6 +15,11 @@
 
 #include "vk_internal.cuh"
 
+// resident 256-thread blocks per SM the step kernel is compiled for (register budget)
+#ifndef VK_KNN2_MIN_BLOCKS
+#define VK_KNN2_MIN_BLOCKS 4
+#endif
+
 namespace vk {
 
 namespace {
@@ -528,7 +533,7 @@ __device__ __forceinline__ void knn2_update(const Rep& R, const StepParams& P, i
 
 // thread-per-particle search + update (the walk of RunGen for every particle)
 template <int KC>
-__global__ void __launch_bounds__(kBlock, 2) knn2_step_kernel(
+__global__ void __launch_bounds__(kBlock, VK_KNN2_MIN_BLOCKS) knn2_step_kernel(
     const Rep* __restrict__ reps, const BlockTask* __restrict__ tasks, const uint32_t* __restrict__ bounds,
     const int2* __restrict__ S_pos, const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G,
     int2* __restrict__ U_pos, float2* __restrict__ U_dir, int32_t* __restrict__ U_id, uint32_t* __restrict__ counts,

@@ -167,8 +167,7 @@ vk_status vk_set_graph_steps(vk_sim* sim, int32_t steps_per_graph);
 
 /* Tracing: when enabled (1), vk_step launches kernels directly (no graph) and
  * brackets every kernel phase with CUDA events on the sim's stream; level 2
- * also collects the search counters of vk_get_search_stats (the kNN search
- * then runs its per-particle walk for every particle, to count it).
+ * also collects the search counters of vk_get_search_stats.
  * vk_get_profile returns, per phase, the summed event time in ms and the
  * launch count since profiling was enabled, plus the phase names. */
 vk_status vk_set_profiling(vk_sim* sim, int32_t enable);
@@ -176,14 +175,14 @@ vk_status vk_get_profile(vk_sim* sim, double* ms, int64_t* launches, int32_t max
                          int32_t* n_phases);
 const char* vk_phase_name(int32_t phase);
 
-/* Search counters of the neighbor search while tracing was on.  At level 2:
- * mean candidates examined per particle, mean contiguous slot runs visited per
- * particle, and the largest candidate count of one particle (per-particle
- * walk).  At level 1 or 2 (2D kNN): the fraction of particle updates that the
- * warp-tile search could not certify and handed to the per-particle walk.
- * Any output may be NULL. */
+/* Search counters of the neighbor search while tracing was on (level 2):
+ * mean candidates examined per particle update, mean contiguous slot runs
+ * read per particle update, the largest candidate count of one particle, the
+ * fraction of 2D kNN particle updates that the warp-cooperative search handed
+ * to the per-particle walk, and the fraction of particle updates whose own
+ * coarse cell was split into sub-cells.  Any output may be NULL. */
 vk_status vk_get_search_stats(vk_sim* sim, double* mean_candidates, double* mean_runs,
-                              int64_t* max_candidates, double* fallback_fraction);
+                              int64_t* max_candidates, double* walk_fraction, double* split_fraction);
 
 /* Sizes chosen at init: total particles, replicas, cells of the search grid. */
 typedef struct {

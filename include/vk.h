@@ -177,12 +177,11 @@ const char* vk_phase_name(int32_t phase);
 
 /* Search counters of the neighbor search while tracing was on (level 2):
  * mean candidates examined per particle update, mean contiguous slot runs
- * read per particle update, the largest candidate count of one particle, the
- * fraction of 2D kNN particle updates that the warp-cooperative search handed
- * to the per-particle walk, and the fraction of particle updates whose own
- * coarse cell was split into sub-cells.  Any output may be NULL. */
+ * read per particle update, the largest candidate count of one particle, and
+ * the fraction of particle updates whose own coarse cell was split into
+ * sub-cells.  Any output may be NULL. */
 vk_status vk_get_search_stats(vk_sim* sim, double* mean_candidates, double* mean_runs,
-                              int64_t* max_candidates, double* walk_fraction, double* split_fraction);
+                              int64_t* max_candidates, double* split_fraction);
 
 /* Sizes chosen at init: total particles, replicas, cells of the search grid. */
 typedef struct {

@@ -724,7 +724,7 @@ vk_status vk_get_profile(vk_sim* s, double* ms, int64_t* launches, int32_t max_p
 }
 
 vk_status vk_get_search_stats(vk_sim* s, double* mean_candidates, double* mean_runs, int64_t* max_candidates,
-                              double* walk_fraction, double* split_fraction) {
+                              double* split_fraction) {
   if (!s) return fail(s, VK_ERR_ARG, "sim is NULL");
   unsigned long long h[6] = {0, 0, 0, 0, 0, 0};
   VK_CUDA(s, cudaMemcpyAsync(h, s->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
@@ -733,8 +733,7 @@ vk_status vk_get_search_stats(vk_sim* s, double* mean_candidates, double* mean_r
   if (mean_candidates) *mean_candidates = (double)h[0] / n;
   if (mean_runs) *mean_runs = (double)h[1] / n;
   if (max_candidates) *max_candidates = (int64_t)h[2];
-  if (walk_fraction) *walk_fraction = (double)h[5] / n;
-  if (split_fraction) *split_fraction = (double)h[4] / n;
+  if (split_fraction) *split_fraction = h[3] ? (double)h[4] / (double)h[3] : 0.0;
   return VK_OK;
 }
 

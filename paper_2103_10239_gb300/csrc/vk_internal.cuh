@@ -57,24 +57,22 @@ struct StepParams {
   int32_t n_rep;
   int32_t phi_cap;
   // tracing only (NULL = off): [candidates, runs, max candidates, particles,
-  // particles whose own coarse cell is split, particles handed to the
-  // per-particle walk]
+  // particles whose own coarse cell is split]
   unsigned long long* stats;
 };
 
 // Tracing: add one particle's search counters to the global totals.
 __device__ __forceinline__ void record_search_stats(unsigned long long* stats, bool valid, uint32_t cand,
-                                                    uint32_t runs, bool split = false, bool walked = false) {
+                                                    uint32_t runs, bool split = false) {
   if (!stats) return;
   unsigned long long c = valid ? cand : 0, r = valid ? runs : 0, n = valid ? 1 : 0;
-  unsigned long long mx = c, sp = (valid && split) ? 1 : 0, fb = (valid && walked) ? 1 : 0;
+  unsigned long long mx = c, sp = (valid && split) ? 1 : 0;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     c += __shfl_xor_sync(0xffffffffu, c, o);
     r += __shfl_xor_sync(0xffffffffu, r, o);
     n += __shfl_xor_sync(0xffffffffu, n, o);
     sp += __shfl_xor_sync(0xffffffffu, sp, o);
-    fb += __shfl_xor_sync(0xffffffffu, fb, o);
     mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   }
   if ((threadIdx.x & 31) == 0 && n) {
@@ -83,7 +81,6 @@ __device__ __forceinline__ void record_search_stats(unsigned long long* stats, b
     atomicMax(stats + 2, mx);
     atomicAdd(stats + 3, n);
     atomicAdd(stats + 4, sp);
-    atomicAdd(stats + 5, fb);
   }
 }
 

@@ -80,33 +80,26 @@ struct Ctx {
   bool split;  // the particle's own coarse cell is split (tracing)
 };
 
-__device__ __forceinline__ int32_t min_image32(int32_t d, int32_t hi, int32_t lo, uint32_t L) {
-  if (d > hi) d = (int32_t)((uint32_t)d - L);
-  else if (d <= lo) d = (int32_t)((uint32_t)d + L);
-  return d;
-}
-
-// candidate slot q into the exact top-k; an exact tie with the current k-th
-// best is decided by the ids
-template <int KC>
-__device__ __forceinline__ void consider(const Ctx& C, const int2* __restrict__ pos, const int32_t* __restrict__ ids,
-                                         uint32_t q, Top<KC>& T) {
-  const int2 pj = __ldg(pos + q);
-  const int32_t dx = min_image32((int32_t)((uint32_t)pj.x - C.px), C.hix, C.lox, C.Lx);
-  const int32_t dy = min_image32((int32_t)((uint32_t)pj.y - C.py), C.hiy, C.loy, C.Ly);
-  const uint64_t D = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy);
-  if (D <= T.d[KC - 1] && (int64_t)q != C.self) {
-    if (D < T.d[KC - 1] || (T.slot[KC - 1] >= 0 && __ldg(ids + q) < __ldg(ids + T.slot[KC - 1])))
-      top_insert<KC>(T, D, (int32_t)q, ids);
-  }
-}
-
 template <int KC>
 __device__ __forceinline__ void scan_run(Ctx& C, const int2* __restrict__ pos, const int32_t* __restrict__ ids,
                                          uint32_t qb, uint32_t qe, Top<KC>& T) {
   C.n_cand += qe - qb;
   C.n_runs += 1;
-  for (uint32_t q = qb; q < qe; ++q) consider<KC>(C, pos, ids, q, T);
+  for (uint32_t q = qb; q < qe; ++q) {
+    const int2 pj = __ldg(pos + q);
+    int32_t dx = (int32_t)((uint32_t)pj.x - C.px);
+    int32_t dy = (int32_t)((uint32_t)pj.y - C.py);
+    if (dx > C.hix) dx = (int32_t)((uint32_t)dx - C.Lx);
+    else if (dx <= C.lox) dx = (int32_t)((uint32_t)dx + C.Lx);
+    if (dy > C.hiy) dy = (int32_t)((uint32_t)dy - C.Ly);
+    else if (dy <= C.loy) dy = (int32_t)((uint32_t)dy + C.Ly);
+    const uint64_t D = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy);
+    if (D <= T.d[KC - 1] && (int64_t)q != C.self) {
+      // an exact tie with the current k-th best is decided by the ids
+      if (D < T.d[KC - 1] || (T.slot[KC - 1] >= 0 && __ldg(ids + q) < __ldg(ids + T.slot[KC - 1])))
+        top_insert<KC>(T, D, (int32_t)q, ids);
+    }
+  }
 }
 
 // sub-cell index of offset u (0 <= u < w) in a cell of width w split s ways:
@@ -457,280 +450,6 @@ __device__ __forceinline__ void knn2_search(Ctx& C, const Rep& R, const uint32_t
   }
 }
 
-// ---------------------------------------------------------------------------
-// Warp-cooperative search (the default of the step and export kernels).
-//
-// The 32 queries of a warp are consecutive in the cell-sorted order, hence
-// close together.  The warp
-//  1. bounds each query's k-th neighbor distance by its k-th nearest among a
-//     window of 32 consecutive particles that contains the queries (the
-//     "mates"): any k other particles bound the k-th nearest distance;
-//  2. stages in shared memory, with coalesced reads, every particle of the
-//     grid cells (sub-cells of split cells) that meet the queries' bounding
-//     box widened by the largest bound, as FP32 offsets from one origin;
-//  3. lets every lane scan all staged candidates in lockstep and keep the
-//     slots whose FP32 squared distance is within a threshold that provably
-//     holds all of the exact k nearest (the FP32 error is bounded from the
-//     magnitude of the offsets), and
-//  4. orders the few kept slots by the exact (int64 D, id) key.
-// A lane whose kept list overflows, and every lane of a warp whose box is
-// wider than half the period or meets too many coarse cells, uses the
-// per-particle walk (knn2_search) instead.  Both give the same result.
-// ---------------------------------------------------------------------------
-constexpr int kStage = 128;       // candidates staged per round
-constexpr int kKeep = 24;         // kept slots per query
-constexpr int kMaxBoxCells = 64;  // coarse cells one warp box may meet
-
-struct WarpStage {
-  float2 mate[32];
-  float2 cpos[kStage];
-  int32_t cslot[kStage];
-  int32_t keep[kKeep][32];  // [entry][lane]: conflict-free appends
-};
-
-// ascending sorting-network insert that keeps the KC smallest values
-template <int KC>
-__device__ __forceinline__ void net_insert(float (&d)[KC], float x) {
-#pragma unroll
-  for (int j = 0; j < KC; ++j) {
-    const float lo = fminf(d[j], x);
-    x = fmaxf(d[j], x);
-    d[j] = lo;
-  }
-}
-
-// FP32 squared distance of offsets a and (qx, qy).  For offsets of magnitude
-// <= E (so differences <= 2E) the error against the exact squared distance is
-// below 50 * 2^-24 * E^2 (rounding of the offsets, the differences, the
-// product and the fused add); the callers use 2^-17 * E^2.
-__device__ __forceinline__ float fsq_dist(float2 a, float qx, float qy) {
-  const float dx = __fsub_rn(a.x, qx), dy = __fsub_rn(a.y, qy);
-  return __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
-}
-
-// unwrapped cell index of an unwrapped coordinate X, -L <= X < 2L
-__device__ __forceinline__ int ucell_of(int64_t X, int n, const uint32_t* __restrict__ bnd, float inv_w, int64_t L) {
-  int w = 0;
-  if (X < 0) {
-    X += L;
-    w = -n;
-  } else if (X >= L) {
-    X -= L;
-    w = n;
-  }
-  return w + cell_of_tab((uint32_t)X, n, bnd, inv_w);
-}
-
-// step 3 over the staged candidates [0, nst)
-__device__ __forceinline__ void scan_stage(WarpStage& W, int nst, float qx, float qy, float thr, int lane, int& cnt) {
-  __syncwarp();
-  for (int c = 0; c < nst; ++c) {
-    if (fsq_dist(W.cpos[c], qx, qy) <= thr) {
-      if (cnt < kKeep) W.keep[cnt][lane] = W.cslot[c];
-      ++cnt;
-    }
-  }
-  __syncwarp();
-}
-
-// All 32 lanes call this together, for a warp whose first query (local index
-// wli0) exists.  Valid lanes (wli0 + lane < R.n) have C set up by init_ctx and
-// T initialised.  Returns true for a valid lane that must use the walk.
-template <int KC>
-__device__ __forceinline__ bool knn2_warp_search(WarpStage& W, const Rep& R, const uint32_t* __restrict__ bounds,
-                                                 const GridView& G, const int2* __restrict__ pos,
-                                                 const int32_t* __restrict__ ids, int wli0, int k, Ctx& C,
-                                                 Top<KC>& T) {
-  constexpr unsigned kAll = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const int n = R.n;
-  const bool valid = wli0 + lane < n;
-  const uint32_t Lx = R.L[0], Ly = R.L[1];
-  const int32_t hix = (int32_t)(Lx / 2), lox = -(int32_t)((Lx + 1) / 2);
-  const int32_t hiy = (int32_t)(Ly / 2), loy = -(int32_t)((Ly + 1) / 2);
-  // the mate window [m0, m0 + nm) holds the queries [wli0, wli0 + 32) ∩ [0, n)
-  const int nm = min(32, n);
-  const int m0 = min(wli0, n - nm);
-  const int64_t ms0 = R.p0 + m0;
-  const int qm = (wli0 - m0 + lane) & 31;  // a valid query's index in the window
-  const int2 o = __ldg(pos + ms0);         // origin of the offsets
-  int32_t rx = 0, ry = 0;
-  if (lane < nm) {
-    const int2 p = __ldg(pos + ms0 + lane);
-    rx = min_image32((int32_t)((uint32_t)p.x - (uint32_t)o.x), hix, lox, Lx);
-    ry = min_image32((int32_t)((uint32_t)p.y - (uint32_t)o.y), hiy, loy, Ly);
-    W.mate[lane] = make_float2((float)rx, (float)ry);
-  }
-  const int32_t qx = __shfl_sync(kAll, rx, qm), qy = __shfl_sync(kAll, ry, qm);
-  const int32_t bx0 = __reduce_min_sync(kAll, valid ? qx : INT_MAX);
-  const int32_t bx1 = __reduce_max_sync(kAll, valid ? qx : INT_MIN);
-  const int32_t by0 = __reduce_min_sync(kAll, valid ? qy : INT_MAX);
-  const int32_t by1 = __reduce_max_sync(kAll, valid ? qy : INT_MIN);
-  const uint32_t em = __reduce_max_sync(kAll, (uint32_t)max(abs(rx), abs(ry)));
-  __syncwarp();
-
-  // 1. k-th nearest mate (FP32), then an integer radius that bounds the
-  // exact k-th neighbor distance
-  const float qxf = (float)qx, qyf = (float)qy;
-  float d[KC];
-#pragma unroll
-  for (int j = 0; j < KC; ++j) d[j] = __int_as_float(0x7f800000);
-  for (int j = 0; j < nm; ++j) {
-    const float Df = fsq_dist(W.mate[j], qxf, qyf);
-    net_insert<KC>(d, j == qm ? __int_as_float(0x7f800000) : Df);
-  }
-  float tau = d[0];
-#pragma unroll
-  for (int j = 1; j < KC; ++j)
-    if (j == k - 1) tau = d[j];
-  const float emf = (float)em;
-  const float delta0 = __fmul_ru(__fmul_ru(emf, emf), 0x1p-17f);
-  uint32_t Ri = 0;
-  if (valid) {
-    const float r = __fsqrt_ru(__fmul_ru(__fadd_ru(tau, delta0), 1.000002f));
-    Ri = r < 1.0e9f ? (uint32_t)ceilf(r) + 1u : 0x7fffffffu;
-  }
-  const uint32_t Rw = __reduce_max_sync(kAll, Ri);
-
-  // 2. the box [b0 - Rw, b1 + Rw] in offsets; it must stay inside one
-  // period's half so that offsets give minimum-image distances
-  const int64_t lx = (int64_t)bx0 - Rw, hx = (int64_t)bx1 + Rw;
-  const int64_t ly = (int64_t)by0 - Rw, hy = (int64_t)by1 + Rw;
-  const int64_t halfx = Lx / 2, halfy = Ly / 2;
-  bool wide = !(lx > 1 - halfx && hx < halfx - 1 && ly > 1 - halfy && hy < halfy - 1 && hx - lx < halfx - 1 &&
-                hy - ly < halfy - 1);
-  const int nx = R.nc[0], ny = R.nc[1];
-  const uint32_t* bxt = bounds + R.bnd[0];
-  const uint32_t* byt = bounds + R.bnd[1];
-  int ucx0 = 0, ucy0 = 0, ncx = 0, ncy = 0;
-  if (!wide) {
-    ucx0 = ucell_of((int64_t)o.x + lx, nx, bxt, R.inv_w[0], Lx);
-    ucy0 = ucell_of((int64_t)o.y + ly, ny, byt, R.inv_w[1], Ly);
-    ncx = ucell_of((int64_t)o.x + hx, nx, bxt, R.inv_w[0], Lx) - ucx0 + 1;
-    ncy = ucell_of((int64_t)o.y + hy, ny, byt, R.inv_w[1], Ly) - ucy0 + 1;
-    if (ncx > nx || ncy > ny || ncx > kMaxBoxCells || ncy > kMaxBoxCells || ncx * ncy > kMaxBoxCells) wide = true;
-  }
-  if (wide) return valid;
-
-  const int64_t Eb = max(max(-lx, hx), max(-ly, hy));
-  const float Ef = (float)max(Eb, (int64_t)em);
-  const float delta = __fmul_ru(__fmul_ru(Ef, Ef), 0x1p-17f);
-  const float thr = valid ? __fmul_ru(__fadd_ru(__fadd_ru(tau, delta0), delta), 1.000002f) : -1.f;
-  int cnt = 0;
-  for (int j = 0; j < nm; ++j) {
-    if (j != qm && fsq_dist(W.mate[j], qxf, qyf) <= thr) {
-      if (cnt < kKeep) W.keep[cnt][lane] = (int32_t)(ms0 + j);
-      ++cnt;
-    }
-  }
-  uint32_t n_cand = (uint32_t)nm - 1u, n_runs = 0;
-  int nst = 0;
-  const int ncell = ncx * ncy;
-  for (int cb = 0; cb < ncell; cb += 32) {
-    // this lane's cell: its first run (an index of sub_off), run width in
-    // sub-cells, row stride and row count
-    uint32_t a = 0, geo = 0;
-    const int c = cb + lane;
-    if (c < ncell) {
-      const int iy = c / ncx, ix = c - iy * ncx;
-      const int ucx = ucx0 + ix, ucy = ucy0 + iy;
-      const int cx = ucx < 0 ? ucx + nx : (ucx >= nx ? ucx - nx : ucx);
-      const int cy = ucy < 0 ? ucy + ny : (ucy >= ny ? ucy - ny : ucy);
-      const int64_t gc = R.c0 + (int64_t)cy * nx + cx;
-      const uint32_t sb = __ldg(G.sub_base + gc), sb1 = __ldg(G.sub_base + gc + 1);
-      if (sb1 - sb == 1) {
-        a = sb;
-        geo = 1u | (1u << 6) | (1u << 12);
-      } else {
-        const int s = __ldg(G.sub_s + gc);
-        const int64_t cx0 = cell_lo_tab(ucx, nx, bxt, Lx), wx = cell_lo_tab(ucx + 1, nx, bxt, Lx) - cx0;
-        const int64_t cy0 = cell_lo_tab(ucy, ny, byt, Ly), wy = cell_lo_tab(ucy + 1, ny, byt, Ly) - cy0;
-        const int64_t ax = (int64_t)o.x + lx - cx0, bxr = (int64_t)o.x + hx - cx0;
-        const int64_t ay = (int64_t)o.y + ly - cy0, byr = (int64_t)o.y + hy - cy0;
-        const int sx0 = ax <= 0 ? 0 : sub_idx(ax, wx, s);
-        const int sx1 = bxr >= wx ? s - 1 : sub_idx(bxr, wx, s);
-        const int sy0 = ay <= 0 ? 0 : sub_idx(ay, wy, s);
-        const int sy1 = byr >= wy ? s - 1 : sub_idx(byr, wy, s);
-        a = sb + (uint32_t)(sy0 * s + sx0);
-        geo = (uint32_t)(sx1 - sx0 + 1) | ((uint32_t)s << 6) | ((uint32_t)(sy1 - sy0 + 1) << 12);
-      }
-    }
-    const int nround = min(32, ncell - cb);
-    for (int j = 0; j < nround; ++j) {
-      const uint32_t ja = __shfl_sync(kAll, a, j), jg = __shfl_sync(kAll, geo, j);
-      const uint32_t w = jg & 63u, stride = (jg >> 6) & 63u, rows = jg >> 12;
-      for (uint32_t r = 0; r < rows; ++r) {
-        const uint32_t i0 = ja + r * stride;
-        const uint32_t qb = __ldg(G.sub_off + i0), qe = __ldg(G.sub_off + i0 + w);
-        ++n_runs;
-        n_cand += qe - qb;
-        for (uint32_t q0 = qb; q0 < qe; q0 += 32) {
-          const uint32_t q = q0 + (uint32_t)lane;
-          bool take = q < qe && (uint64_t)((int64_t)q - ms0) >= (uint64_t)nm;
-          float2 f = make_float2(0.f, 0.f);
-          if (take) {
-            const int2 p = __ldg(pos + q);
-            f.x = (float)min_image32((int32_t)((uint32_t)p.x - (uint32_t)o.x), hix, lox, Lx);
-            f.y = (float)min_image32((int32_t)((uint32_t)p.y - (uint32_t)o.y), hiy, loy, Ly);
-          }
-          const unsigned bal = __ballot_sync(kAll, take);
-          const int nb = __popc(bal);
-          if (nst + nb > kStage) {
-            scan_stage(W, nst, qxf, qyf, thr, lane, cnt);
-            nst = 0;
-          }
-          if (take) {
-            const int idx = nst + __popc(bal & ((1u << lane) - 1u));
-            W.cpos[idx] = f;
-            W.cslot[idx] = (int32_t)q;
-          }
-          nst += nb;
-        }
-      }
-    }
-  }
-  scan_stage(W, nst, qxf, qyf, thr, lane, cnt);
-
-  // 4. exact order of the kept slots
-  const int ce = min(cnt, kKeep);
-  const int cmax = (int)__reduce_max_sync(kAll, (uint32_t)ce);
-  for (int e = 0; e < cmax; ++e)
-    if (e < ce) consider<KC>(C, pos, ids, (uint32_t)W.keep[e][lane], T);
-  __syncwarp();
-  if (valid) {
-    C.n_cand = n_cand;
-    C.n_runs = n_runs;
-  }
-  return valid && cnt > kKeep;
-}
-
-// is the coarse cell of (px, py) split (tracing)
-__device__ __forceinline__ bool own_cell_split(const Rep& R, const uint32_t* __restrict__ bounds, const GridView& G,
-                                               uint32_t px, uint32_t py) {
-  const int cx = cell_of_tab(px, R.nc[0], bounds + R.bnd[0], R.inv_w[0]);
-  const int cy = cell_of_tab(py, R.nc[1], bounds + R.bnd[1], R.inv_w[1]);
-  const int64_t gc = R.c0 + (int64_t)cy * R.nc[0] + cx;
-  return __ldg(G.sub_base + gc + 1) - __ldg(G.sub_base + gc) > 1;
-}
-
-// search of every lane of the warp: warp-cooperative, the walk where needed
-template <int KC>
-__device__ __forceinline__ void knn2_find(WarpStage& W, const Rep& R, const uint32_t* __restrict__ bounds,
-                                          const GridView& G, const int2* __restrict__ pos,
-                                          const int32_t* __restrict__ ids, int wli0, bool valid, int k, bool trace,
-                                          Ctx& C, Top<KC>& T, bool& walked) {
-  walked = false;
-  if (wli0 >= R.n) return;  // warp-uniform
-  walked = knn2_warp_search<KC>(W, R, bounds, G, pos, ids, wli0, k, C, T);
-  if (walked) {
-    top_init<KC>(T, k);
-    C.n_cand = 0;
-    C.n_runs = 0;
-    knn2_search<KC>(C, R, bounds, G, pos, ids, T);
-  }
-  if (trace && valid) C.split = own_cell_split(R, bounds, G, C.px, C.py);
-}
-
 __device__ __forceinline__ void init_ctx(Ctx& C, const Rep& R, int64_t self, int2 p) {
   C.self = self;
   C.px = (uint32_t)p.x;
@@ -812,7 +531,7 @@ __device__ __forceinline__ void knn2_update(const Rep& R, const StepParams& P, i
   atomicAdd(counts + R.c0 + (int64_t)ncy * R.nc[0] + ncx, 1u);
 }
 
-// one thread per particle: search (warp-cooperative) + update
+// thread-per-particle search + update (the walk of RunGen for every particle)
 template <int KC>
 __global__ void __launch_bounds__(kBlock, VK_KNN2_MIN_BLOCKS) knn2_step_kernel(
     const Rep* __restrict__ reps, const BlockTask* __restrict__ tasks, const uint32_t* __restrict__ bounds,
@@ -820,34 +539,28 @@ __global__ void __launch_bounds__(kBlock, VK_KNN2_MIN_BLOCKS) knn2_step_kernel(
     int2* __restrict__ U_pos, float2* __restrict__ U_dir, int32_t* __restrict__ U_id, uint32_t* __restrict__ counts,
     double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P) {
   __shared__ PhiShared phs;
-  __shared__ WarpStage stage[kBlock / 32];
   phi_block_begin(phs);
   const BlockTask t = tasks[blockIdx.x];
   const Rep R = reps[t.rep];
   const int li = t.first + (int)threadIdx.x;
-  const int wli0 = t.first + (int)(threadIdx.x & ~31u);
-  const bool valid = li < R.n;
   const int64_t step = *d_step;
   float nnew[3] = {0.f, 0.f, 0.f};
-  const int64_t s = R.p0 + (valid ? li : 0);
-  int2 p = make_int2(0, 0);
   Ctx C;
-  init_ctx(C, R, -1, p);
-  if (valid) {
-    p = S_pos[s];
-    init_ctx(C, R, s, p);
-  }
-  Top<KC> T;
-  top_init<KC>(T, P.k);
-  bool walked;
-  knn2_find<KC>(stage[threadIdx.x >> 5], R, bounds, G, S_pos, S_id, wli0, valid, P.k, P.stats != nullptr, C, T,
-                walked);
-  if (valid) {
+  C.n_cand = 0;
+  C.n_runs = 0;
+  C.split = false;
+  if (li < R.n) {
+    const int64_t s = R.p0 + li;
+    const int2 p = S_pos[s];
     const float2 nv = S_dir[s];
     const int32_t id = S_id[s];
+    init_ctx(C, R, s, p);
+    Top<KC> T;
+    top_init<KC>(T, P.k);
+    knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T);
     knn2_update<KC>(R, P, step, s, p, nv, id, T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
   }
-  record_search_stats(P.stats, valid, C.n_cand, C.n_runs, C.split, walked);
+  record_search_stats(P.stats, li < R.n, C.n_cand, C.n_runs, C.split);
   phi_block_end<2>(phs, nnew, phi_acc + ((size_t)(step % P.phi_cap) * (size_t)P.n_rep + (size_t)t.rep) * 3);
 }
 
@@ -857,20 +570,15 @@ __global__ void __launch_bounds__(kBlock, 2) knn2_export_kernel(const Rep* __res
                                                                 const int2* __restrict__ S_pos,
                                                                 const int32_t* __restrict__ S_id, GridView G, int k,
                                                                 int32_t* __restrict__ out) {
-  __shared__ WarpStage stage[kBlock / 32];
   const Rep R = reps[rep];
   const int li = blockIdx.x * kBlock + (int)threadIdx.x;
-  const int wli0 = blockIdx.x * kBlock + (int)(threadIdx.x & ~31u);
-  const bool valid = li < R.n;
-  const int64_t s = R.p0 + (valid ? li : 0);
+  if (li >= R.n) return;
+  const int64_t s = R.p0 + li;
   Ctx C;
-  init_ctx(C, R, -1, make_int2(0, 0));
-  if (valid) init_ctx(C, R, s, S_pos[s]);
+  init_ctx(C, R, s, S_pos[s]);
   Top<KC> T;
   top_init<KC>(T, k);
-  bool walked;
-  knn2_find<KC>(stage[threadIdx.x >> 5], R, bounds, G, S_pos, S_id, wli0, valid, k, false, C, T, walked);
-  if (!valid) return;
+  knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T);
   const int32_t id = S_id[s];
 #pragma unroll
   for (int j = 0; j < KC; ++j)

@@ -82,7 +82,7 @@ _SIGS = {
     "vk_phase_name": (ctypes.c_char_p, [ctypes.c_int32]),
     "vk_get_search_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
-                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+                                           ctypes.POINTER(ctypes.c_double)]),
     "vk_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(vk_info)]),
     "vk_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.POINTER(ctypes.c_float)]),
@@ -282,16 +282,15 @@ class Sim:
         return {lib.vk_phase_name(p).decode(): (float(ms[p]), int(la[p])) for p in range(nph.value)}
 
     def search_stats(self) -> dict:
-        """Search counters per particle update while tracing (level 2) was on."""
+        """Mean candidates / runs per particle update while tracing was on."""
         c = ctypes.c_double(0.0)
         r = ctypes.c_double(0.0)
         m = ctypes.c_int64(0)
-        w = ctypes.c_double(0.0)
         f = ctypes.c_double(0.0)
         _check(load().vk_get_search_stats(self._h, ctypes.byref(c), ctypes.byref(r), ctypes.byref(m),
-                                          ctypes.byref(w), ctypes.byref(f)), self._h)
+                                          ctypes.byref(f)), self._h)
         return {"mean_candidates": c.value, "mean_runs": r.value, "max_candidates": m.value,
-                "walk_fraction": w.value, "split_fraction": f.value}
+                "split_fraction": f.value}
 
     def autotune(self, candidates: Sequence[float], trial_steps: int = 3) -> float:
         c = np.ascontiguousarray(candidates, dtype=np.float32)

@@ -134,3 +134,47 @@ def test_huge_cell_takes_the_overflow_path():
         assert off[1] - off[0] == 60
         for _ in range(2):
             check_step(sim, w, "voronoi")
+
+
+@pytest.mark.parametrize("occ", [2.0, 8.0])
+def test_condensed_bands_with_voids(occ):
+    """Dense bands and blobs separated by large empty regions, the kind of
+    state a low-noise flock condenses into: cells at void edges reach far
+    across the voids, and their sites must all be found."""
+    rng = np.random.default_rng(11)
+    L, F = 96, 16
+    t = rng.uniform(0, L, 5000)
+    band = np.stack([t, 0.3 * t + 20 + rng.normal(0, 1.5, t.size)], 1)
+    centers = rng.uniform(0, L, (6, 2))
+    blob = centers[rng.integers(0, 6, 2000)] + rng.normal(0, 1.0, (2000, 2))
+    lq = L << F
+    pos = np.floor(np.concatenate([band, blob]) * (1 << F)).astype(np.int64) % lq
+    pos = np.unique(pos, axis=0).astype(np.int32)
+    pos = pos[rng.permutation(pos.shape[0])]
+    w = W.Workload(name="bands_voids", dim=2, pos_q=pos, dir=W.random_dirs(pos.shape[0]), theta=None,
+                   box_q=(lq, lq), frac_bits=F, rule="voronoi", k=0, v0=0.3, eta=0.1)
+    with vk.from_workload(w, cell_occupancy=occ) as sim:
+        _same(sim, pos, w.box_q)
+        for _ in range(2):
+            check_step(sim, w, "voronoi")
+
+
+def test_blobs_across_voids_use_the_warp_path():
+    """Two dense blobs far apart: the cells on the rim of a blob reach across
+    the void to the other blob, so they see hundreds of candidates and are
+    finished one warp per cell; lists and the update must match the oracle."""
+    rng = np.random.default_rng(12)
+    L, F = 80, 16
+    blob = np.concatenate([rng.normal(20, 2.0, (1500, 2)), rng.normal(60, 2.0, (1500, 2))])
+    lq = L << F
+    pos = np.floor(blob * (1 << F)).astype(np.int64) % lq
+    pos = np.unique(pos, axis=0).astype(np.int32)
+    pos = pos[rng.permutation(pos.shape[0])]
+    w = W.Workload(name="blobs", dim=2, pos_q=pos, dir=W.random_dirs(pos.shape[0]), theta=None,
+                   box_q=(lq, lq), frac_bits=F, rule="voronoi", k=0, v0=0.3, eta=0.2)
+    with vk.from_workload(w) as sim:
+        sim.set_profiling(True, counters=True)
+        _same(sim, pos, w.box_q)
+        check_step(sim, w, "voronoi")
+        assert sim.search_stats()["max_candidates"] > 384  # some cells went to the warp path
+        check_step(sim, w, "voronoi")

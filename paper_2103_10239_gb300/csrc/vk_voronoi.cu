@@ -40,6 +40,9 @@ constexpr int kFastCap = 32;    // polygon capacity of the main kernel
 constexpr int kSlowCap = kVoronoiMaxDeg;  // capacity of the overflow kernel and the export
 constexpr uint32_t kHeavy = 384;  // candidates after which the main kernel hands a cell to the overflow kernel
 
+__device__ __noinline__ int vertex_cut_exact(int32_t ax, int32_t ay, int32_t bx, int32_t by, int32_t mx,
+                                             int32_t my);
+
 // sign of incircle(0, a, b, m): > 0 iff m lies strictly inside the circle
 // through the origin, a and b (with (0, a, b) counter-clockwise), i.e. iff
 // the vertex defined by a and b is strictly closer to m than to the origin.
@@ -56,7 +59,13 @@ __device__ __forceinline__ int vertex_cut_sign(int32_t ax, int32_t ay, int32_t b
   const float bound = perm * 1.9073486328125e-06f;  // 2^-19: 32 ulps of the permanent
   if (det > bound) return -1;
   if (det < -bound) return 1;
-  // exact
+  return vertex_cut_exact(ax, ay, bx, by, mx, my);
+}
+
+// the exact incircle sign (int128), kept out of line: it is rarely needed,
+// and a small hot loop keeps divergent warps in the instruction cache
+__device__ __noinline__ int vertex_cut_exact(int32_t ax, int32_t ay, int32_t bx, int32_t by, int32_t mx,
+                                             int32_t my) {
   const int64_t al = (int64_t)ax * ax + (int64_t)ay * ay;
   const int64_t bl = (int64_t)bx * bx + (int64_t)by * by;
   const int64_t ml = (int64_t)mx * mx + (int64_t)my * my;
@@ -70,8 +79,8 @@ __device__ __forceinline__ int vertex_cut_sign(int32_t ax, int32_t ay, int32_t b
 // Vertex V = circumcenter of (0, a, b) (consecutive edge sites, so that
 // ax*by - ay*bx > 0): FP32 estimate (vx, vy) with |vx - Vx|, |vy - Vy| <= e,
 // and a rigorous FP32 upper bound of |V|^2 (returned).
-__device__ __forceinline__ float vertex_geom(int32_t ax, int32_t ay, int32_t bx, int32_t by, float* vx, float* vy,
-                                             float* e, bool* bad) {
+__device__ __noinline__ float vertex_geom(int32_t ax, int32_t ay, int32_t bx, int32_t by, float* vx, float* vy,
+                                          float* e, bool* bad) {
   const int64_t dh = (int64_t)ax * by - (int64_t)ay * bx;  // exact
   if (dh <= 0) {
     *bad = true;
@@ -160,7 +169,7 @@ __device__ __forceinline__ void poly_refresh_max(Poly<CAP>& P) {
 // recompute the relevance box; between calls it is stale but still valid,
 // since the cell only shrinks
 template <int CAP>
-__device__ __forceinline__ void poly_refresh_box(Poly<CAP>& P) {
+__device__ __noinline__ void poly_refresh_box(Poly<CAP>& P) {
   float x0 = 3.0e38f, x1 = -3.0e38f, y0 = 3.0e38f, y1 = -3.0e38f;
   for (int a = 0; a < P.m; ++a) {
     const float r = __fadd_ru(__fsqrt_ru(P.vr2[a]), P.ve[a]);
@@ -192,6 +201,56 @@ __device__ __forceinline__ void poly_init(Poly<CAP>& P, int32_t self_id, uint32_
                            bad);
   poly_refresh_max(P);
   poly_refresh_box(P);
+}
+
+// replace the cut vertices [s, s + c) (cyclic) by site m; returns false if
+// the polygon would outgrow CAP.  Out of line: only actual cuts run it.
+template <int CAP>
+__device__ __noinline__ bool poly_apply_cut(Poly<CAP>& P, int s, int c, int32_t mx, int32_t my, int32_t mid,
+                                            int32_t mslot, bool* bad) {
+  const int m = P.m;
+  const int t = (s + c - 1) % m;
+  const int newm = m - c + 2;
+  if (newm > CAP) return false;
+  int mpos;
+  if (s <= t) {
+    // keep e_0..e_s, insert m, keep e_{t+1}..e_{m-1}
+    const int delta = s + 2 - (t + 1);  // <= 1
+    if (delta < 0) {
+      for (int a = t + 1; a < m; ++a) {
+        P.qx[a + delta] = P.qx[a]; P.qy[a + delta] = P.qy[a]; P.id[a + delta] = P.id[a];
+        P.slot[a + delta] = P.slot[a]; P.vr2[a + delta] = P.vr2[a];
+        P.vx[a + delta] = P.vx[a]; P.vy[a + delta] = P.vy[a]; P.ve[a + delta] = P.ve[a];
+      }
+    } else if (delta > 0) {
+      for (int a = m - 1; a >= t + 1; --a) {
+        P.qx[a + delta] = P.qx[a]; P.qy[a + delta] = P.qy[a]; P.id[a + delta] = P.id[a];
+        P.slot[a + delta] = P.slot[a]; P.vr2[a + delta] = P.vr2[a];
+        P.vx[a + delta] = P.vx[a]; P.vy[a + delta] = P.vy[a]; P.ve[a + delta] = P.ve[a];
+      }
+    }
+    mpos = s + 1;
+  } else {
+    // the run wraps: keep e_{t+1}..e_s (contiguous), then m
+    const int sh = t + 1;
+    for (int a = sh; a <= s; ++a) {
+      P.qx[a - sh] = P.qx[a]; P.qy[a - sh] = P.qy[a]; P.id[a - sh] = P.id[a];
+      P.slot[a - sh] = P.slot[a]; P.vr2[a - sh] = P.vr2[a];
+      P.vx[a - sh] = P.vx[a]; P.vy[a - sh] = P.vy[a]; P.ve[a - sh] = P.ve[a];
+    }
+    mpos = s - sh + 1;
+  }
+  P.qx[mpos] = mx;
+  P.qy[mpos] = my;
+  P.id[mpos] = mid;
+  P.slot[mpos] = mslot;
+  P.m = newm;
+  const int before = (mpos == 0) ? newm - 1 : mpos - 1;
+  const int after = (mpos + 1 == newm) ? 0 : mpos + 1;
+  P.vr2[before] = vertex_geom(P.qx[before], P.qy[before], mx, my, &P.vx[before], &P.vy[before], &P.ve[before], bad);
+  P.vr2[mpos] = vertex_geom(mx, my, P.qx[after], P.qy[after], &P.vx[mpos], &P.vy[mpos], &P.ve[mpos], bad);
+  poly_refresh_max(P);
+  return true;
 }
 
 // clip the cell by the bisector of site (mx, my); returns false on overflow
@@ -248,48 +307,7 @@ __device__ __forceinline__ bool poly_clip(Poly<CAP>& P, int32_t mx, int32_t my, 
     *bad = true;
     return true;
   }
-  const int t = (s + c - 1) % m;
-  const int newm = m - c + 2;
-  if (newm > CAP) return false;
-  int mpos;
-  if (s <= t) {
-    // keep e_0..e_s, insert m, keep e_{t+1}..e_{m-1}
-    const int delta = s + 2 - (t + 1);  // <= 1
-    if (delta < 0) {
-      for (int a = t + 1; a < m; ++a) {
-        P.qx[a + delta] = P.qx[a]; P.qy[a + delta] = P.qy[a]; P.id[a + delta] = P.id[a];
-        P.slot[a + delta] = P.slot[a]; P.vr2[a + delta] = P.vr2[a];
-        P.vx[a + delta] = P.vx[a]; P.vy[a + delta] = P.vy[a]; P.ve[a + delta] = P.ve[a];
-      }
-    } else if (delta > 0) {
-      for (int a = m - 1; a >= t + 1; --a) {
-        P.qx[a + delta] = P.qx[a]; P.qy[a + delta] = P.qy[a]; P.id[a + delta] = P.id[a];
-        P.slot[a + delta] = P.slot[a]; P.vr2[a + delta] = P.vr2[a];
-        P.vx[a + delta] = P.vx[a]; P.vy[a + delta] = P.vy[a]; P.ve[a + delta] = P.ve[a];
-      }
-    }
-    mpos = s + 1;
-  } else {
-    // the run wraps: keep e_{t+1}..e_s (contiguous), then m
-    const int sh = t + 1;
-    for (int a = sh; a <= s; ++a) {
-      P.qx[a - sh] = P.qx[a]; P.qy[a - sh] = P.qy[a]; P.id[a - sh] = P.id[a];
-      P.slot[a - sh] = P.slot[a]; P.vr2[a - sh] = P.vr2[a];
-      P.vx[a - sh] = P.vx[a]; P.vy[a - sh] = P.vy[a]; P.ve[a - sh] = P.ve[a];
-    }
-    mpos = s - sh + 1;
-  }
-  P.qx[mpos] = mx;
-  P.qy[mpos] = my;
-  P.id[mpos] = mid;
-  P.slot[mpos] = mslot;
-  P.m = newm;
-  const int before = (mpos == 0) ? newm - 1 : mpos - 1;
-  const int after = (mpos + 1 == newm) ? 0 : mpos + 1;
-  P.vr2[before] = vertex_geom(P.qx[before], P.qy[before], mx, my, &P.vx[before], &P.vy[before], &P.ve[before], bad);
-  P.vr2[mpos] = vertex_geom(mx, my, P.qx[after], P.qy[after], &P.vx[mpos], &P.vy[mpos], &P.ve[mpos], bad);
-  poly_refresh_max(P);
-  return true;
+  return poly_apply_cut(P, s, c, mx, my, mid, mslot, bad);
 }
 
 // Walk of the cell grid for one Voronoi cell: rings of sub-cells inside the
@@ -449,6 +467,26 @@ __device__ bool voronoi_walk(const Rep& R, const int32_t* pi, const GridView& G,
   }
 }
 
+// tiny boxes: visit the eight non-minimum periodic images of every other
+// particle (out of line: small systems only)
+template <class VisitFn>
+__device__ __noinline__ void far_images(const Rep& R, int64_t self, const int32_t* pi, const int2* __restrict__ pos,
+                                        const int32_t* __restrict__ ids, VisitFn& visit) {
+  const int64_t Lx = R.L[0], Ly = R.L[1];
+  for (int64_t q = R.p0; q < R.p0 + R.n; ++q) {
+    if (q == self) continue;
+    const int2 pj = pos[q];
+    const int32_t qx0 = (int32_t)min_image((int64_t)pj.x - pi[0], Lx);
+    const int32_t qy0 = (int32_t)min_image((int64_t)pj.y - pi[1], Ly);
+    for (int sy = -1; sy <= 1; ++sy)
+      for (int sx = -1; sx <= 1; ++sx) {
+        if (sx == 0 && sy == 0) continue;
+        const int64_t X = (int64_t)qx0 + sx * Lx, Y = (int64_t)qy0 + sy * Ly;
+        visit((int32_t)X, (int32_t)Y, ids[q], (int32_t)q);
+      }
+  }
+}
+
 // Voronoi cell of the particle at slot `self`.  Status codes are latched on
 // internal inconsistencies (kStRange); capacity overflow is returned.
 // Returns false (and leaves the cell unusable) if the polygon or the twin list
@@ -525,20 +563,7 @@ __device__ bool voronoi_cell(const Rep& R, int64_t self, const int32_t* pi, int3
     // the cell when the relevance box reaches half a period
     poly_refresh_box(P);
     const int64_t b[4] = {P.bx0, P.bx1, P.by0, P.by1};
-    if (!within_half(b, Lx, Ly)) {
-      for (int64_t q = R.p0; q < R.p0 + R.n; ++q) {
-        if (q == self) continue;
-        const int2 pj = pos[q];
-        const int32_t qx0 = (int32_t)min_image((int64_t)pj.x - pi[0], Lx);
-        const int32_t qy0 = (int32_t)min_image((int64_t)pj.y - pi[1], Ly);
-        for (int sy = -1; sy <= 1; ++sy)
-          for (int sx = -1; sx <= 1; ++sx) {
-            if (sx == 0 && sy == 0) continue;
-            const int64_t X = (int64_t)qx0 + sx * Lx, Y = (int64_t)qy0 + sy * Ly;
-            visit((int32_t)X, (int32_t)Y, ids[q], (int32_t)q);
-          }
-      }
-    }
+    if (!within_half(b, Lx, Ly)) far_images(R, self, pi, pos, ids, visit);
   }
   if (bad) set_status(status, kStRange);
   return !overflow;
@@ -755,6 +780,8 @@ __global__ void __launch_bounds__(kBlock) voronoi_step_kernel(
     int2* __restrict__ U_pos, float2* __restrict__ U_dir, int32_t* __restrict__ U_id,
     uint32_t* __restrict__ counts, double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams Pm,
     int2* __restrict__ ovf_list, int32_t* __restrict__ ovf_count, int32_t* status) {
+  __shared__ PhiShared phs;
+  phi_block_begin(phs);
   const BlockTask t = tasks[blockIdx.x];
   const Rep R = reps[t.rep];
   const int li = t.first + (int)threadIdx.x;
@@ -779,7 +806,7 @@ __global__ void __launch_bounds__(kBlock) voronoi_step_kernel(
     }
   }
   record_search_stats(Pm.stats, li < R.n, n_cand, n_runs);
-  block_phi_accumulate<2>(nnew, phi_acc + ((size_t)(step % Pm.phi_cap) * (size_t)Pm.n_rep + (size_t)t.rep) * 3);
+  phi_block_end<2>(phs, nnew, phi_acc + ((size_t)(step % Pm.phi_cap) * (size_t)Pm.n_rep + (size_t)t.rep) * 3);
 }
 
 // Overflow kernel: the few particles whose cell outgrew the main kernel's

@@ -246,7 +246,7 @@ def run_ours(args, rank, world, dist):
     if not args.no_autotune:
         # the library's autotuner picks the coarse-grid occupancy on the
         # warmed-up state (state and step counter are restored afterwards)
-        occupancy = sim.autotune([1.0, 2.0, 4.0, 8.0, 16.0], trial_steps=2)
+        occupancy = sim.autotune([64.0, 128.0, 256.0, 512.0, 1024.0, 2048.0, 4096.0, 8192.0], trial_steps=2)
     torch.cuda.synchronize()
     sim.set_profiling(True)
 

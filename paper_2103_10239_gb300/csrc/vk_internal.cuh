@@ -209,7 +209,7 @@ __device__ __forceinline__ int32_t wrap_add(int32_t p, int32_t d, uint32_t L) {
 // row-major), so every row of sub-cells, and every row of coarse cells, is a
 // contiguous run of the sorted arrays.
 // --------------------------------------------------------------------------
-constexpr int kSubMax = 32;      // largest sub-grid side
+constexpr int kSubMax = 64;      // largest sub-grid side (sub_s is 8 bits)
 constexpr int kSubTarget = 2;    // target particles per sub-cell
 
 __device__ __host__ __forceinline__ int sub_side(uint32_t m) {

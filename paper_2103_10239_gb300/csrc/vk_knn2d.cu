@@ -208,6 +208,19 @@ __device__ __forceinline__ bool gen_rect(RunGen& g, int64_t gc, int ucx, int ucy
     return true;
   }
   const int64_t rad = radius_upper(r2);
+  // Rings visit every cell once, at its offset in [-(n-1)/2, n/2].  If the
+  // box [p - rad, p + rad] reaches past that range (few cells per axis, or a
+  // large radius), the cell can meet the box through another periodic image:
+  // then all of it is scanned (every candidate is measured by its minimum
+  // image, so scanning more is always correct).
+  if (rad >= g.px - cell_lo_tab(g.cx - (g.nx - 1) / 2, g.nx, g.bx, R.L[0]) ||
+      rad >= cell_lo_tab(g.cx + g.nx / 2 + 1, g.nx, g.bx, R.L[0]) - g.px ||
+      rad >= g.py - cell_lo_tab(g.cy - (g.ny - 1) / 2, g.ny, g.by, R.L[1]) ||
+      rad >= cell_lo_tab(g.cy + g.ny / 2 + 1, g.ny, g.by, R.L[1]) - g.py) {
+    g.sx0r = 0; g.sx1r = s - 1; g.sr = 0; g.sr1 = s - 1;
+    g.in_rect = true;
+    return true;
+  }
   const int64_t cx0 = cell_lo_tab(ucx, g.nx, g.bx, R.L[0]);
   const int64_t wx = cell_lo_tab(ucx + 1, g.nx, g.bx, R.L[0]) - cx0;
   const int64_t cy0 = cell_lo_tab(ucy, g.ny, g.by, R.L[1]);
@@ -263,7 +276,10 @@ __device__ __forceinline__ void gen_init(RunGen& g, const Rep& R, const uint32_t
   g.ob0 = __ldg(G.sub_base + g.own);
   const uint32_t ob1 = __ldg(G.sub_base + g.own + 1);
   g.r = 0;
-  if (ob1 - g.ob0 > 1) {
+  // phase 1 (sub-cell rings inside the own cell) bounds the rest of the own
+  // cell by its distance to the scanned sub-block, which needs the own cell
+  // to be narrower than half a period: at least 3 cells per axis
+  if (ob1 - g.ob0 > 1 && g.nx >= 3 && g.ny >= 3) {
     g.phase = 1;
     g.s1 = __ldg(G.sub_s + g.own);
     g.cx0 = __ldg(g.bx + g.cx);

@@ -45,7 +45,7 @@ def test_ragged_sizes_and_k(n, L, bits, k):
             check_step(sim, w, "knn")
 
 
-@pytest.mark.parametrize("occ", [0.3, 1.0, 2.0, 4.0, 9.0, 40.0])
+@pytest.mark.parametrize("occ", [0.3, 1.0, 2.0, 4.0, 9.0, 40.0, 512.0, 4096.0])
 def test_lists_do_not_depend_on_the_cell_grid(occ):
     w = W.uniform_system(2500, 50.0, 16, 2, input_seed=3, rule="knn", k=7)
     want = oracle.knn(w.pos_q, w.box_q, 7)
@@ -73,10 +73,11 @@ def test_translation_invariance_on_gpu():
             assert np.array_equal(_knn_lists(sim, 7), base)
 
 
-@pytest.mark.parametrize("occ", [0.5, 2.0, 8.0, 40.0])
+@pytest.mark.parametrize("occ", [0.5, 2.0, 8.0, 40.0, 512.0, 4096.0, 32768.0])
 def test_clustered_lists_for_any_coarse_occupancy(occ):
     """Dense coarse cells are split into sub-grids; the lists must not
-    depend on how the two-level grid is cut."""
+    depend on how the two-level grid is cut (up to a single coarse cell with
+    a 64 x 64 sub-grid)."""
     w = W.clustered_large(n=1 << 15)
     want = oracle.knn(w.pos_q, w.box_q, 7)
     with vk.from_workload(w, cell_occupancy=occ) as sim:

@@ -94,7 +94,10 @@ typedef struct {
   int32_t include_self; /* 1: add n_i(t) to the sum (default 0, Eq. 2 literally) */
   int32_t advect_new;   /* 1: advect with n_i(t+dt) instead of n_i(t) (default 0) */
   int32_t sum_mode;     /* vk_sum_mode for the heading sums (default compensated) */
-  float cell_occupancy; /* target particles per cell of the search grid; 0 = default */
+  float cell_occupancy; /* target particles per coarse cell of the search grid at the mean
+                           density; 0 = default (512 for 2D kNN, 2 for Voronoi, 3 for 3D kNN).
+                           Dense coarse cells get sub-grids of about 2 particles per sub-cell.
+                           Results never depend on it; only the speed does. */
   int32_t phi_capacity; /* order-parameter history kept per replica; 0 = 4096 steps */
 } vk_params;
 

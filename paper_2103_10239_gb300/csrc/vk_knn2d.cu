@@ -258,7 +258,7 @@ __device__ __forceinline__ void gen_ring1(RunGen& g) {
 }
 
 __device__ __forceinline__ void gen_init(RunGen& g, const Rep& R, const uint32_t* __restrict__ bounds,
-                                         const GridView& G, uint32_t px, uint32_t py) {
+                                         const GridView& G, uint32_t px, uint32_t py, int k) {
   g.R = &R;
   g.bx = bounds + R.bnd[0];
   g.by = bounds + R.bnd[1];
@@ -288,7 +288,20 @@ __device__ __forceinline__ void gen_init(RunGen& g, const Rep& R, const uint32_t
     g.wy1 = (int64_t)__ldg(g.by + g.cy + 1) - g.cy0;
     g.sx = sub_idx(px - g.cx0, g.wx1, g.s1);
     g.sy = sub_idx(py - g.cy0, g.wy1, g.s1);
-    gen_ring1(g);
+    // Start with the 3 x 3 block of sub-cells, scanned as whole rows, rather
+    // than the own sub-cell and a ring around it: the own sub-cell (about 2
+    // particles) rarely holds and certifies the k nearest.  Only a very dense
+    // own sub-cell (more than 16 k particles, where the 64 x 64 cap of the
+    // sub-grid leaves dense cluster cores) starts alone.
+    const uint32_t os = g.ob0 + (uint32_t)(g.sy * g.s1 + g.sx);
+    if (__ldg(G.sub_off + os + 1) - __ldg(G.sub_off + os) <= (uint32_t)(16 * k)) {
+      g.r = 1;
+      gen_ring1(g);
+      g.px0 = 1;
+      g.px1 = 0;
+    } else {
+      gen_ring1(g);
+    }
   } else {
     g.phase = 2;
     gen_ring2(g);
@@ -447,9 +460,9 @@ __device__ __forceinline__ int gen_next(RunGen& g, uint64_t r2, uint32_t& qb, ui
 template <int KC>
 __device__ __forceinline__ void knn2_search(Ctx& C, const Rep& R, const uint32_t* __restrict__ bounds,
                                             const GridView& G, const int2* __restrict__ pos,
-                                            const int32_t* __restrict__ ids, Top<KC>& T) {
+                                            const int32_t* __restrict__ ids, Top<KC>& T, int k) {
   RunGen g;
-  gen_init(g, R, bounds, G, C.px, C.py);
+  gen_init(g, R, bounds, G, C.px, C.py, k);
   C.split = g.phase == 1;
   for (;;) {
     uint32_t qb = 0, qe = 0;
@@ -573,7 +586,7 @@ __global__ void __launch_bounds__(kBlock, VK_KNN2_MIN_BLOCKS) knn2_step_kernel(
     init_ctx(C, R, s, p);
     Top<KC> T;
     top_init<KC>(T, P.k);
-    knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T);
+    knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T, P.k);
     knn2_update<KC>(R, P, step, s, p, nv, id, T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
   }
   record_search_stats(P.stats, li < R.n, C.n_cand, C.n_runs, C.split);
@@ -594,7 +607,7 @@ __global__ void __launch_bounds__(kBlock, 2) knn2_export_kernel(const Rep* __res
   init_ctx(C, R, s, S_pos[s]);
   Top<KC> T;
   top_init<KC>(T, k);
-  knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T);
+  knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T, k);
   const int32_t id = S_id[s];
 #pragma unroll
   for (int j = 0; j < KC; ++j)

@@ -201,9 +201,33 @@ def oracle_sample_rate(w, budget_s: float, min_q: int = 32, m_fixed=None, seed: 
     sub_ids[sub_ids < 0] = 0  # neighbours outside the sample: any valid index (timing only)
     t0 = time.perf_counter()
     oracle.vicsek_step(w.pos_q[q], w.dir[q], w.box_q, off, sub_ids.astype(np.int32), frac_bits=w.frac_bits,
-                       v0=w.v0, dt=w.dt, eta=w.eta, seed=w.seed, step=0)
+                       v0=w.v0, dt=w.dt, eta=w.eta, seed=w.seed, step=0, noise=w.noise)
     t_upd = time.perf_counter() - t0
     return m / (t_knn + t_upd), m, oracle.num_threads(), t_knn + t_upd
+
+
+def scenario_cpu_baseline(w, budget_s: float) -> dict:
+    """The oracle on the host cores for a secondary workload, on its initial
+    state: a whole step (exact Delaunay triangulation of the periodic set,
+    neighbor lists, FP64 update) for the Voronoi rule; a bounded sample for
+    kNN."""
+    import oracle
+    oracle.build()
+    if w.rule == "voronoi":
+        t0 = time.perf_counter()
+        off, ids = oracle.voronoi(w.pos_q, w.box_q)
+        t_nb = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.vicsek_step(w.pos_q, w.dir, w.box_q, off, ids, frac_bits=w.frac_bits, v0=w.v0, dt=w.dt,
+                           eta=w.eta, seed=w.seed, step=0)
+        t_upd = time.perf_counter() - t0
+        return {"value": w.n / (t_nb + t_upd), "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                "sample": f"one whole step of all {w.n} particles ({t_nb + t_upd:.1f} s): serial Bowyer-Watson "
+                          f"triangulation ({t_nb:.1f} s) + FP64 update on {oracle.num_threads()} threads"}
+    rate, m, cores, secs = oracle_sample_rate(w, budget_s)
+    return {"value": rate, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{m} random particles of the {w.n}-particle workload: brute-force kNN over all N "
+                      f"+ FP64 update ({secs:.1f} s)"}
 
 
 # ---------------------------------------------------------------------------
@@ -339,7 +363,8 @@ def run_ours(args, rank, world, dist):
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+f32",
-        "data": "synthetic", "config": dict(workload_config(w, args), cell_occupancy=occupancy),
+        "data": "synthetic", "config": dict(workload_config(w, args), cell_occupancy=occupancy,
+                                            l2_bytes=int(torch.cuda.get_device_properties(dev).L2_cache_size)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "knn2_step_kernel (kNN search + align + advect)",
@@ -348,6 +373,11 @@ def run_ours(args, rank, world, dist):
         "step_roofline": {"achieved_gbs": alg_bytes / (ms_per_step * 1e-3) / 1e9,
                           "frac": alg_bytes / (ms_per_step * 1e-3) / 1e9 / peak,
                           "note": "24 B per particle-step over the whole step"},
+        # secondary, labelled: the implementation's state with the heading as an
+        # FP32 unit vector (pos 8 B + heading 8 B, read and written once)
+        "roofline_float2_state": {"bytes_per_particle_step": 32,
+                                  "achieved_gbs": 32 * w.n / (per_launch_ms * 1e-3) / 1e9,
+                                  "frac": 32 * w.n / (per_launch_ms * 1e-3) / 1e9 / peak},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(info.kernels_per_step) * args.steps,
         "clocks": clk, "phases": phases, "wall_s_timed_region": t_wall,
     }
@@ -426,6 +456,8 @@ def run_scenario(args):
                     "unit": "particle-steps/s", "ms_per_step": ms,
                     "config": {"workload": w.name, "n": w.n, "rule": w.rule, "k": w.k, "dim": w.dim},
                     "phases_ms_per_step": {k: v[0] / 3 for k, v in prof.items() if v[1]}})
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = scenario_cpu_baseline(w, args.cpu_seconds)
     print(json.dumps(out), flush=True)
 
 

@@ -126,3 +126,32 @@ def test_autotune_keeps_results():
         assert before[3] == after[3]
         sim.step(1)
         check_step(sim, w, "knn")
+
+
+def test_free_running_order_parameter_statistics():
+    """Free-running trajectories of the GPU (FP32 sums) and of the oracle
+    (FP64 sums) separate after a while, since rounding differences flip
+    neighbor choices and the dynamics amplifies them. So they are compared
+    statistically: the order parameter averaged over the second half of the
+    run and over independent replicas, within four standard errors of the
+    difference (standard errors from the spread of the replica means)."""
+    R, n, steps, eta = 8, 400, 300, 1.5
+    ws = [W.uniform_system(n, 20.0, 16, 2, input_seed=60 + r, rule="knn", k=7, v0=0.5, eta=eta, replica=r)
+          for r in range(R)]
+    with vk.batch_from_workloads(ws) as sim:
+        sim.step(steps)
+        gpu = np.array([sim.order_parameter(r)[steps // 2:].mean() for r in range(R)])
+    cpu = np.zeros(R)
+    for r, w in enumerate(ws):
+        pos, d = w.pos_q.copy(), w.dir.astype(np.float32)
+        phis = []
+        for t in range(steps):
+            off, ids = oracle.csr_from_dense(oracle.knn(pos, w.box_q, 7))
+            pos, d64, _ = oracle.vicsek_step(pos, d, w.box_q, off, ids, frac_bits=16, v0=w.v0, dt=w.dt, eta=w.eta,
+                                             seed=w.seed, step=t, replica=r)
+            d = d64.astype(np.float32)
+            phis.append(np.linalg.norm(d64.sum(0)) / n)
+        cpu[r] = np.mean(phis[steps // 2:])
+    se = np.sqrt(gpu.var(ddof=1) / R + cpu.var(ddof=1) / R)
+    assert 0.05 < gpu.mean() < 0.99  # an ordered but fluctuating regime
+    assert abs(gpu.mean() - cpu.mean()) <= 4 * se + 1e-3, (gpu.mean(), cpu.mean(), se)

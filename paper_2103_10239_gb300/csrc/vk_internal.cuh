@@ -253,115 +253,45 @@ __device__ __forceinline__ int64_t radius_upper(uint64_t r2) {
   return r;
 }
 
-// Walk the grid around the particle at pi.  run(qb, qe) receives runs of
-// sorted slots; radius2() is an upper bound of the squared distance beyond
-// which candidates no longer matter (~0ull while unknown; never increasing);
-// stop(B2) is asked after each coarse ring, B2 being the exact squared
-// distance from the particle to the nearest point outside the scanned block
-// of coarse cells.  Returns true iff the whole box was scanned.
-//
-// Phase 1 (own coarse cell split in sub-cells): rings of sub-cells around
-// the particle's sub-cell, until the remaining sub-cells are provably farther
-// than radius2 or the cell is exhausted.  Phase 2: rings of coarse cells
-// (clamped so that no cell is visited twice); in a split cell only the
-// sub-cells meeting the box [p - r, p + r], r^2 >= radius2(), are scanned.
-template <int DIM, class RunFn, class R2Fn, class StopFn>
-__device__ __forceinline__ bool grid_walk(const Rep& R, const int32_t* pi, const GridView& G, RunFn& run,
-                                          R2Fn& radius2, StopFn& stop) {
-  int c[3] = {0, 0, 0};
+// Walk the 3D grid around the particle at pi (3D coarse cells are never
+// split into sub-cells).  run(qb, qe) receives runs of sorted slots (a row
+// segment of coarse cells along x is one run); stop(B2) is asked after each
+// ring of cells, B2 being the exact squared distance from the particle to the
+// nearest point outside the scanned block.  Rings are clamped so that no cell
+// is visited twice; every candidate is measured by its minimum image.
+// Returns true iff the whole box was scanned.
+template <class RunFn, class StopFn>
+__device__ __forceinline__ bool grid_walk3(const Rep& R, const int32_t* pi, const GridView& G, RunFn& run,
+                                           StopFn& stop) {
+  int c[3];
 #pragma unroll
-  for (int a = 0; a < DIM; ++a) c[a] = cell_of(pi[a], R.nc[a], R.L[a]);
-  int64_t own = 0;
-#pragma unroll
-  for (int a = DIM - 1; a >= 0; --a) own = own * R.nc[a] + c[a];
-  own += R.c0;
-  const int s_own = G.sub_s[own];
-  bool own_done = false;
-  if (DIM == 2 && s_own > 1) {
-    // ---- phase 1: sub-cell rings inside the own coarse cell
-    const int s = s_own;
-    const int64_t x0 = cell_lo(c[0], R.nc[0], R.L[0]), y0 = cell_lo(c[1], R.nc[1], R.L[1]);
-    const int64_t wx = cell_lo(c[0] + 1, R.nc[0], R.L[0]) - x0, wy = cell_lo(c[1] + 1, R.nc[1], R.L[1]) - y0;
-    const int sx = sub_index(pi[0] - x0, wx, s), sy = sub_index(pi[1] - y0, wy, s);
-    const uint32_t base = G.sub_base[own];
-    for (int r = 0;; ++r) {
-      const int bx0 = max(sx - r, 0), bx1 = min(sx + r, s - 1), by0 = max(sy - r, 0), by1 = min(sy + r, s - 1);
-      const int px0 = r ? max(sx - r + 1, 0) : 1, px1 = r ? min(sx + r - 1, s - 1) : 0;
-      const int py0 = r ? max(sy - r + 1, 0) : 1, py1 = r ? min(sy + r - 1, s - 1) : 0;
-      for (int yy = by0; yy <= by1; ++yy) {
-        const uint32_t rb = base + (uint32_t)yy * s;
-        if (yy < py0 || yy > py1 || px0 > px1) {
-          run(G.sub_off[rb + bx0], G.sub_off[rb + bx1 + 1]);
-        } else {
-          if (bx0 < px0) run(G.sub_off[rb + bx0], G.sub_off[rb + px0]);
-          if (bx1 > px1) run(G.sub_off[rb + px1 + 1], G.sub_off[rb + bx1 + 1]);
-        }
-      }
-      if (bx0 == 0 && by0 == 0 && bx1 == s - 1 && by1 == s - 1) break;
-      int64_t B = INT64_MAX;
-      if (bx0 > 0) B = min(B, (int64_t)pi[0] - (x0 + (bx0 * wx + s - 1) / s) + 1);
-      if (bx1 < s - 1) B = min(B, x0 + ((bx1 + 1) * wx + s - 1) / s - (int64_t)pi[0]);
-      if (by0 > 0) B = min(B, (int64_t)pi[1] - (y0 + (by0 * wy + s - 1) / s) + 1);
-      if (by1 < s - 1) B = min(B, y0 + ((by1 + 1) * wy + s - 1) / s - (int64_t)pi[1]);
-      if (radius2() < (uint64_t)B * (uint64_t)B) break;
-    }
-    own_done = true;
-  }
-  // ---- phase 2: coarse rings
-  // visit coarse cells x-offsets [a, b] of the row at unwrapped y offset uy
-  auto visit_row = [&](int a, int b, int64_t rowbase, int64_t ucy, int64_t ucz) {
+  for (int a = 0; a < 3; ++a) c[a] = cell_of(pi[a], R.nc[a], R.L[a]);
+  // cells x-offsets [a, b] of the row whose first cell is rowbase: one run
+  // per wrap-free segment
+  auto visit_row = [&](int a, int b, int64_t rowbase) {
     if (a > b) return;
     const int nx = R.nc[0];
     uint32_t pend_b = 0, pend_e = 0;
     bool pend = false;
     for (int ox = a; ox <= b; ++ox) {
-      const int xc = wrap_index(c[0] + ox, nx);
-      const int64_t g = rowbase + xc;
-      const int s = G.sub_s[g];
-      if ((g == own && own_done) || s > 1) {
-        if (pend) run(pend_b, pend_e);
-        pend = false;
-        if (g == own && own_done) continue;
-        // split cell: only the sub-cells meeting the box [p - rad, p + rad]
-        const uint64_t r2 = radius2();
-        if (r2 == ~0ull) {
-          run(G.off[g], G.off[g + 1]);
-          continue;
-        }
-        const int64_t rad = radius_upper(r2);
-        const int64_t ucx = (int64_t)c[0] + ox;
-        const int64_t x0 = cell_lo(ucx, R.nc[0], R.L[0]), y0 = cell_lo(ucy, R.nc[1], R.L[1]);
-        const int64_t wx = cell_lo(ucx + 1, R.nc[0], R.L[0]) - x0, wy = cell_lo(ucy + 1, R.nc[1], R.L[1]) - y0;
-        const int64_t lx = (int64_t)pi[0] - rad - x0, hx = (int64_t)pi[0] + rad - x0;
-        const int64_t ly = (int64_t)pi[1] - rad - y0, hy = (int64_t)pi[1] + rad - y0;
-        if (hx < 0 || lx >= wx || hy < 0 || ly >= wy) continue;
-        const int sx0 = lx <= 0 ? 0 : sub_index(lx, wx, s), sx1 = hx >= wx ? s - 1 : sub_index(hx, wx, s);
-        const int sy0 = ly <= 0 ? 0 : sub_index(ly, wy, s), sy1 = hy >= wy ? s - 1 : sub_index(hy, wy, s);
-        const uint32_t base = G.sub_base[g];
-        for (int yy = sy0; yy <= sy1; ++yy) {
-          const uint32_t rb = base + (uint32_t)yy * s;
-          run(G.sub_off[rb + sx0], G.sub_off[rb + sx1 + 1]);
-        }
+      const int64_t g = rowbase + wrap_index(c[0] + ox, nx);
+      const uint32_t qb = G.off[g], qe = G.off[g + 1];
+      if (pend && qb == pend_e) {
+        pend_e = qe;
       } else {
-        const uint32_t qb = G.off[g], qe = G.off[g + 1];
-        if (pend && qb == pend_e) {
-          pend_e = qe;
-        } else {
-          if (pend) run(pend_b, pend_e);
-          pend = true;
-          pend_b = qb;
-          pend_e = qe;
-        }
+        if (pend) run(pend_b, pend_e);
+        pend = true;
+        pend_b = qb;
+        pend_e = qe;
       }
     }
     if (pend) run(pend_b, pend_e);
-    (void)ucz;
   };
   for (int r = 0;; ++r) {
     int lo[3], hi[3], plo[3], phi[3];
     bool full_all = true, any_new = (r == 0);
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) {
+    for (int a = 0; a < 3; ++a) {
       lo[a] = ring_lo(r, R.nc[a]);
       hi[a] = ring_hi(r, R.nc[a]);
       plo[a] = r ? ring_lo(r - 1, R.nc[a]) : 1;
@@ -370,37 +300,23 @@ __device__ __forceinline__ bool grid_walk(const Rep& R, const int32_t* pi, const
       any_new = any_new || lo[a] < plo[a] || hi[a] > phi[a];
     }
     if (!any_new) return true;
-    if (DIM == 2) {
+    for (int oz = lo[2]; oz <= hi[2]; ++oz) {
+      const int64_t zb = (int64_t)wrap_index(c[2] + oz, R.nc[2]) * R.nc[1];
+      const bool oldz = !(oz < plo[2] || oz > phi[2]);
       for (int oy = lo[1]; oy <= hi[1]; ++oy) {
-        const int64_t rowbase = R.c0 + (int64_t)wrap_index(c[1] + oy, R.nc[1]) * R.nc[0];
-        const int64_t ucy = (int64_t)c[1] + oy;
-        if (oy < plo[1] || oy > phi[1]) {
-          visit_row(lo[0], hi[0], rowbase, ucy, 0);
+        const int64_t rowbase = R.c0 + (zb + wrap_index(c[1] + oy, R.nc[1])) * R.nc[0];
+        if (!oldz || oy < plo[1] || oy > phi[1]) {
+          visit_row(lo[0], hi[0], rowbase);
         } else {
-          visit_row(lo[0], plo[0] - 1, rowbase, ucy, 0);
-          visit_row(phi[0] + 1, hi[0], rowbase, ucy, 0);
-        }
-      }
-    } else {
-      for (int oz = lo[2]; oz <= hi[2]; ++oz) {
-        const int64_t zb = (int64_t)wrap_index(c[2] + oz, R.nc[2]) * R.nc[1];
-        const bool oldz = !(oz < plo[2] || oz > phi[2]);
-        for (int oy = lo[1]; oy <= hi[1]; ++oy) {
-          const int64_t rowbase = R.c0 + (zb + wrap_index(c[1] + oy, R.nc[1])) * R.nc[0];
-          const int64_t ucy = (int64_t)c[1] + oy;
-          if (!oldz || oy < plo[1] || oy > phi[1]) {
-            visit_row(lo[0], hi[0], rowbase, ucy, 0);
-          } else {
-            visit_row(lo[0], plo[0] - 1, rowbase, ucy, 0);
-            visit_row(phi[0] + 1, hi[0], rowbase, ucy, 0);
-          }
+          visit_row(lo[0], plo[0] - 1, rowbase);
+          visit_row(phi[0] + 1, hi[0], rowbase);
         }
       }
     }
     if (full_all) return true;
     int64_t B = INT64_MAX;
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) {
+    for (int a = 0; a < 3; ++a) {
       if (hi[a] - lo[a] + 1 == R.nc[a]) continue;
       const int64_t bl = (int64_t)pi[a] - cell_lo((int64_t)c[a] - r, R.nc[a], R.L[a]) + 1;
       const int64_t bh = cell_lo((int64_t)c[a] + r + 1, R.nc[a], R.L[a]) - (int64_t)pi[a];
@@ -659,7 +575,7 @@ cudaError_t launch_export_state(const Geometry& g, const Buffers& b, int rep, in
 cudaError_t launch_import_state(const Geometry& g, const Buffers& b, int rep, int64_t p0, int32_t n,
                                 const int32_t* pos_in, const float* dir_in, cudaStream_t st);
 
-// vk_knn.cu
+// vk_knn.cu (3D)
 cudaError_t launch_knn_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st);
 cudaError_t launch_knn_export(const Geometry& g, const Buffers& b, int k, int rep, int n, int32_t* out,
                               cudaStream_t st);

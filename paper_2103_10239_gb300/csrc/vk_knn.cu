@@ -1,7 +1,7 @@
 // vk_knn.cu -- k-nearest-neighbor rule (Sec. "Metric and topological flocking
 // models": each particle aligns with its k nearest neighbors, at any distance,
 // so the relation is not reciprocal) fused with the Vicsek update of Eq. (1)
-// and Eq. (2).
+// and Eq. (2), in 3D (the 2D rule, the benchmark's, is in vk_knn2d.cu).
 //
 // One thread per particle, in cell-sorted order.  The search walks rings of
 // cells around the particle's cell; each row segment of a ring is one
@@ -93,9 +93,8 @@ __device__ __forceinline__ void knn_search(const Rep& R, int64_t self, const int
   // every unscanned particle is at squared distance >= B2: stop once the
   // k-th best is strictly closer (an equal distance could still win on id)
   auto stop = [&](uint64_t B2) { return T.d[KC - 1] < B2; };
-  // candidates beyond the k-th best (ties included) cannot enter
-  auto radius2 = [&]() { return T.d[KC - 1]; };
-  grid_walk<DIM>(R, pi, G, run, radius2, stop);
+  static_assert(DIM == 3, "the 2D rule is vk_knn2d.cu");
+  grid_walk3(R, pi, G, run, stop);
 }
 
 template <int DIM, int KC>
@@ -199,11 +198,7 @@ cudaError_t export_dispatch(const Geometry& g, const Buffers& b, int k, int rep,
 }  // namespace
 
 cudaError_t launch_knn_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st) {
-  if (g.dim == 2) {
-    if (P.k <= 8) return step_dispatch<2, 8>(g, b, P, st);
-    if (P.k <= 16) return step_dispatch<2, 16>(g, b, P, st);
-    return step_dispatch<2, 32>(g, b, P, st);
-  }
+  if (g.dim != 3) return cudaErrorInvalidValue;  // 2D: launch_knn2_step
   if (P.k <= 8) return step_dispatch<3, 8>(g, b, P, st);
   if (P.k <= 16) return step_dispatch<3, 16>(g, b, P, st);
   return step_dispatch<3, 32>(g, b, P, st);
@@ -211,11 +206,7 @@ cudaError_t launch_knn_step(const Geometry& g, const Buffers& b, const StepParam
 
 cudaError_t launch_knn_export(const Geometry& g, const Buffers& b, int k, int rep, int n, int32_t* out,
                               cudaStream_t st) {
-  if (g.dim == 2) {
-    if (k <= 8) return export_dispatch<2, 8>(g, b, k, rep, n, out, st);
-    if (k <= 16) return export_dispatch<2, 16>(g, b, k, rep, n, out, st);
-    return export_dispatch<2, 32>(g, b, k, rep, n, out, st);
-  }
+  if (g.dim != 3) return cudaErrorInvalidValue;  // 2D: launch_knn2_export
   if (k <= 8) return export_dispatch<3, 8>(g, b, k, rep, n, out, st);
   if (k <= 16) return export_dispatch<3, 16>(g, b, k, rep, n, out, st);
   return export_dispatch<3, 32>(g, b, k, rep, n, out, st);

@@ -56,6 +56,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kBlock) count_kernel(const Rep* __restrict__ reps,
                                                        const BlockTask* __restrict__ tasks,
                                                        const typename Vec<DIM>::P* __restrict__ U_pos,
+                                                       const uint32_t* __restrict__ bounds,
                                                        uint32_t* __restrict__ counts) {
   const BlockTask t = tasks[blockIdx.x];
   const Rep R = reps[t.rep];
@@ -64,7 +65,13 @@ __global__ void __launch_bounds__(kBlock) count_kernel(const Rep* __restrict__ r
   const int64_t s = R.p0 + li;
   int32_t p[3];
   unpack(U_pos[s], p);
-  atomicAdd(counts + linear_cell<DIM>(R, p), 1u);
+  int c[3] = {0, 0, 0};
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) c[a] = cell_of_tab((uint32_t)p[a], R.nc[a], bounds + R.bnd[a], R.inv_w[a]);
+  int64_t lin = 0;
+#pragma unroll
+  for (int a = DIM - 1; a >= 0; --a) lin = lin * R.nc[a] + c[a];
+  atomicAdd(counts + R.c0 + lin, 1u);
 }
 
 // sub-cell histogram of U: the rank of every particle inside its sub-cell
@@ -72,7 +79,8 @@ template <int DIM>
 __global__ void __launch_bounds__(kBlock) sub_count_kernel(const Rep* __restrict__ reps,
                                                            const BlockTask* __restrict__ tasks,
                                                            const typename Vec<DIM>::P* __restrict__ U_pos,
-                                                           GridView G, uint32_t* __restrict__ sub_count,
+                                                           const uint32_t* __restrict__ bounds, GridView G,
+                                                           uint32_t* __restrict__ sub_count,
                                                            uint32_t* __restrict__ U_rank) {
   const BlockTask t = tasks[blockIdx.x];
   const Rep R = reps[t.rep];
@@ -81,7 +89,8 @@ __global__ void __launch_bounds__(kBlock) sub_count_kernel(const Rep* __restrict
   const int64_t s = R.p0 + li;
   int32_t p[3];
   unpack(U_pos[s], p);
-  const int64_t g = sub_cell_of<DIM>(R, G, p, linear_cell<DIM>(R, p));
+  int64_t gc, g;
+  locate_tab<DIM>(R, G, bounds, p, &gc, &g);
   U_rank[s] = atomicAdd(sub_count + g, 1u);
 }
 
@@ -273,7 +282,8 @@ __global__ void __launch_bounds__(kBlock) scatter_kernel(const Rep* __restrict__
                                                          const typename Vec<DIM>::P* __restrict__ U_pos,
                                                          const typename Vec<DIM>::F* __restrict__ U_dir,
                                                          const int32_t* __restrict__ U_id,
-                                                         const uint32_t* __restrict__ U_rank, GridView G,
+                                                         const uint32_t* __restrict__ U_rank,
+                                                         const uint32_t* __restrict__ bounds, GridView G,
                                                          typename Vec<DIM>::P* __restrict__ S_pos,
                                                          typename Vec<DIM>::F* __restrict__ S_dir,
                                                          int32_t* __restrict__ S_id, int advance_step,
@@ -298,7 +308,9 @@ __global__ void __launch_bounds__(kBlock) scatter_kernel(const Rep* __restrict__
   const typename Vec<DIM>::P pv = U_pos[s];
   int32_t p[3];
   unpack(pv, p);
-  const uint32_t dst = G.sub_off[sub_cell_of<DIM>(R, G, p, linear_cell<DIM>(R, p))] + U_rank[s];
+  int64_t gc, g;
+  locate_tab<DIM>(R, G, bounds, p, &gc, &g);
+  const uint32_t dst = G.sub_off[g] + U_rank[s];
   S_pos[dst] = pv;
   S_dir[dst] = U_dir[s];
   S_id[dst] = U_id[s];
@@ -379,9 +391,9 @@ static GridView grid_view(const Buffers& b) {
 
 cudaError_t launch_count(const Geometry& g, const Buffers& b, cudaStream_t st) {
   if (g.dim == 2)
-    count_kernel<2><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int2*)b.U_pos, b.counts);
+    count_kernel<2><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int2*)b.U_pos, b.bounds, b.counts);
   else
-    count_kernel<3><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int4*)b.U_pos, b.counts);
+    count_kernel<3><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int4*)b.U_pos, b.bounds, b.counts);
   return cudaGetLastError();
 }
 
@@ -393,10 +405,10 @@ cudaError_t launch_build(const Geometry& g, const Buffers& b, cudaStream_t st) {
                                            b.sub_base);
   const GridView G = grid_view(b);
   if (g.dim == 2)
-    sub_count_kernel<2><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int2*)b.U_pos, G, b.sub_count,
+    sub_count_kernel<2><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int2*)b.U_pos, b.bounds, G, b.sub_count,
                                                        b.U_rank);
   else
-    sub_count_kernel<3><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int4*)b.U_pos, G, b.sub_count,
+    sub_count_kernel<3><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int4*)b.U_pos, b.bounds, G, b.sub_count,
                                                        b.U_rank);
   const int nb2 = (int)((g.n_sub_max + kScanTile - 1) / kScanTile);
   scan_reduce_kernel<<<nb2, kBlock, 0, st>>>(b.sub_count, g.n_sub_max, b.bsum2);
@@ -410,12 +422,12 @@ cudaError_t launch_scatter(const Geometry& g, const Buffers& b, const StepParams
   const GridView G = grid_view(b);
   if (g.dim == 2)
     scatter_kernel<2><<<g.n_tasks, kBlock, 0, st>>>(
-        g.reps, g.tasks, (const int2*)b.U_pos, (const float2*)b.U_dir, b.U_id, b.U_rank, G,
+        g.reps, g.tasks, (const int2*)b.U_pos, (const float2*)b.U_dir, b.U_id, b.U_rank, b.bounds, G,
         (int2*)b.S_pos, (float2*)b.S_dir, b.S_id, advance_step, b.d_step, b.phi_acc, P.n_rep, P.phi_cap,
         b.ovf_count);
   else
     scatter_kernel<3><<<g.n_tasks, kBlock, 0, st>>>(
-        g.reps, g.tasks, (const int4*)b.U_pos, (const float4*)b.U_dir, b.U_id, b.U_rank, G,
+        g.reps, g.tasks, (const int4*)b.U_pos, (const float4*)b.U_dir, b.U_id, b.U_rank, b.bounds, G,
         (int4*)b.S_pos, (float4*)b.S_dir, b.S_id, advance_step, b.d_step, b.phi_acc, P.n_rep, P.phi_cap,
         b.ovf_count);
   return cudaGetLastError();

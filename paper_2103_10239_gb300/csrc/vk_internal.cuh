@@ -244,6 +244,41 @@ __device__ __forceinline__ int64_t sub_cell_of(const Rep& R, const GridView& G, 
   return (int64_t)G.sub_base[gcell] + j;
 }
 
+// sub-cell index of offset u (0 <= u < w) in a cell of width w split s ways:
+// floor(u*s/w), from a float estimate corrected with exact products
+__device__ __forceinline__ int sub_idx(int64_t u, int64_t w, int s) {
+  int j = min(max((int)((float)u * ((float)s / (float)w)), 0), s - 1);
+  const int64_t us = u * s;
+  while (j > 0 && us < (int64_t)j * w) --j;
+  while (j < s - 1 && us >= (int64_t)(j + 1) * w) ++j;
+  return j;
+}
+
+// Coarse cell and sub-cell (global indices) of a position, from the
+// per-replica boundary tables (no 64-bit division); the same cells as
+// linear_cell / sub_cell_of.
+template <int DIM>
+__device__ __forceinline__ void locate_tab(const Rep& R, const GridView& G, const uint32_t* __restrict__ bounds,
+                                           const int32_t* p, int64_t* gcell, int64_t* gsub) {
+  int c[3] = {0, 0, 0};
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) c[a] = cell_of_tab((uint32_t)p[a], R.nc[a], bounds + R.bnd[a], R.inv_w[a]);
+  int64_t lin = 0;
+#pragma unroll
+  for (int a = DIM - 1; a >= 0; --a) lin = lin * R.nc[a] + c[a];
+  *gcell = R.c0 + lin;
+  const int s = G.sub_s[*gcell];
+  int64_t j = 0;
+  if (DIM == 2 && s > 1) {
+    const uint32_t* bx = bounds + R.bnd[0];
+    const uint32_t* by = bounds + R.bnd[1];
+    const int64_t x0 = __ldg(bx + c[0]), wx = (int64_t)__ldg(bx + c[0] + 1) - x0;
+    const int64_t y0 = __ldg(by + c[1]), wy = (int64_t)__ldg(by + c[1] + 1) - y0;
+    j = (int64_t)sub_idx(p[1] - y0, wy, s) * s + sub_idx(p[0] - x0, wx, s);
+  }
+  *gsub = (int64_t)G.sub_base[*gcell] + j;
+}
+
 // upper bound (integer) of the square root of r2; r2 may be ~0ull (infinite)
 __device__ __forceinline__ int64_t radius_upper(uint64_t r2) {
   if (r2 >= (1ull << 62)) return INT64_MAX / 4;

@@ -102,16 +102,6 @@ __device__ __forceinline__ void scan_run(Ctx& C, const int2* __restrict__ pos, c
   }
 }
 
-// sub-cell index of offset u (0 <= u < w) in a cell of width w split s ways:
-// floor(u*s/w), from a float estimate corrected with exact products
-__device__ __forceinline__ int sub_idx(int64_t u, int64_t w, int s) {
-  int j = min(max((int)((float)u * ((float)s / (float)w)), 0), s - 1);
-  const int64_t us = u * s;
-  while (j > 0 && us < (int64_t)j * w) --j;
-  while (j < s - 1 && us >= (int64_t)(j + 1) * w) ++j;
-  return j;
-}
-
 // first offset of sub-cell b: ceil(b*w/s)
 __device__ __forceinline__ int64_t sub_lo(int b, int64_t w, int s) {
   const int64_t bw = (int64_t)b * w;

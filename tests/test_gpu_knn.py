@@ -93,13 +93,16 @@ def test_clustered_density_contrast():
             check_step(sim, w, "knn")
 
 
-def test_full_scale_clustered_sampled_parity():
+@pytest.mark.parametrize("occ,steps", [(None, 2), (2048.0, 40)])
+def test_full_scale_clustered_sampled_parity(occ, steps):
     """N = 2^22 (the benchmark workload): sampled particles against brute
-    force over all N, plus a teacher-forced step on the same sample."""
+    force over all N, plus a teacher-forced step on the same sample; with the
+    library's default grid, and in the benchmark's launch configuration
+    (2048 particles per coarse cell) on the clumped state after 40 steps."""
     w = W.clustered_large()
     rng = np.random.default_rng(0)
-    with vk.from_workload(w) as sim:
-        sim.step(2)
+    with vk.from_workload(w, **({} if occ is None else {"cell_occupancy": occ})) as sim:
+        sim.step(steps)
         pos0, d0, _, t0 = sim.state()
         off, ids = sim.neighbors()
         q = np.sort(rng.choice(w.n, 1024, replace=False))

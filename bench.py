@@ -260,6 +260,19 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def reduce_job(dist, units: float, seconds: float, device):
+    """Whole-job totals over the ranks: the units all ranks processed (sum)
+    and the slowest rank's time (max).  Without a process group: unchanged."""
+    if dist is None:
+        return float(units), float(seconds)
+    import torch
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
 def run_ours(args, rank, world, dist):
     import torch
     from paper_2103_10239_gb300 import vk
@@ -310,12 +323,9 @@ def run_ours(args, rank, world, dist):
     total_ms = float(sum(step_ms))
     prof = sim.profile()
     sim.set_profiling(False)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * w.n * args.steps / (total_ms * 1e-3)
+    units, secs = reduce_job(dist, w.n * args.steps, total_ms * 1e-3, dev)
+    ms_per_step = secs * 1e3 / args.steps
+    value = units / secs
 
     # dominant kernel: the fused search + update
     su_ms, su_launches = prof["search_update"]
@@ -327,13 +337,13 @@ def run_ours(args, rank, world, dist):
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
-    if rank == 0 or True:
+    if True:  # every rank, so that the whole-job figure covers them all
         pos_h = torch.empty((w.n, 2), dtype=torch.int32, pin_memory=True)
         dir_h = torch.empty((w.n, 2), dtype=torch.float32, pin_memory=True)
         pos_h.numpy()[:] = w.pos_q
         dir_h.numpy()[:] = w.dir
         phi_h = np.zeros(1, dtype=np.float64)
-        torch.cuda.synchronize()
+        barrier()
         t_e = []
         for i in range(args.e2e_steps + 1):
             t0 = time.perf_counter()
@@ -343,7 +353,8 @@ def run_ours(args, rank, world, dist):
             phi_h[0] = sim.order_parameter(max_values=1)[-1]
             t_e.append(time.perf_counter() - t0)
         t_e = t_e[1:]
-        e2e = {"value": w.n / (sum(t_e) / len(t_e)), "unit": "particle-steps/s",
+        e_units, e_secs = reduce_job(dist, w.n * len(t_e), sum(t_e), dev)
+        e2e = {"value": e_units / e_secs, "unit": "particle-steps/s",
                "h2d_bytes_per_step": int(w.n * 16), "d2h_bytes_per_step": int(w.n * 16 + 8),
                "note": "vk_set_state from pinned host + vk_step(1) + vk_get_state to pinned host + phi"}
 

@@ -340,8 +340,8 @@ def run_ours(args, rank, world, dist):
     if True:  # every rank, so that the whole-job figure covers them all
         pos_h = torch.empty((w.n, 2), dtype=torch.int32, pin_memory=True)
         dir_h = torch.empty((w.n, 2), dtype=torch.float32, pin_memory=True)
-        pos_h.numpy()[:] = w.pos_q
-        dir_h.numpy()[:] = w.dir
+        # the host-driven loop continues the simulation from its current state
+        sim.get_state_into(0, pos_h, dir_h)
         phi_h = np.zeros(1, dtype=np.float64)
         barrier()
         t_e = []

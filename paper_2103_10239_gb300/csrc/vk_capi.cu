@@ -33,6 +33,10 @@ struct vk_sim {
   int n_rep = 0;
   int64_t n_total = 0;
   int64_t n_cells = 0;
+  // staging of vk_get_state / vk_set_state, allocated at the first call
+  int32_t* st_pos = nullptr;
+  float* st_dir = nullptr;
+  float* st_theta = nullptr;
   int64_t cells_cap = 0;
   std::vector<Rep> reps_h;
   std::vector<BlockTask> tasks_h;
@@ -575,17 +579,30 @@ vk_status vk_get_order_parameter(vk_sim* s, int32_t replica, double* phi, int64_
   return VK_OK;
 }
 
+// device staging for the largest replica (id-ordered arrays), kept for the
+// sim's lifetime so that state transfers allocate nothing per call
+vk_status ensure_staging(vk_sim* s) {
+  if (s->st_pos) return VK_OK;
+  int64_t nmax = 0;
+  for (const Rep& R : s->reps_h) nmax = std::max<int64_t>(nmax, R.n);
+  const size_t n = (size_t)std::max<int64_t>(nmax, 1), d = (size_t)s->dim;
+  cudaError_t e = dalloc(&s->st_pos, n * d);
+  if (e == cudaSuccess) e = dalloc(&s->st_dir, n * d);
+  if (e == cudaSuccess) e = dalloc(&s->st_theta, n);
+  if (e != cudaSuccess) return cuda_fail(s, e, "state staging");
+  return VK_OK;
+}
+
 vk_status vk_get_state(vk_sim* s, int32_t replica, int32_t* pos_q, float* dir, float* theta, int64_t* step) {
   if (!s || replica < 0 || replica >= s->n_rep) return fail(s, VK_ERR_ARG, "bad arguments");
   cudaStreamSynchronize(cudaStreamLegacy);
+  if (vk_status st = ensure_staging(s)) return st;
   const Rep& R = s->reps_h[replica];
   const size_t n = (size_t)R.n, d = (size_t)s->dim;
-  int32_t* pd = nullptr;
-  float* dd = nullptr;
-  float* td = nullptr;
-  cudaError_t e = dalloc(&pd, n * d);
-  if (e == cudaSuccess) e = dalloc(&dd, n * d);
-  if (e == cudaSuccess) e = dalloc(&td, n);
+  int32_t* pd = s->st_pos;
+  float* dd = s->st_dir;
+  float* td = s->st_theta;
+  cudaError_t e = cudaSuccess;
   if (e == cudaSuccess)
     e = launch_export_state(s->g, s->b, replica, R.p0, R.n, pd, dd, s->dim == 2 ? td : nullptr, s->stream);
   if (e == cudaSuccess && pos_q) e = cudaMemcpyAsync(pos_q, pd, sizeof(int32_t) * n * d, cudaMemcpyDefault, s->stream);
@@ -593,9 +610,6 @@ vk_status vk_get_state(vk_sim* s, int32_t replica, int32_t* pos_q, float* dir, f
   if (e == cudaSuccess && theta && s->dim == 2)
     e = cudaMemcpyAsync(theta, td, sizeof(float) * n, cudaMemcpyDefault, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-  cudaFree(pd);
-  cudaFree(dd);
-  cudaFree(td);
   if (e != cudaSuccess) return cuda_fail(s, e, "get_state");
   if (step) *step = s->step;
   return read_status(s);
@@ -608,24 +622,24 @@ vk_status vk_set_state(vk_sim* s, int32_t replica, const int32_t* pos_q, const f
   const size_t n = (size_t)R.n, d = (size_t)s->dim, N = (size_t)s->n_total;
   const size_t pv = s->dim == 2 ? sizeof(int2) : sizeof(int4);
   const size_t fv = s->dim == 2 ? sizeof(float2) : sizeof(float4);
-  int32_t* pd = nullptr;
-  float* dd = nullptr;
-  cudaError_t e = dalloc(&pd, n * d);
-  if (e == cudaSuccess) e = dalloc(&dd, n * d);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(pd, pos_q, sizeof(int32_t) * n * d, cudaMemcpyDefault, s->stream);
+  if (vk_status st = ensure_staging(s)) return st;
+  int32_t* pd = s->st_pos;
+  float* dd = s->st_dir;
+  cudaError_t e = cudaMemcpyAsync(pd, pos_q, sizeof(int32_t) * n * d, cudaMemcpyDefault, s->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dd, dir, sizeof(float) * n * d, cudaMemcpyDefault, s->stream);
   // every other replica keeps its state: S -> U, then overwrite this replica
-  if (e == cudaSuccess) e = cudaMemcpyAsync(s->b.U_pos, s->b.S_pos, pv * N, cudaMemcpyDeviceToDevice, s->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(s->b.U_dir, s->b.S_dir, fv * N, cudaMemcpyDeviceToDevice, s->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(s->b.U_id, s->b.S_id, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s->stream);
+  if (s->n_rep > 1) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->b.U_pos, s->b.S_pos, pv * N, cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->b.U_dir, s->b.S_dir, fv * N, cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s->b.U_id, s->b.S_id, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s->stream);
+  }
+  // the import flags positions outside the box (and wraps them into it, so
+  // that the sort below stays in bounds) and non-finite headings; the status
+  // is read once at the end
   if (e == cudaSuccess) e = launch_import_state(s->g, s->b, replica, R.p0, R.n, pd, dd, s->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-  cudaFree(pd);
-  cudaFree(dd);
   if (e != cudaSuccess) return cuda_fail(s, e, "set_state");
-  vk_status st = read_status(s);
-  if (st) return st;
+  vk_status st;
   if ((st = sort_from_U(s))) return st;
   if (step >= 0) {
     s->step = step;
@@ -668,7 +682,8 @@ void vk_destroy(vk_sim* s) {
   void* bufs[] = {s->b.S_pos, s->b.S_dir, s->b.S_id, s->b.U_pos, s->b.U_dir, s->b.U_id, s->b.U_rank,
                   s->b.counts, s->b.offsets, s->b.bsum, s->b.phi_acc, s->b.d_step, s->b.d_status,
                   s->b.ovf_list, s->b.ovf_count, s->reps_d, s->tasks_d, s->b.sub_s, s->b.sub_base,
-                  s->b.sub_count, s->b.sub_off, s->b.bsum2, s->d_stats, s->b.bounds};
+                  s->b.sub_count, s->b.sub_off, s->b.bsum2, s->d_stats, s->b.bounds,
+                  s->st_pos, s->st_dir, s->st_theta};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);

@@ -359,7 +359,10 @@ __global__ void __launch_bounds__(kBlock) import_state_kernel(
   for (int a = 0; a < DIM; ++a) {
     p[a] = pos_in[(int64_t)li * DIM + a];
     h[a] = dir_in[(int64_t)li * DIM + a];
-    if (p[a] < 0 || (uint32_t)p[a] >= L[a]) set_status(status, kStRange);
+    if (p[a] < 0 || (uint32_t)p[a] >= L[a]) {
+      set_status(status, kStRange);
+      p[a] = wrap_add(p[a], 0, L[a]);  // keeps the following sort in bounds; the call reports the error
+    }
     if (!isfinite(h[a])) set_status(status, kStArg);
   }
   U_pos[p0 + li] = make_p(p, (P*)nullptr);

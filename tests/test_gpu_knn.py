@@ -147,6 +147,30 @@ def test_theta_input_matches_dir_input():
     assert diff.max() < 1e-6
 
 
+def test_set_state_reports_bad_inputs():
+    """vk_set_state reports positions outside the box and non-finite
+    headings; a valid call afterwards restores a state that matches the
+    oracle (the status word is sticky, so a new simulation is used)."""
+    w = W.uniform_system(300, 17.0, 16, 2, input_seed=8, rule="knn", k=7)
+    bad = w.pos_q.copy()
+    bad[7, 1] = -5
+    with vk.from_workload(w) as sim:
+        with pytest.raises(vk.VKError) as e:
+            sim.set_state(bad, w.dir)
+        assert e.value.status == vk.VK_ERR_RANGE
+    d = w.dir.copy()
+    d[2, 0] = np.inf
+    with vk.from_workload(w) as sim:
+        with pytest.raises(vk.VKError) as e:
+            sim.set_state(w.pos_q, d)
+        assert e.value.status == vk.VK_ERR_ARG
+    with vk.from_workload(w) as sim:
+        sim.step(3)
+        sim.set_state(w.pos_q, w.dir, step=0)
+        assert np.array_equal(_knn_lists(sim, 7), oracle.knn(w.pos_q, w.box_q, 7))
+        check_step(sim, w, "knn")
+
+
 def test_input_errors():
     w = W.uniform_system(100, 10.0, 16, 2, input_seed=1)
     bad = w.pos_q.copy()

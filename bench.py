@@ -144,10 +144,10 @@ def measured_peaks():
 
 
 def kernel_source_sha() -> str:
+    """Hash of the sources the dominant kernel (knn2_step_kernel) is built from."""
     h = hashlib.sha256()
-    for f in sorted(os.listdir(CSRC)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(CSRC, f), "rb").read())
+    for f in ("vk_internal.cuh", "vk_knn2d.cu"):
+        h.update(open(os.path.join(CSRC, f), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -147,6 +147,10 @@ struct RunGen {
   int sstride;
   bool in_rect;
   bool own_done;
+  // the box [p - rad, p + rad] stays within every ring's representative cell
+  // offsets (so a cell meets it at its visited offset only) while rad < safe
+  int64_t safe;
+  int64_t prad;  // radius used to skip rows and cells of the current part (-1: none)
   // split cells met while the search radius was still unknown, revisited at
   // the end of the ring (when it usually is known)
   int ndef;
@@ -203,10 +207,7 @@ __device__ __forceinline__ bool gen_rect(RunGen& g, int64_t gc, int ucx, int ucy
   // large radius), the cell can meet the box through another periodic image:
   // then all of it is scanned (every candidate is measured by its minimum
   // image, so scanning more is always correct).
-  if (rad >= g.px - cell_lo_tab(g.cx - (g.nx - 1) / 2, g.nx, g.bx, R.L[0]) ||
-      rad >= cell_lo_tab(g.cx + g.nx / 2 + 1, g.nx, g.bx, R.L[0]) - g.px ||
-      rad >= g.py - cell_lo_tab(g.cy - (g.ny - 1) / 2, g.ny, g.by, R.L[1]) ||
-      rad >= cell_lo_tab(g.cy + g.ny / 2 + 1, g.ny, g.by, R.L[1]) - g.py) {
+  if (rad >= g.safe) {
     g.sx0r = 0; g.sx1r = s - 1; g.sr = 0; g.sr1 = s - 1;
     g.in_rect = true;
     return true;
@@ -260,6 +261,11 @@ __device__ __forceinline__ void gen_init(RunGen& g, const Rep& R, const uint32_t
   g.cx = cell_of_tab(px, g.nx, g.bx, R.inv_w[0]);
   g.cy = cell_of_tab(py, g.ny, g.by, R.inv_w[1]);
   g.own = R.c0 + (int64_t)g.cy * g.nx + g.cx;
+  g.safe = min(min((int64_t)px - cell_lo_tab(g.cx - (g.nx - 1) / 2, g.nx, g.bx, R.L[0]),
+                   cell_lo_tab(g.cx + g.nx / 2 + 1, g.nx, g.bx, R.L[0]) - (int64_t)px),
+               min((int64_t)py - cell_lo_tab(g.cy - (g.ny - 1) / 2, g.ny, g.by, R.L[1]),
+                   cell_lo_tab(g.cy + g.ny / 2 + 1, g.ny, g.by, R.L[1]) - (int64_t)py));
+  g.prad = -1;
   g.own_done = false;
   g.in_rect = false;
   g.ndef = 0;
@@ -402,6 +408,20 @@ __device__ __forceinline__ int gen_next(RunGen& g, uint64_t r2, uint32_t& qb, ui
     }
     const int x0 = g.pa[g.part], x1 = g.pb[g.part];
     if (g.x < 0) {  // start of a part: one run when no cell in it is split
+      // once the radius is known, a row that misses the box is skipped, and
+      // so are (below) its cells that miss it
+      g.prad = -1;
+      if (r2 != ~0ull) {
+        const int64_t rad = radius_upper(r2);
+        if (rad < g.safe) {
+          if (cell_lo_tab(g.ucy, g.ny, g.by, g.R->L[1]) > g.py + rad ||
+              cell_lo_tab(g.ucy + 1, g.ny, g.by, g.R->L[1]) <= g.py - rad) {
+            ++g.part;
+            continue;
+          }
+          g.prad = rad;
+        }
+      }
       const uint32_t sb0 = __ldg(G.sub_base + g.rowbase + x0), sb1 = __ldg(G.sub_base + g.rowbase + x1 + 1);
       if (sb1 - sb0 == (uint32_t)(x1 - x0 + 1)) {
         ++g.part;
@@ -415,6 +435,14 @@ __device__ __forceinline__ int gen_next(RunGen& g, uint64_t r2, uint32_t& qb, ui
       ++g.part;
       g.x = -1;
       continue;
+    }
+    if (g.prad >= 0) {
+      const int ucx = g.pu[g.part] + (g.x - x0);
+      if (cell_lo_tab(ucx, g.nx, g.bx, g.R->L[0]) > g.px + g.prad ||
+          cell_lo_tab(ucx + 1, g.nx, g.bx, g.R->L[0]) <= g.px - g.prad) {
+        ++g.x;
+        continue;
+      }
     }
     // per cell: a maximal run of unsplit cells, or one split cell
     const int64_t gc = g.rowbase + g.x;

@@ -59,3 +59,19 @@ def test_reference_arm_runs_on_rank_zero_only():
     import bench
     # any rank other than 0 returns at once, without touching the oracle
     assert bench.run_reference(None, 1, 2) is None
+
+
+def test_oracle_legs_of_the_bench_on_small_systems():
+    """The bench's CPU legs (the oracle timed as it stands) run without a GPU:
+    a bounded kNN sample, a 3D sample and a whole Voronoi step."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2103_10239_gb300 import workloads as W
+    w = W.uniform_system(3000, 54.0, 16, 2, input_seed=4, rule="knn", k=7, v0=0.5, eta=0.3)
+    rate, m, cores, secs = bench.oracle_sample_rate(w, 0.05)
+    assert rate > 0 and 32 <= m <= w.n and cores >= 1 and secs > 0
+    w3 = W.uniform_system(2000, 12.6, 16, 3, input_seed=5, rule="knn", k=7, v0=0.5, eta=0.3, noise="vectorial")
+    assert bench.scenario_cpu_baseline(w3, 0.05)["value"] > 0
+    wv = W.uniform_system(500, 22.4, 16, 2, input_seed=6, rule="voronoi", k=0, v0=0.3, eta=0.1)
+    cb = bench.scenario_cpu_baseline(wv, 0.05)
+    assert cb["value"] > 0 and cb["kind"] == "oracle" and cb["cores"] == 1

@@ -251,7 +251,7 @@ def run_reference(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
-            "config": workload_config(w, args),
+            "config": dict(workload_config(w, args), cell_occupancy=args.occupancy),
             "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"{m_used} random particles per step: brute-force kNN over all "
                                        f"{w.n} + FP64 update"},

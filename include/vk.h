@@ -41,9 +41,15 @@
  *
  * Errors
  *   - Every call returns a vk_status and never aborts.  Device-side failures
- *     (capacity overflow, coincident points under the Voronoi rule) latch a
- *     sticky status word on the device; it is returned by the next vk_sync or
- *     vk_get_* call.  vk_last_error gives a message for the last failure.
+ *     (capacity overflow, values out of range) latch a sticky status word on
+ *     the device; it is returned by the next vk_sync or vk_get_* call.
+ *     vk_last_error gives a message for the last failure.
+ *   - Coincident particles are valid input under both rules.  The paper
+ *     leaves the Voronoi cell of coincident points undefined; this library
+ *     reads them as one Voronoi site: they are each other's neighbors and
+ *     share the site's other neighbors.  (An earlier reading returned
+ *     VK_ERR_DEGENERATE; coincident points do occur on the fixed-point grid
+ *     in long runs, so an error would end the simulation.)
  */
 #ifndef VK_NM_H
 #define VK_NM_H
@@ -63,7 +69,7 @@ typedef enum {
   VK_ERR_OOM = 3,        /* device allocation failed */
   VK_ERR_CAPACITY = 4,   /* an output buffer or an internal bound was too small */
   VK_ERR_RANGE = 5,      /* box / fixed-point range outside the supported limits */
-  VK_ERR_DEGENERATE = 6, /* coincident points under the Voronoi rule */
+  VK_ERR_DEGENERATE = 6, /* reserved: no current call returns it (coincident points are one site) */
   VK_ERR_TIMEOUT = 7,    /* a bounded device wait gave up */
   VK_ERR_STATE = 8       /* call not valid in the current state */
 } vk_status;
@@ -129,27 +135,38 @@ vk_status vk_batch_init(int32_t n_rep, const int64_t* n_r, const int32_t* pos_q,
 vk_status vk_step(vk_sim* sim, int64_t nsteps);
 
 /* Neighbor lists of the CURRENT positions of one replica, in id order:
- * offsets (n+1 int64, CSR) and ids (int32).  If ids_capacity is too small
- * (or ids is NULL), *nnz_needed receives the count and VK_ERR_CAPACITY is
- * returned (VK_OK when ids is NULL).  Synchronous. */
+ * offsets (n+1 int64, CSR) and ids (int32).  kNN rule: the k nearest other
+ * particles at any distance, not reciprocal (Sec. "Metric and topological
+ * flocking models"), row i ordered by (D, id).  Voronoi rule: the particles
+ * whose Voronoi cell shares an edge of positive length with i's, i.e. the
+ * Delaunay neighbors by the empty-circumcircle property (Sec. "Computational
+ * tools: Voronoi neighbor lists"), row i sorted by id.  These are the lists
+ * the next vk_step uses.  If ids_capacity is too small (or ids is NULL),
+ * *nnz_needed receives the count and VK_ERR_CAPACITY is returned (VK_OK when
+ * ids is NULL).  Synchronous. */
 vk_status vk_get_neighbors(vk_sim* sim, int32_t replica, int64_t* offsets, int32_t* ids,
                            int64_t ids_capacity, int64_t* nnz_needed);
 
 /* Polar order parameter phi(t) = |sum_i n_i(t)| / N of one replica after
  * each of the last *count steps (oldest first; at most phi_capacity and at
- * most max_values are written).  Sums are FP32 compensated per block and FP64
- * across blocks.  Synchronous. */
+ * most max_values are written).  The paper does not define it: it is the
+ * standard observable of the Vicsek model whose dynamics Eq. (1)-(2) state.
+ * Sums are FP32 compensated per block and FP64 across blocks.  Synchronous. */
 vk_status vk_get_order_parameter(vk_sim* sim, int32_t replica, double* phi, int64_t max_values,
                                  int64_t* count);
 
-/* Current state of one replica in id order: pos_q (n*dim int32), dir (n*dim
- * FP32), theta (n FP32, 2D; may be NULL), step counter.  Any output may be
- * NULL.  Synchronous. */
+/* Current state of one replica in id order: the positions r_i of Eq. (1)
+ * as pos_q (n*dim int32), the headings n_i of Eq. (2) as dir (n*dim FP32),
+ * theta = atan2(n_y, n_x) in [0, 2pi) (n FP32, 2D; may be NULL), and the
+ * step counter t.  Any output may be NULL.  Synchronous. */
 vk_status vk_get_state(vk_sim* sim, int32_t replica, int32_t* pos_q, float* dir, float* theta,
                        int64_t* step);
 
-/* Overwrite the state of one replica (id order) and, if step >= 0, the step
- * counter of the whole simulation (teacher forcing, checkpoint resume). */
+/* Overwrite the state (r_i, n_i) of Eq. (1)-(2) of one replica (id order,
+ * same layout as vk_get_state) and, if step >= 0, the step counter of the
+ * whole simulation (teacher forcing, checkpoint resume).  Positions outside
+ * [0, L_q) give VK_ERR_RANGE and non-finite headings VK_ERR_ARG.
+ * Synchronous. */
 vk_status vk_set_state(vk_sim* sim, int32_t replica, const int32_t* pos_q, const float* dir,
                        int64_t step);
 

@@ -51,6 +51,10 @@ def parse():
                     help="coarse-grid occupancy (particles per cell) of the headline run; 2048 was the "
                          "fastest of a sweep on the clustered 4M workload (1024: 5.59, 2048: 5.38, "
                          "4096: 5.37 ms/step)")
+    ap.add_argument("--search", choices=["tile", "walk"], default="tile",
+                    help="2D kNN search: warp tiles (default) or the per-particle walk only")
+    ap.add_argument("--halo", type=float, default=0.0,
+                    help="warp-tile halo as a multiple of the previous k-th distance (0: library default)")
     ap.add_argument("--autotune", action="store_true",
                     help="let the library's autotuner pick the occupancy on the warmed-up state instead")
     ap.add_argument("--scenario", choices=["headline", "replicas", "voronoi", "knn3d"], default="headline",
@@ -68,7 +72,7 @@ def workload(args, rank=0):
 def workload_config(w, args):
     return {"workload": w.name, "n": w.n, "rule": w.rule, "k": w.k, "dim": w.dim,
             "frac_bits": w.frac_bits, "box_q": int(w.box_q[0]), "density": round(w.density, 4),
-            "v0": w.v0, "eta": w.eta, "layout": args.layout,
+            "v0": w.v0, "eta": w.eta, "layout": args.layout, "search": args.search,
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
@@ -251,13 +255,24 @@ def run_reference(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
-            "config": dict(workload_config(w, args), cell_occupancy=args.occupancy),
+            "config": dict(workload_config(w, args), cell_occupancy=args.occupancy, l2_bytes=_l2_bytes()),
             "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"{m_used} random particles per step: brute-force kNN over all "
                                        f"{w.n} + FP64 update"},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _l2_bytes():
+    """L2 size of GPU 0, as the measured arm records it (None without a GPU)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.get_device_properties(0).L2_cache_size)
+    except Exception:
+        pass
+    return None
 
 
 def reduce_job(dist, units: float, seconds: float, device):
@@ -286,7 +301,8 @@ def run_ours(args, rank, world, dist):
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    sim = vk.from_workload(w, stream=stream, cell_occupancy=args.occupancy)
+    sim = vk.from_workload(w, stream=stream, cell_occupancy=args.occupancy,
+                           knn_search=0 if args.search == "tile" else 1, search_halo=args.halo)
     sim.step(args.warmup)
     occupancy = args.occupancy
     if args.autotune:

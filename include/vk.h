@@ -105,6 +105,13 @@ typedef struct {
                            Dense coarse cells get sub-grids of about 2 particles per sub-cell.
                            Results never depend on it; only the speed does. */
   int32_t phi_capacity; /* order-parameter history kept per replica; 0 = 4096 steps */
+  int32_t knn_search;   /* 2D kNN search: 0 = radius first (default), 1 = per-particle walk only.
+                           Results never depend on it; only the speed does. */
+  float search_halo;    /* radius first: half-width of a particle's search square, as a multiple
+                           of its k-th neighbor distance at the previous step; 0 = default (1.25).
+                           Results never depend on it; only the speed does. */
+  float search_halo_step; /* radius first: plus this multiple of the distance a particle moves
+                           in one step (v0 dt); < 0 = default (0).  Speed only. */
 } vk_params;
 
 /* Fills p with the defaults: kNN, k = 7, v0 = 0.5, dt = 1, eta = 0.3, seed = 1,
@@ -197,11 +204,26 @@ const char* vk_phase_name(int32_t phase);
 
 /* Search counters of the neighbor search while tracing was on (level 2):
  * mean candidates examined per particle update, mean contiguous slot runs
- * read per particle update, the largest candidate count of one particle, and
- * the fraction of particle updates whose own coarse cell was split into
- * sub-cells.  Any output may be NULL. */
+ * read per particle update (2D kNN radius first: mean squares scanned), the
+ * largest candidate count of one particle, and the fraction of particle
+ * updates whose own coarse cell was split into sub-cells (2D kNN radius
+ * first: that fell back to the per-particle walk).  Any output may be NULL. */
 vk_status vk_get_search_stats(vk_sim* sim, double* mean_candidates, double* mean_runs,
                               int64_t* max_candidates, double* split_fraction);
+
+/* Raw totals of the search counters collected while tracing at level 2, in
+ * this order: 0 candidates examined (summed over particle updates), 1 slot
+ * runs (walk) or squares scanned (radius first), 2 largest candidate count
+ * of one particle update, 3 particle updates, 4 updates whose own coarse
+ * cell was split (walk) or that fell back to the walk (radius first); radius
+ * first only, over the particles it served or handed on: 5 squares scanned,
+ * 6 slot runs, 7 candidates, 8 coarse cells visited, 9 hits merged, and the
+ * particles the step kernel deferred because 10 the square was too wide for
+ * the box or listed too many slot runs (these go straight to the walk),
+ * 11 the square held fewer than k hits (a larger square follows), 12 two
+ * candidates were at the same distance (walk), 13 (unused, 0).  Writes
+ * min(max_values, 14) values; *n (may be NULL) receives 14. */
+vk_status vk_get_search_counters(vk_sim* sim, int64_t* values, int32_t max_values, int32_t* n);
 
 /* Sizes chosen at init: total particles, replicas, cells of the search grid. */
 typedef struct {

@@ -21,6 +21,7 @@ using namespace vk;
 namespace {
 
 constexpr int kPhases = 5;
+constexpr int kCounters = 14;  // search counters (tracing level 2)
 const char* kPhaseNames[kPhases] = {"search_update", "build", "scatter", "load_sort", "export"};
 
 thread_local std::string g_init_error;
@@ -104,6 +105,9 @@ StepParams step_params(const vk_sim* s) {
   P.seed_hi = (uint32_t)(s->prm.seed >> 32);
   P.n_rep = s->n_rep;
   P.phi_cap = s->phi_cap;
+  P.knn_search = s->prm.knn_search;
+  P.halo_alpha = s->prm.search_halo > 0.f ? s->prm.search_halo : 1.25f;
+  P.halo_beta = s->prm.search_halo_step >= 0.f ? s->prm.search_halo_step : 0.f;
   P.stats = (s->prof && s->prof_counters) ? s->d_stats : nullptr;
   return P;
 }
@@ -223,6 +227,8 @@ vk_status sort_from_U(vk_sim* s) {
   cudaEvent_t e0 = nullptr;
   vk_status st = record_begin(s, 3, &e0);
   if (st) return st;
+  // a new state: the previous k-th distances no longer describe it
+  if (s->b.U_hint) VK_CUDA(s, cudaMemsetAsync(s->b.U_hint, 0, sizeof(float) * (size_t)s->n_total, s->stream));
   VK_CUDA(s, launch_count(s->g, s->b, s->stream));
   VK_CUDA(s, launch_build(s->g, s->b, s->stream));
   VK_CUDA(s, launch_scatter(s->g, s->b, step_params(s), 0, s->stream));
@@ -247,9 +253,13 @@ vk_status clear_phi(vk_sim* s) {
   return VK_OK;
 }
 
-// kernels of the search+update phase: one for kNN; the Voronoi kernel and
-// its overflow kernel
-int search_launches(const vk_sim* s) { return s->prm.rule == VK_RULE_KNN ? 1 : 2; }
+// kernels of the search+update phase: for 2D kNN the radius-first kernel
+// and the walk-list kernel (one kernel with the walk only); one for 3D kNN;
+// the Voronoi kernel and its overflow kernel
+int search_launches(const vk_sim* s) {
+  if (s->prm.rule == VK_RULE_KNN) return (s->dim == 2 && s->prm.knn_search == 0) ? 2 : 1;
+  return 2;
+}
 
 vk_status enqueue_step(vk_sim* s) {
   const StepParams P = step_params(s);
@@ -303,6 +313,9 @@ bool valid_params(const vk_params* p, int dim, std::string* why) {
   if (!std::isfinite(p->v0) || !std::isfinite(p->dt) || !std::isfinite(p->eta))
     return *why = "v0, dt and eta must be finite", false;
   if (p->phi_capacity < 0 || p->phi_capacity == 1) return *why = "phi_capacity must be 0 or >= 2", false;
+  if (p->knn_search != 0 && p->knn_search != 1) return *why = "knn_search must be 0 or 1", false;
+  if (!(p->search_halo >= 0.f) || !std::isfinite(p->search_halo)) return *why = "search_halo must be >= 0", false;
+  if (!std::isfinite(p->search_halo_step)) return *why = "search_halo_step must be finite", false;
   return true;
 }
 
@@ -398,9 +411,13 @@ vk_status build_sim(int32_t n_rep, const int64_t* n_r, const int32_t* pos_q, con
       (e = dalloc(&s->b.phi_acc, 3 * (size_t)s->phi_cap * n_rep)) || (e = dalloc(&s->b.d_step, 1)) ||
       (e = dalloc(&s->b.d_status, 1)) || (e = dalloc(&s->reps_d, n_rep)) ||
       (e = dalloc(&s->b.ovf_list, N)) || (e = dalloc(&s->b.ovf_count, 1)) ||
-      (e = dalloc(&s->d_stats, 6)) ||
+      (e = dalloc(&s->d_stats, kCounters)) ||
       (e = dalloc(&s->tasks_d, s->tasks_h.size())))
     return bail(cuda_fail(s, e, "cudaMalloc"));
+  if (params->rule == VK_RULE_KNN && dim == 2) {
+    if ((e = dalloc(&s->b.S_hint, N)) || (e = dalloc(&s->b.U_hint, N)) || (e = prepare_knn2()))
+      return bail(cuda_fail(s, e, "kNN search buffers"));
+  }
   if (ensure_cells_capacity(s)) return bail(VK_ERR_OOM);
   if ((e = cudaMemsetAsync(s->b.d_step, 0, sizeof(int64_t), s->stream)) ||
       (e = cudaMemsetAsync(s->b.ovf_count, 0, sizeof(int32_t), s->stream)) ||
@@ -453,6 +470,9 @@ void vk_default_params(vk_params* p) {
   p->sum_mode = VK_SUM_COMPENSATED;
   p->cell_occupancy = 0.f;
   p->phi_capacity = 0;
+  p->knn_search = 0;
+  p->search_halo = 0.f;
+  p->search_halo_step = -1.f;
 }
 
 vk_status vk_init(const int32_t* pos_q, const float* heading, int32_t heading_kind, int64_t n,
@@ -508,7 +528,8 @@ vk_status vk_get_neighbors(vk_sim* s, int32_t replica, int64_t* offsets, int32_t
     const int k = s->prm.k;
     int32_t* out_d = nullptr;
     VK_CUDA(s, dalloc(&out_d, (size_t)n * k));
-    cudaError_t e = s->dim == 2 ? launch_knn2_export(s->g, s->b, k, replica, (int)n, out_d, s->stream)
+    cudaError_t e = s->dim == 2 ? launch_knn2_export(s->g, s->b, k, replica, (int)n, out_d, s->stream,
+                                                     step_params(s))
                                 : launch_knn_export(s->g, s->b, k, replica, (int)n, out_d, s->stream);
     if (e == cudaSuccess) {
       ids_h.resize((size_t)n * k);
@@ -683,7 +704,7 @@ void vk_destroy(vk_sim* s) {
                   s->b.counts, s->b.offsets, s->b.bsum, s->b.phi_acc, s->b.d_step, s->b.d_status,
                   s->b.ovf_list, s->b.ovf_count, s->reps_d, s->tasks_d, s->b.sub_s, s->b.sub_base,
                   s->b.sub_count, s->b.sub_off, s->b.bsum2, s->d_stats, s->b.bounds,
-                  s->st_pos, s->st_dir, s->st_theta};
+                  s->st_pos, s->st_dir, s->st_theta, s->b.S_hint, s->b.U_hint};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -704,7 +725,7 @@ vk_status vk_set_profiling(vk_sim* s, int32_t enable) {
   drop_graph(s);  // the captured launches carry the tracing switch
   if (s->prof) {
     cudaStreamSynchronize(s->stream);
-    VK_CUDA(s, cudaMemsetAsync(s->d_stats, 0, 6 * sizeof(unsigned long long), s->stream));
+    VK_CUDA(s, cudaMemsetAsync(s->d_stats, 0, kCounters * sizeof(unsigned long long), s->stream));
     for (int p = 0; p < kPhases; ++p) {
       for (auto& pr : s->ev[p]) {
         cudaEventDestroy(pr.first);
@@ -751,6 +772,16 @@ vk_status vk_get_search_stats(vk_sim* s, double* mean_candidates, double* mean_r
   if (mean_runs) *mean_runs = (double)h[1] / n;
   if (max_candidates) *max_candidates = (int64_t)h[2];
   if (split_fraction) *split_fraction = h[3] ? (double)h[4] / (double)h[3] : 0.0;
+  return VK_OK;
+}
+
+vk_status vk_get_search_counters(vk_sim* s, int64_t* values, int32_t max_values, int32_t* n) {
+  if (!s || (max_values > 0 && !values)) return fail(s, VK_ERR_ARG, "bad arguments");
+  unsigned long long h[kCounters] = {};
+  VK_CUDA(s, cudaMemcpyAsync(h, s->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+  VK_CUDA(s, cudaStreamSynchronize(s->stream));
+  for (int i = 0; i < std::min<int>(kCounters, std::max<int>(0, max_values)); ++i) values[i] = (int64_t)h[i];
+  if (n) *n = kCounters;
   return VK_OK;
 }
 

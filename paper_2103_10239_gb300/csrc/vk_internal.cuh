@@ -56,8 +56,16 @@ struct StepParams {
   uint32_t seed_lo, seed_hi;
   int32_t n_rep;
   int32_t phi_cap;
-  // tracing only (NULL = off): [candidates, runs, max candidates, particles,
-  // particles whose own coarse cell is split]
+  // 2D kNN search: 0 = radius first (per-particle walk as the last resort),
+  // 1 = per-particle walk only
+  int32_t knn_search;
+  // radius-first search square: halo_alpha * (the particle's k-th distance at
+  // the previous step) + halo_beta * (grid step per unit heading)
+  float halo_alpha, halo_beta;
+  // tracing only (NULL = off): [candidates, runs or squares, max candidates,
+  // particles, particles whose own coarse cell is split (walk) or that fell
+  // back to the walk (radius first), then radius first only: squares, runs,
+  // candidates, coarse cells, hits]
   unsigned long long* stats;
 };
 
@@ -209,7 +217,10 @@ __device__ __forceinline__ int32_t wrap_add(int32_t p, int32_t d, uint32_t L) {
 // row-major), so every row of sub-cells, and every row of coarse cells, is a
 // contiguous run of the sorted arrays.
 // --------------------------------------------------------------------------
-constexpr int kSubMax = 64;      // largest sub-grid side (sub_s is 8 bits)
+#ifndef VK_SUB_MAX
+#define VK_SUB_MAX 64
+#endif
+constexpr int kSubMax = VK_SUB_MAX;  // largest sub-grid side (sub_s is 8 bits: at most 255)
 constexpr int kSubTarget = 2;    // target particles per sub-cell
 
 __device__ __host__ __forceinline__ int sub_side(uint32_t m) {
@@ -582,6 +593,11 @@ struct Buffers {
   int32_t* d_status;
   int2* ovf_list;      // Voronoi: (slot, replica) of cells too large for the main kernel
   int32_t* ovf_count;
+  // 2D kNN: each particle's k-th neighbor distance (grid units) found at the
+  // previous step, in S order, and the one found now in U order (0 = unknown);
+  // only a search hint, results never depend on it (NULL for other rules)
+  float* S_hint;
+  float* U_hint;
 };
 
 struct Geometry {
@@ -618,7 +634,9 @@ cudaError_t launch_knn_export(const Geometry& g, const Buffers& b, int k, int re
 // vk_knn2d.cu (the 2D kNN hot path)
 cudaError_t launch_knn2_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st);
 cudaError_t launch_knn2_export(const Geometry& g, const Buffers& b, int k, int rep, int n, int32_t* out,
-                               cudaStream_t st);
+                               cudaStream_t st, const StepParams& P);
+// one-time kernel attributes (shared memory of the radius-first search)
+cudaError_t prepare_knn2();
 
 // vk_voronoi.cu
 cudaError_t launch_voronoi_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st);

@@ -11,13 +11,22 @@
 //   * the block's order-parameter partials are combined by the last warp to
 //     finish (no barrier that would hold finished warps).
 // The search is the two-level walk documented in vk_internal.cuh.
+#include <algorithm>
 #include <climits>
 
 #include "vk_internal.cuh"
 
-// resident 256-thread blocks per SM the step kernel is compiled for (register budget)
+// resident 256-thread blocks per SM the step kernels are compiled for
+// (register budget): the per-particle walk, and the radius-first search
 #ifndef VK_KNN2_MIN_BLOCKS
 #define VK_KNN2_MIN_BLOCKS 4
+#endif
+#ifndef VK_KNN2_BOX_BLOCKS
+#define VK_KNN2_BOX_BLOCKS 3
+#endif
+// slot runs one square of the radius-first search may list
+#ifndef VK_KNN2_BOX_RUNS
+#define VK_KNN2_BOX_RUNS 16
 #endif
 
 namespace vk {
@@ -632,6 +641,430 @@ __global__ void __launch_bounds__(kBlock, 2) knn2_export_kernel(const Rep* __res
     if (j >= KC - k) out[(int64_t)id * k + (j - (KC - k))] = __ldg(S_id + T.slot[j]);
 }
 
+// ---------------------------------------------------------------------------
+// Radius-first search (the default).  Each particle knows roughly how far
+// its k-th neighbor is: its k-th distance at the previous step, kept as a
+// per-particle hint in the state (particles move by at most v0 dt per step,
+// and neighbors mostly move together).  So it scans, once, every particle of
+// the square [p - a, p + a], a a little above that distance: the sub-cell
+// rows of the one to four coarse cells that overlap the square, each a
+// contiguous run of the sorted arrays.  A candidate whose exact int64
+// squared distance D is <= tau = (a+1)^2 - 1 goes to the particle's short
+// hit list in shared memory; nothing outside the square is that close, so
+// with at least k hits the k best hits by (D, id) are exactly the k nearest.
+// The hits are merged into the register top-k by a branch-free insertion on
+// D.  With fewer than k hits the square doubles and the scan repeats.  Equal
+// distances (the ids must decide), a full hit list, or a square wider than
+// half the period hand the particle to the per-particle walk, which runs in
+// a separate kernel over a device list so that its code and registers stay
+// out of this one; so do particles that need a second square, so that a
+// warp never waits for one particle's rescan.
+// ---------------------------------------------------------------------------
+constexpr int kBoxTries = 4;  // square sizes tried before the walk takes over
+
+template <int KC>
+struct BoxHits {
+  static constexpr int kCap = KC + 16;  // buffered hits per particle (merged when full)
+  static constexpr int kRuns = VK_KNN2_BOX_RUNS;  // slot runs of one square
+  int32_t slot[kCap][kBlock];           // one column per thread
+  uint2 run[kRuns][kBlock];             // (first slot, length << 4 | image shift codes)
+};
+
+// tracing counters of the radius-first search
+struct BoxCount {
+  uint32_t cand = 0;   // candidates examined
+  uint32_t tries = 0;  // squares scanned
+  uint32_t runs = 0;   // contiguous slot runs read
+  uint32_t hits = 0;   // hits merged
+  uint32_t cells = 0;  // coarse cells visited
+  uint32_t why = 0;    // fallback reason: 0 none, 1 square too wide (or too many runs), 2 too few hits, 3 tie
+};
+
+// unwrapped coarse-cell index of an unwrapped coordinate x, -L <= x < 2L
+__device__ __forceinline__ int box_ucell(int64_t x, int n, const uint32_t* __restrict__ bnd, float inv_w, int64_t L) {
+  if (x < 0) return cell_of_tab((uint32_t)(x + L), n, bnd, inv_w) - n;
+  if (x >= L) return cell_of_tab((uint32_t)(x - L), n, bnd, inv_w) + n;
+  return cell_of_tab((uint32_t)x, n, bnd, inv_w);
+}
+
+__device__ __forceinline__ uint64_t box_dist2(const Ctx& C, int2 pj) {
+  int32_t dx = (int32_t)((uint32_t)pj.x - C.px);
+  int32_t dy = (int32_t)((uint32_t)pj.y - C.py);
+  if (dx > C.hix) dx = (int32_t)((uint32_t)dx - C.Lx);
+  else if (dx <= C.lox) dx = (int32_t)((uint32_t)dx + C.Lx);
+  if (dy > C.hiy) dy = (int32_t)((uint32_t)dy - C.Ly);
+  else if (dy <= C.loy) dy = (int32_t)((uint32_t)dy + C.Ly);
+  return (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy);
+}
+
+// Merge the thread's hits into T by a branch-free insertion on D.  Sets
+// *tie if two candidates at the same distance met (their order, or which of
+// them is kept, needs the ids: the caller falls back to the walk).
+template <int KC>
+__device__ __forceinline__ void box_merge(const BoxHits<KC>& H, int cnt, const Ctx& C, const int2* __restrict__ pos,
+                                          Top<KC>& T, bool* tie) {
+  bool t = false;
+  for (int b = 0; b < cnt; ++b) {
+    const int32_t q = H.slot[b][threadIdx.x];
+    const uint64_t D = box_dist2(C, __ldg(pos + q));
+    t |= D == T.d[KC - 1];
+    if (D < T.d[KC - 1]) {
+      bool lt_hi = true;
+#pragma unroll
+      for (int s = KC - 1; s > 0; --s) {
+        const bool lt_lo = D < T.d[s - 1];
+        t |= D == T.d[s - 1];
+        const uint64_t nd = lt_lo ? T.d[s - 1] : (lt_hi ? D : T.d[s]);
+        const int32_t ns = lt_lo ? T.slot[s - 1] : (lt_hi ? q : T.slot[s]);
+        T.d[s] = nd;
+        T.slot[s] = ns;
+        lt_hi = lt_lo;
+      }
+      if (lt_hi) {
+        T.d[0] = D;
+        T.slot[0] = q;
+      }
+    }
+  }
+  *tie = *tie || t;
+}
+
+// Scan the square [p - a, p + a] into T (initialised by the caller): every
+// slot other than self with D <= tau = (a+1)^2 - 1 is a hit.  First the
+// square's slot runs (the sub-cell rows of the coarse cells it meets) are
+// listed, each with the periodic image its cell lies in; then one flat loop
+// walks all of them, so that threads of a warp whose squares split into
+// different numbers of runs still scan candidates together.  Hits are
+// buffered and merged into T at the end (and, rarely, when the buffer
+// fills, after which tau shrinks to T's k-th distance).  Returns the number of hits
+// (>= k exactly when T is full), or -1 when the square is too wide for the
+// minimum image, meets a coarse cell through two periodic images, or has
+// more runs than the list holds.
+template <int KC>
+__device__ __forceinline__ int box_scan(BoxHits<KC>& H, const Rep& R, const uint32_t* __restrict__ bounds,
+                                        const GridView& G, const int2* __restrict__ pos, const Ctx& C, int64_t a,
+                                        Top<KC>& T, bool* tie, BoxCount& bc) {
+  const int64_t Lx = C.Lx, Ly = C.Ly;
+  if (2 * (2 * a + 1) >= Lx || 2 * (2 * a + 1) >= Ly) return -1;
+  uint64_t tau = (uint64_t)(a + 1) * (uint64_t)(a + 1) - 1;
+  const int nx = R.nc[0], ny = R.nc[1];
+  const uint32_t* bx = bounds + R.bnd[0];
+  const uint32_t* by = bounds + R.bnd[1];
+  const int64_t qx0 = (int64_t)C.px - a, qx1 = (int64_t)C.px + a;
+  const int64_t qy0 = (int64_t)C.py - a, qy1 = (int64_t)C.py + a;
+  const int ucx0 = box_ucell(qx0, nx, bx, R.inv_w[0], Lx), ucx1 = box_ucell(qx1, nx, bx, R.inv_w[0], Lx);
+  const int ucy0 = box_ucell(qy0, ny, by, R.inv_w[1], Ly), ucy1 = box_ucell(qy1, ny, by, R.inv_w[1], Ly);
+  if (ucx1 - ucx0 + 1 > nx || ucy1 - ucy0 + 1 > ny) return -1;
+  bc.tries += 1;
+  // list the runs; shift code per axis: 0 same image, 1 the image at -L, 2 at +L
+  int nrun = 0;
+  for (int ucy = ucy0; ucy <= ucy1; ++ucy) {
+    const int cy = ucy < 0 ? ucy + ny : (ucy >= ny ? ucy - ny : ucy);
+    const uint32_t ycode = ucy < 0 ? 1u : (ucy >= ny ? 2u : 0u);
+    const int64_t y0c = cell_lo_tab(ucy, ny, by, Ly);
+    const int64_t wy = cell_lo_tab(ucy + 1, ny, by, Ly) - y0c;
+    const int64_t ly0 = max(qy0 - y0c, (int64_t)0), ly1 = min(qy1 - y0c, wy - 1);
+    for (int ucx = ucx0; ucx <= ucx1; ++ucx) {
+      const int cx = ucx < 0 ? ucx + nx : (ucx >= nx ? ucx - nx : ucx);
+      const uint32_t code = (ucx < 0 ? 1u : (ucx >= nx ? 2u : 0u)) << 2 | ycode;
+      const int64_t gc = R.c0 + (int64_t)cy * nx + cx;
+      const uint32_t sb0 = __ldg(G.sub_base + gc);
+      bc.cells += 1;
+      if (__ldg(G.sub_base + gc + 1) - sb0 > 1) {
+        const int64_t x0c = cell_lo_tab(ucx, nx, bx, Lx);
+        const int64_t wx = cell_lo_tab(ucx + 1, nx, bx, Lx) - x0c;
+        const int s = __ldg(G.sub_s + gc);
+        const int sx0 = sub_idx(max(qx0 - x0c, (int64_t)0), wx, s);
+        const int sx1 = sub_idx(min(qx1 - x0c, wx - 1), wx, s);
+        const int sy0 = sub_idx(ly0, wy, s), sy1 = sub_idx(ly1, wy, s);
+        for (int row = sy0; row <= sy1; ++row) {
+          const uint32_t rb = sb0 + (uint32_t)row * (uint32_t)s;
+          const uint32_t qb = __ldg(G.sub_off + rb + sx0), qe = __ldg(G.sub_off + rb + sx1 + 1);
+          if (qe > qb) {
+            if (nrun == BoxHits<KC>::kRuns) return -1;
+            H.run[nrun++][threadIdx.x] = make_uint2(qb, (qe - qb) << 4 | code);
+          }
+        }
+      } else {
+        const uint32_t qb = __ldg(G.off + gc), qe = __ldg(G.off + gc + 1);
+        if (qe > qb) {
+          if (nrun == BoxHits<KC>::kRuns) return -1;
+          H.run[nrun++][threadIdx.x] = make_uint2(qb, (qe - qb) << 4 | code);
+        }
+      }
+    }
+  }
+  bc.runs += (uint32_t)nrun;
+  // one flat loop over the listed runs
+  int cnt = 0, hits = 0;
+  int r = -1;
+  uint32_t q = 0, qe = 0, ox = 0, oy = 0;
+  const uint32_t self = (uint32_t)C.self;
+  // candidates go four at a time (the loads of a group are independent, so
+  // they are in flight together); a group never crosses a run
+  constexpr int kGroup = 4;
+  for (;;) {
+    if (q == qe) {
+      if (++r == nrun) break;
+      const uint2 e = H.run[r][threadIdx.x];
+      q = e.x;
+      qe = e.x + (e.y >> 4);
+      // reference shifted into the run's periodic image: dx = x_j - ox exactly
+      const uint32_t cxd = (e.y >> 2) & 3u, cyd = e.y & 3u;
+      ox = C.px + (cxd == 1u ? (uint32_t)C.Lx : 0u) - (cxd == 2u ? (uint32_t)C.Lx : 0u);
+      oy = C.py + (cyd == 1u ? (uint32_t)C.Ly : 0u) - (cyd == 2u ? (uint32_t)C.Ly : 0u);
+      bc.cand += qe - q;
+    }
+    const uint32_t n = min(qe - q, (uint32_t)kGroup);
+    int2 pj[kGroup];
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) pj[u] = __ldg(pos + q + min((uint32_t)u, n - 1));
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      const int32_t dx = (int32_t)((uint32_t)pj[u].x - ox), dy = (int32_t)((uint32_t)pj[u].y - oy);
+      const uint64_t D = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy);
+      const uint32_t qu = q + (uint32_t)u;
+      if ((uint32_t)u < n && D <= tau && qu != self) {
+        H.slot[cnt][threadIdx.x] = (int32_t)qu;
+        ++cnt;
+        ++hits;
+        if (cnt == BoxHits<KC>::kCap) {  // rare: a full buffer is merged on the spot
+          box_merge<KC>(H, cnt, C, pos, T, tie);
+          cnt = 0;
+          if (T.d[KC - 1] < tau) tau = T.d[KC - 1];
+        }
+      }
+    }
+    q += n;
+  }
+  box_merge<KC>(H, cnt, C, pos, T, tie);  // after the loop, where the threads have reconverged
+  return hits;
+}
+
+// search radius without a hint: a multiple of the k-th distance expected
+// from the density of the particle's own sub-cell
+__device__ __forceinline__ float box_radius_estimate(const Rep& R, const uint32_t* __restrict__ bounds,
+                                                     const GridView& G, int2 p, int k) {
+  const uint32_t* bx = bounds + R.bnd[0];
+  const uint32_t* by = bounds + R.bnd[1];
+  const int cx = cell_of_tab((uint32_t)p.x, R.nc[0], bx, R.inv_w[0]);
+  const int cy = cell_of_tab((uint32_t)p.y, R.nc[1], by, R.inv_w[1]);
+  const int64_t gc = R.c0 + (int64_t)cy * R.nc[0] + cx;
+  const uint32_t sb0 = __ldg(G.sub_base + gc), sb1 = __ldg(G.sub_base + gc + 1);
+  const int64_t x0 = __ldg(bx + cx), wx = (int64_t)__ldg(bx + cx + 1) - x0;
+  const int64_t y0 = __ldg(by + cy), wy = (int64_t)__ldg(by + cy + 1) - y0;
+  int s = 1;
+  uint32_t cnt;
+  if (sb1 - sb0 > 1) {
+    s = __ldg(G.sub_s + gc);
+    const uint32_t sub = sb0 + (uint32_t)(sub_idx((int64_t)p.y - y0, wy, s) * s + sub_idx((int64_t)p.x - x0, wx, s));
+    cnt = __ldg(G.sub_off + sub + 1) - __ldg(G.sub_off + sub);
+  } else {
+    cnt = __ldg(G.off + gc + 1) - __ldg(G.off + gc);
+  }
+  const float area = (float)wx * (float)wy / ((float)s * (float)s);
+  return 1.6f * sqrtf((float)k * area / (3.14159265f * (float)max(cnt, 1u)));
+}
+
+// The radius-first search of one particle with a first radius r: up to
+// `tries` squares.  A square with fewer than k hits is followed by one with
+// the radius scaled up towards about 1.5 k expected hits (hits grow with the
+// area, the square of the radius).
+// Returns true when T holds the exact top-k; otherwise *r_next is the radius
+// to try next, or -1 when only the walk can serve the particle (a square
+// too wide for the box, or two candidates at the same distance).
+template <int KC>
+__device__ __forceinline__ bool box_search(BoxHits<KC>& H, const Rep& R, const uint32_t* __restrict__ bounds,
+                                           const GridView& G, const int2* __restrict__ pos, const Ctx& C, float r,
+                                           int k, int tries, Top<KC>& T, BoxCount& bc, float* r_next) {
+  for (int tr = 0; tr < tries; ++tr) {
+    const int64_t a = (int64_t)ceilf(fminf(r, 2.0e9f));
+    bool tie = false;
+    top_init<KC>(T, k);
+    const int hits = box_scan<KC>(H, R, bounds, G, pos, C, a, T, &tie, bc);
+    if (hits < 0) {
+      bc.why = 1u;
+      *r_next = -1.f;
+      return false;
+    }
+    if (hits >= k) {
+      bc.hits += (uint32_t)hits;
+      if (!tie) return true;
+      bc.why = 3u;
+      *r_next = -1.f;
+      return false;
+    }
+    const float want = 1.5f * (float)k + 1.f;
+    const float f = hits > 0 ? sqrtf(want / (float)hits) : 2.f;
+    r = (float)a * fminf(f, 2.f);
+  }
+  bc.why = 2u;
+  *r_next = r;
+  return false;
+}
+
+// Tracing: totals of the radius-first counters (stats[5..13]).
+__device__ __forceinline__ void record_box_stats(unsigned long long* stats, const BoxCount& bc) {
+  if (!stats) return;
+  unsigned long long v[9] = {bc.tries, bc.runs, bc.cand, bc.cells, bc.hits, bc.why == 1u, bc.why == 2u,
+                              bc.why == 3u, bc.why == 4u};
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int i = 0; i < 9; ++i) atomicAdd(stats + 5 + i, v[i]);
+}
+
+// Search + update, radius first, one square per particle.  Particles it
+// cannot serve go on the deferred list (slot, replica) with the radius to
+// try next in U_hint (-1: walk), and knn2_deferred_kernel finishes them: a
+// warp here never waits for one particle's second square.
+template <int KC>
+__global__ void __launch_bounds__(kBlock, VK_KNN2_BOX_BLOCKS) knn2_box_step_kernel(
+    const Rep* __restrict__ reps, const BlockTask* __restrict__ tasks, const uint32_t* __restrict__ bounds,
+    const int2* __restrict__ S_pos, const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id,
+    const float* __restrict__ S_hint, GridView G, int2* __restrict__ U_pos, float2* __restrict__ U_dir,
+    int32_t* __restrict__ U_id, float* __restrict__ U_hint, uint32_t* __restrict__ counts,
+    double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P, int2* __restrict__ defer_list,
+    int32_t* __restrict__ defer_count) {
+  extern __shared__ __align__(16) unsigned char box_smem[];
+  BoxHits<KC>& H = *reinterpret_cast<BoxHits<KC>*>(box_smem);
+  __shared__ PhiShared phs;
+  phi_block_begin(phs);
+  const BlockTask t = tasks[blockIdx.x];
+  const Rep R = reps[t.rep];
+  const int li = t.first + (int)threadIdx.x;
+  const bool valid = li < R.n;
+  const int64_t step = *d_step;
+  float nnew[3] = {0.f, 0.f, 0.f};
+  BoxCount bc;
+  bool served = false;
+  if (valid) {
+    const int64_t s = R.p0 + li;
+    const int2 p = S_pos[s];
+    const float hint = S_hint[s];
+    Ctx C;
+    init_ctx(C, R, s, p);
+    Top<KC> T;
+    const float r =
+        hint > 0.f ? P.halo_alpha * hint + P.halo_beta * fabsf(R.s) : box_radius_estimate(R, bounds, G, p, P.k);
+    float r_next = -1.f;
+    served = box_search<KC>(H, R, bounds, G, S_pos, C, r, P.k, 1, T, bc, &r_next);
+    if (served) {
+      knn2_update<KC>(R, P, step, s, p, S_dir[s], S_id[s], T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
+      U_hint[s] = sqrtf((float)T.d[KC - 1]) * 1.0001f + 1.f;
+    } else {
+      U_hint[s] = r_next;
+      defer_list[atomicAdd(defer_count, 1)] = make_int2((int)s, t.rep);
+    }
+  }
+  record_search_stats(P.stats, served, bc.cand, bc.tries, false);
+  record_box_stats(P.stats, bc);
+  phi_block_end<2>(phs, nnew, phi_acc + ((size_t)(step % P.phi_cap) * (size_t)P.n_rep + (size_t)t.rep) * 3);
+}
+
+// Search + update of the deferred particles: more squares from the radius
+// the step kernel left in U_hint, then the per-particle walk.  A fixed grid
+// strides over the list (its length is read on the device, so the launch can
+// sit in a CUDA graph); each particle adds its new heading to its replica's
+// order parameter directly in FP64.
+template <int KC>
+__global__ void __launch_bounds__(kBlock, 2) knn2_deferred_kernel(
+    const Rep* __restrict__ reps, const uint32_t* __restrict__ bounds, const int2* __restrict__ S_pos,
+    const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G, int2* __restrict__ U_pos,
+    float2* __restrict__ U_dir, int32_t* __restrict__ U_id, float* __restrict__ U_hint,
+    uint32_t* __restrict__ counts, double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P,
+    const int2* __restrict__ defer_list, const int32_t* __restrict__ defer_count) {
+  extern __shared__ __align__(16) unsigned char box_smem[];
+  BoxHits<KC>& H = *reinterpret_cast<BoxHits<KC>*>(box_smem);
+  const int total = *defer_count;
+  const int64_t step = *d_step;
+  for (int i = blockIdx.x * kBlock + (int)threadIdx.x; i < total; i += gridDim.x * kBlock) {
+    const int2 e = defer_list[i];
+    const int64_t s = e.x;
+    const Rep R = reps[e.y];
+    const int2 p = S_pos[s];
+    Ctx C;
+    init_ctx(C, R, s, p);
+    Top<KC> T;
+    BoxCount bc;
+    const float r = U_hint[s];
+    float r_next = -1.f;
+    const bool ok = r > 0.f && box_search<KC>(H, R, bounds, G, S_pos, C, r, P.k, kBoxTries, T, bc, &r_next);
+    if (!ok) {
+      top_init<KC>(T, P.k);
+      knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T, P.k);
+    }
+    float nnew[3] = {0.f, 0.f, 0.f};
+    knn2_update<KC>(R, P, step, s, p, S_dir[s], S_id[s], T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
+    U_hint[s] = sqrtf((float)T.d[KC - 1]) * 1.0001f + 1.f;
+    double* acc = phi_acc + ((size_t)(step % P.phi_cap) * (size_t)P.n_rep + (size_t)e.y) * 3;
+    atomicAdd(acc + 0, (double)nnew[0]);
+    atomicAdd(acc + 1, (double)nnew[1]);
+    if (P.stats) {
+      atomicAdd(P.stats + 0, (unsigned long long)(ok ? bc.cand : C.n_cand));
+      atomicAdd(P.stats + 1, (unsigned long long)(ok ? bc.tries : C.n_runs));
+      atomicMax(P.stats + 2, (unsigned long long)(ok ? bc.cand : C.n_cand));
+      atomicAdd(P.stats + 3, 1ull);
+      if (!ok) atomicAdd(P.stats + 4, 1ull);
+    }
+  }
+}
+
+template <int KC>
+__global__ void __launch_bounds__(kBlock, 3) knn2_box_export_kernel(
+    const Rep* __restrict__ reps, int rep, const uint32_t* __restrict__ bounds, const int2* __restrict__ S_pos,
+    const int32_t* __restrict__ S_id, const float* __restrict__ S_hint, GridView G, int k, float alpha, float beta,
+    int32_t* __restrict__ out, int2* __restrict__ walk_list, int32_t* __restrict__ walk_count) {
+  extern __shared__ __align__(16) unsigned char box_smem[];
+  BoxHits<KC>& H = *reinterpret_cast<BoxHits<KC>*>(box_smem);
+  const Rep R = reps[rep];
+  const int li = blockIdx.x * kBlock + (int)threadIdx.x;
+  if (li >= R.n) return;
+  const int64_t s = R.p0 + li;
+  const int2 p = S_pos[s];
+  Ctx C;
+  init_ctx(C, R, s, p);
+  Top<KC> T;
+  BoxCount bc;
+  const float hint = S_hint ? S_hint[s] : 0.f;
+  const float r = hint > 0.f ? alpha * hint + beta * fabsf(R.s) : box_radius_estimate(R, bounds, G, p, k);
+  float r_next = -1.f;
+  if (!box_search<KC>(H, R, bounds, G, S_pos, C, r, k, kBoxTries, T, bc, &r_next)) {
+    walk_list[atomicAdd(walk_count, 1)] = make_int2((int)s, rep);
+    return;
+  }
+  const int32_t id = S_id[s];
+#pragma unroll
+  for (int j = 0; j < KC; ++j)
+    if (j >= KC - k) out[(int64_t)id * k + (j - (KC - k))] = __ldg(S_id + T.slot[j]);
+}
+
+// the per-particle walk for the listed particles of an export
+template <int KC>
+__global__ void __launch_bounds__(kBlock, 2) knn2_walk_export_list_kernel(
+    const Rep* __restrict__ reps, const uint32_t* __restrict__ bounds, const int2* __restrict__ S_pos,
+    const int32_t* __restrict__ S_id, GridView G, int k, int32_t* __restrict__ out,
+    const int2* __restrict__ walk_list, const int32_t* __restrict__ walk_count) {
+  const int total = *walk_count;
+  for (int i = blockIdx.x * kBlock + (int)threadIdx.x; i < total; i += gridDim.x * kBlock) {
+    const int2 e = walk_list[i];
+    const int64_t s = e.x;
+    const Rep R = reps[e.y];
+    Ctx C;
+    init_ctx(C, R, s, S_pos[s]);
+    Top<KC> T;
+    top_init<KC>(T, k);
+    knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T, k);
+    const int32_t id = S_id[s];
+#pragma unroll
+    for (int j = 0; j < KC; ++j)
+      if (j >= KC - k) out[(int64_t)id * k + (j - (KC - k))] = __ldg(S_id + T.slot[j]);
+  }
+}
+
 GridView view_of(const Buffers& b) {
   GridView G;
   G.off = b.offsets;
@@ -642,23 +1075,80 @@ GridView view_of(const Buffers& b) {
 }
 
 template <int KC>
+constexpr size_t box_smem_bytes() {
+  return sizeof(BoxHits<KC>);
+}
+
+// blocks of the list kernels: enough threads for a list of every particle
+// (the length is known only on the device; threads past it exit at once),
+// so a long list never queues on a few threads
+int walk_blocks(const Geometry& g) { return (int)std::max<int64_t>(1, (g.n_total + kBlock - 1) / kBlock); }
+
+template <int KC>
 cudaError_t step2(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st) {
-  knn2_step_kernel<KC><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, b.bounds, (const int2*)b.S_pos,
-                                                     (const float2*)b.S_dir, b.S_id, view_of(b), (int2*)b.U_pos,
-                                                     (float2*)b.U_dir, b.U_id, b.counts, b.phi_acc, b.d_step, P);
+  if (P.knn_search == 1 || !b.S_hint) {
+    knn2_step_kernel<KC><<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, b.bounds, (const int2*)b.S_pos,
+                                                       (const float2*)b.S_dir, b.S_id, view_of(b), (int2*)b.U_pos,
+                                                       (float2*)b.U_dir, b.U_id, b.counts, b.phi_acc, b.d_step, P);
+    if (b.U_hint) cudaMemsetAsync(b.U_hint, 0, sizeof(float) * (size_t)g.n_total, st);
+  } else {
+    // the walk list is empty here: the previous scatter (or init) cleared it
+    knn2_box_step_kernel<KC><<<g.n_tasks, kBlock, box_smem_bytes<KC>(), st>>>(
+        g.reps, g.tasks, b.bounds, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id, b.S_hint, view_of(b),
+        (int2*)b.U_pos, (float2*)b.U_dir, b.U_id, b.U_hint, b.counts, b.phi_acc, b.d_step, P, b.ovf_list,
+        b.ovf_count);
+    knn2_deferred_kernel<KC><<<walk_blocks(g), kBlock, box_smem_bytes<KC>(), st>>>(
+        g.reps, b.bounds, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id, view_of(b), (int2*)b.U_pos,
+        (float2*)b.U_dir, b.U_id, b.U_hint, b.counts, b.phi_acc, b.d_step, P, b.ovf_list, b.ovf_count);
+  }
   return cudaGetLastError();
 }
 
 template <int KC>
-cudaError_t export2(const Geometry& g, const Buffers& b, int k, int rep, int n, int32_t* out, cudaStream_t st) {
+cudaError_t export2(const Geometry& g, const Buffers& b, int k, int rep, int n, int32_t* out, cudaStream_t st,
+                    const StepParams& P) {
   const int nb = (n + kBlock - 1) / kBlock;
   if (nb == 0) return cudaSuccess;
-  knn2_export_kernel<KC><<<nb, kBlock, 0, st>>>(g.reps, rep, b.bounds, (const int2*)b.S_pos, b.S_id, view_of(b), k,
-                                                out);
+  if (P.knn_search == 1 || !b.S_hint) {
+    knn2_export_kernel<KC><<<nb, kBlock, 0, st>>>(g.reps, rep, b.bounds, (const int2*)b.S_pos, b.S_id, view_of(b),
+                                                  k, out);
+  } else {
+    cudaError_t e = cudaMemsetAsync(b.ovf_count, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    knn2_box_export_kernel<KC><<<nb, kBlock, box_smem_bytes<KC>(), st>>>(
+        g.reps, rep, b.bounds, (const int2*)b.S_pos, b.S_id, b.S_hint, view_of(b), k, P.halo_alpha, P.halo_beta,
+        out, b.ovf_list, b.ovf_count);
+    knn2_walk_export_list_kernel<KC><<<walk_blocks(g), kBlock, 0, st>>>(g.reps, b.bounds, (const int2*)b.S_pos,
+                                                                         b.S_id, view_of(b), k, out, b.ovf_list,
+                                                                         b.ovf_count);
+    // leave the list empty for the next step
+    e = cudaMemsetAsync(b.ovf_count, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 
+template <int KC>
+cudaError_t prepare2() {
+  cudaError_t e = cudaFuncSetAttribute(knn2_box_step_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)box_smem_bytes<KC>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(knn2_box_export_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)box_smem_bytes<KC>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(knn2_deferred_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)box_smem_bytes<KC>());
+  return e;
+}
+
 }  // namespace
+
+cudaError_t prepare_knn2() {
+  cudaError_t e = prepare2<8>();
+  if (e == cudaSuccess) e = prepare2<16>();
+  if (e == cudaSuccess) e = prepare2<32>();
+  return e;
+}
 
 cudaError_t launch_knn2_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st) {
   if (P.k <= 8) return step2<8>(g, b, P, st);
@@ -667,10 +1157,10 @@ cudaError_t launch_knn2_step(const Geometry& g, const Buffers& b, const StepPara
 }
 
 cudaError_t launch_knn2_export(const Geometry& g, const Buffers& b, int k, int rep, int n, int32_t* out,
-                               cudaStream_t st) {
-  if (k <= 8) return export2<8>(g, b, k, rep, n, out, st);
-  if (k <= 16) return export2<16>(g, b, k, rep, n, out, st);
-  return export2<32>(g, b, k, rep, n, out, st);
+                               cudaStream_t st, const StepParams& P) {
+  if (k <= 8) return export2<8>(g, b, k, rep, n, out, st, P);
+  if (k <= 16) return export2<16>(g, b, k, rep, n, out, st, P);
+  return export2<32>(g, b, k, rep, n, out, st, P);
 }
 
 }  // namespace vk

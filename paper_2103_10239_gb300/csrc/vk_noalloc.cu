@@ -193,6 +193,7 @@ extern "C" vk_status vk_knn_lists_noalloc(const int32_t* pos_q, int64_t n, const
   P.k = k;
   P.n_rep = 1;
   P.phi_cap = 2;
+  P.knn_search = 1;  // the per-particle walk: no hint buffers, no shared-memory attribute to set
 
   noalloc_setup_kernel<<<64, 256, 0, st>>>(R, tasks_d, n_tasks, rep_d, b.bounds, b.counts, n_cells, b.sub_count,
                                            n_sub, status_d);
@@ -202,7 +203,7 @@ extern "C" vk_status vk_knn_lists_noalloc(const int32_t* pos_q, int64_t n, const
   if (e == cudaSuccess) e = launch_count(g, b, st);
   if (e == cudaSuccess) e = launch_build(g, b, st);
   if (e == cudaSuccess) e = launch_scatter(g, b, P, 0, st);
-  if (e == cudaSuccess) e = launch_knn2_export(g, b, k, 0, (int)n, out_ids, st);
+  if (e == cudaSuccess) e = launch_knn2_export(g, b, k, 0, (int)n, out_ids, st, P);
   if (e == cudaSuccess && dev_status)
     e = cudaMemcpyAsync(dev_status, status_d, sizeof(int32_t), cudaMemcpyDefault, st);
   if (e != cudaSuccess) {

@@ -41,7 +41,9 @@ class vk_params(ctypes.Structure):
                 ("dt", ctypes.c_float), ("eta", ctypes.c_float), ("seed", ctypes.c_uint64),
                 ("noise", ctypes.c_int32), ("include_self", ctypes.c_int32),
                 ("advect_new", ctypes.c_int32), ("sum_mode", ctypes.c_int32),
-                ("cell_occupancy", ctypes.c_float), ("phi_capacity", ctypes.c_int32)]
+                ("cell_occupancy", ctypes.c_float), ("phi_capacity", ctypes.c_int32),
+                ("knn_search", ctypes.c_int32), ("search_halo", ctypes.c_float),
+                ("search_halo_step", ctypes.c_float)]
 
 
 class vk_info(ctypes.Structure):
@@ -83,6 +85,8 @@ _SIGS = {
     "vk_get_search_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                            ctypes.POINTER(ctypes.c_double)]),
+    "vk_get_search_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_int32)]),
     "vk_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(vk_info)]),
     "vk_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.POINTER(ctypes.c_float)]),
@@ -291,6 +295,17 @@ class Sim:
                                           ctypes.byref(f)), self._h)
         return {"mean_candidates": c.value, "mean_runs": r.value, "max_candidates": m.value,
                 "split_fraction": f.value}
+
+    SEARCH_COUNTERS = ("candidates", "runs_or_squares", "max_candidates", "updates", "split_or_walked",
+                       "rf_squares", "rf_runs", "rf_candidates", "rf_cells", "rf_hits", "rf_walk_wide",
+                       "rf_walk_full", "rf_walk_tie", "rf_walk_few")
+
+    def search_counters(self) -> dict:
+        """Raw totals of the search counters while tracing at level 2."""
+        vals = np.zeros(len(self.SEARCH_COUNTERS), dtype=np.int64)
+        n = ctypes.c_int32(0)
+        _check(load().vk_get_search_counters(self._h, vals.ctypes.data, len(vals), ctypes.byref(n)), self._h)
+        return dict(zip(self.SEARCH_COUNTERS, (int(v) for v in vals)))
 
     def autotune(self, candidates: Sequence[float], trial_steps: int = 3) -> float:
         c = np.ascontiguousarray(candidates, dtype=np.float32)

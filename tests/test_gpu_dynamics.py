@@ -110,8 +110,11 @@ def test_profiling_counts_phases():
         sim.set_profiling(True)
         sim.step(5)
         prof = sim.profile()
-    assert prof["search_update"][1] == 5 and prof["build"][1] == 35 and prof["scatter"][1] == 5
+        kps = sim.info().kernels_per_step
+    # 2D kNN: the warp-tile kernel and the walk-list kernel per step
+    assert prof["search_update"][1] == 10 and prof["build"][1] == 35 and prof["scatter"][1] == 5
     assert prof["search_update"][0] > 0
+    assert kps == 10
 
 
 def test_autotune_keeps_results():

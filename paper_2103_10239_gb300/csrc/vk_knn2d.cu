@@ -819,23 +819,24 @@ __device__ __forceinline__ int box_scan(BoxHits<KC>& H, const Rep& R, const uint
     int2 pj[kGroup];
 #pragma unroll
     for (int u = 0; u < kGroup; ++u) pj[u] = __ldg(pos + q + min((uint32_t)u, n - 1));
+    // branch-free append: every candidate is written at the next free slot,
+    // and the slot advances only for a hit
 #pragma unroll
     for (int u = 0; u < kGroup; ++u) {
       const int32_t dx = (int32_t)((uint32_t)pj[u].x - ox), dy = (int32_t)((uint32_t)pj[u].y - oy);
       const uint64_t D = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy);
       const uint32_t qu = q + (uint32_t)u;
-      if ((uint32_t)u < n && D <= tau && qu != self) {
-        H.slot[cnt][threadIdx.x] = (int32_t)qu;
-        ++cnt;
-        ++hits;
-        if (cnt == BoxHits<KC>::kCap) {  // rare: a full buffer is merged on the spot
-          box_merge<KC>(H, cnt, C, pos, T, tie);
-          cnt = 0;
-          if (T.d[KC - 1] < tau) tau = T.d[KC - 1];
-        }
-      }
+      const bool hit = (uint32_t)u < n && D <= tau && qu != self;
+      H.slot[cnt][threadIdx.x] = (int32_t)qu;
+      cnt += hit ? 1 : 0;
+      hits += hit ? 1 : 0;
     }
     q += n;
+    if (cnt > BoxHits<KC>::kCap - kGroup) {  // rare: a nearly full buffer is merged on the spot
+      box_merge<KC>(H, cnt, C, pos, T, tie);
+      cnt = 0;
+      if (T.d[KC - 1] < tau) tau = T.d[KC - 1];
+    }
   }
   box_merge<KC>(H, cnt, C, pos, T, tie);  // after the loop, where the threads have reconverged
   return hits;

@@ -253,11 +253,11 @@ vk_status clear_phi(vk_sim* s) {
   return VK_OK;
 }
 
-// kernels of the search+update phase: for 2D kNN the radius-first kernel
-// and the walk-list kernel (one kernel with the walk only); one for 3D kNN;
-// the Voronoi kernel and its overflow kernel
+// kernels of the search+update phase: for 2D kNN the radius-first kernel,
+// the deferred-particle kernel and the walk-list kernel (one kernel with the
+// walk only); one for 3D kNN; the Voronoi kernel and its overflow kernel
 int search_launches(const vk_sim* s) {
-  if (s->prm.rule == VK_RULE_KNN) return (s->dim == 2 && s->prm.knn_search == 0) ? 2 : 1;
+  if (s->prm.rule == VK_RULE_KNN) return (s->dim == 2 && s->prm.knn_search == 0) ? 3 : 1;
   return 2;
 }
 
@@ -410,7 +410,7 @@ vk_status build_sim(int32_t n_rep, const int64_t* n_r, const int32_t* pos_q, con
       (e = dalloc(&s->b.U_id, N)) || (e = dalloc(&s->b.U_rank, N)) ||
       (e = dalloc(&s->b.phi_acc, 3 * (size_t)s->phi_cap * n_rep)) || (e = dalloc(&s->b.d_step, 1)) ||
       (e = dalloc(&s->b.d_status, 1)) || (e = dalloc(&s->reps_d, n_rep)) ||
-      (e = dalloc(&s->b.ovf_list, N)) || (e = dalloc(&s->b.ovf_count, 1)) ||
+      (e = dalloc(&s->b.ovf_list, 2 * N)) || (e = dalloc(&s->b.ovf_count, 2)) ||
       (e = dalloc(&s->d_stats, kCounters)) ||
       (e = dalloc(&s->tasks_d, s->tasks_h.size())))
     return bail(cuda_fail(s, e, "cudaMalloc"));
@@ -420,7 +420,7 @@ vk_status build_sim(int32_t n_rep, const int64_t* n_r, const int32_t* pos_q, con
   }
   if (ensure_cells_capacity(s)) return bail(VK_ERR_OOM);
   if ((e = cudaMemsetAsync(s->b.d_step, 0, sizeof(int64_t), s->stream)) ||
-      (e = cudaMemsetAsync(s->b.ovf_count, 0, sizeof(int32_t), s->stream)) ||
+      (e = cudaMemsetAsync(s->b.ovf_count, 0, 2 * sizeof(int32_t), s->stream)) ||
       (e = cudaMemsetAsync(s->b.d_status, 0, sizeof(int32_t), s->stream)) ||
       (e = cudaMemcpyAsync(s->tasks_d, s->tasks_h.data(), sizeof(BlockTask) * s->tasks_h.size(),
                            cudaMemcpyHostToDevice, s->stream)))

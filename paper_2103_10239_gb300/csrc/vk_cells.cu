@@ -302,7 +302,8 @@ __global__ void __launch_bounds__(kBlock) scatter_kernel(const Rep* __restrict__
     __syncthreads();
     if (threadIdx.x == 0) {
       *d_step = nxt;
-      *ovf_count = 0;  // the Voronoi overflow list of this step has been consumed
+      ovf_count[0] = 0;  // the lists of this step (Voronoi overflow, kNN deferred and walk) are consumed
+      ovf_count[1] = 0;
     }
   }
   if (li >= R.n) return;

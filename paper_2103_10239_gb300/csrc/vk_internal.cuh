@@ -591,8 +591,9 @@ struct Buffers {
   double* phi_acc;    // phi_cap * n_rep * 3
   int64_t* d_step;
   int32_t* d_status;
-  int2* ovf_list;      // Voronoi: (slot, replica) of cells too large for the main kernel
-  int32_t* ovf_count;
+  int2* ovf_list;      // 2 N entries of (slot, replica): Voronoi cells too large for the main kernel;
+                       // 2D kNN: deferred particles (first half) and particles for the walk (second)
+  int32_t* ovf_count;  // 2 counters for those lists, cleared by the scatter of every step
   // 2D kNN: each particle's k-th neighbor distance (grid units) found at the
   // previous step, in S order, and the one found now in U order (0 = unknown);
   // only a search hint, results never depend on it (NULL for other rules)

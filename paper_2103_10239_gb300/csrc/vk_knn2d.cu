@@ -706,6 +706,7 @@ __device__ __forceinline__ void box_merge(const BoxHits<KC>& H, int cnt, const C
   bool t = false;
   for (int b = 0; b < cnt; ++b) {
     const int32_t q = H.slot[b][threadIdx.x];
+    if ((int64_t)q == C.self) continue;  // the particle is a hit of its own square
     const uint64_t D = box_dist2(C, __ldg(pos + q));
     t |= D == T.d[KC - 1];
     if (D < T.d[KC - 1]) {
@@ -730,16 +731,16 @@ __device__ __forceinline__ void box_merge(const BoxHits<KC>& H, int cnt, const C
 }
 
 // Scan the square [p - a, p + a] into T (initialised by the caller): every
-// slot other than self with D <= tau = (a+1)^2 - 1 is a hit.  First the
-// square's slot runs (the sub-cell rows of the coarse cells it meets) are
-// listed, each with the periodic image its cell lies in; then one flat loop
-// walks all of them, so that threads of a warp whose squares split into
-// different numbers of runs still scan candidates together.  Hits are
-// buffered and merged into T at the end (and, rarely, when the buffer
-// fills, after which tau shrinks to T's k-th distance).  Returns the number of hits
-// (>= k exactly when T is full), or -1 when the square is too wide for the
-// minimum image, meets a coarse cell through two periodic images, or has
-// more runs than the list holds.
+// slot with D <= tau = (a+1)^2 - 1 is a hit (the particle itself too; the
+// merge skips it).  The square's slot runs (the sub-cell rows of the coarse
+// cells it meets) are listed, each with the periodic image its cell lies in,
+// up to kRuns at a time; one flat loop walks each batch, so that threads of
+// a warp whose squares split into different numbers of runs still scan
+// candidates together.  Hits are buffered and merged into T at the end (and,
+// rarely, when the buffer fills, after which tau shrinks to T's k-th
+// distance).  Returns the number of hits (>= k exactly when T is full), or
+// -1 when the square is too wide for the minimum image or meets a coarse
+// cell through two periodic images.
 template <int KC>
 __device__ __forceinline__ int box_scan(BoxHits<KC>& H, const Rep& R, const uint32_t* __restrict__ bounds,
                                         const GridView& G, const int2* __restrict__ pos, const Ctx& C, int64_t a,
@@ -756,90 +757,106 @@ __device__ __forceinline__ int box_scan(BoxHits<KC>& H, const Rep& R, const uint
   const int ucy0 = box_ucell(qy0, ny, by, R.inv_w[1], Ly), ucy1 = box_ucell(qy1, ny, by, R.inv_w[1], Ly);
   if (ucx1 - ucx0 + 1 > nx || ucy1 - ucy0 + 1 > ny) return -1;
   bc.tries += 1;
-  // list the runs; shift code per axis: 0 same image, 1 the image at -L, 2 at +L
-  int nrun = 0;
-  for (int ucy = ucy0; ucy <= ucy1; ++ucy) {
-    const int cy = ucy < 0 ? ucy + ny : (ucy >= ny ? ucy - ny : ucy);
-    const uint32_t ycode = ucy < 0 ? 1u : (ucy >= ny ? 2u : 0u);
-    const int64_t y0c = cell_lo_tab(ucy, ny, by, Ly);
-    const int64_t wy = cell_lo_tab(ucy + 1, ny, by, Ly) - y0c;
-    const int64_t ly0 = max(qy0 - y0c, (int64_t)0), ly1 = min(qy1 - y0c, wy - 1);
-    for (int ucx = ucx0; ucx <= ucx1; ++ucx) {
-      const int cx = ucx < 0 ? ucx + nx : (ucx >= nx ? ucx - nx : ucx);
-      const uint32_t code = (ucx < 0 ? 1u : (ucx >= nx ? 2u : 0u)) << 2 | ycode;
-      const int64_t gc = R.c0 + (int64_t)cy * nx + cx;
-      const uint32_t sb0 = __ldg(G.sub_base + gc);
-      bc.cells += 1;
-      if (__ldg(G.sub_base + gc + 1) - sb0 > 1) {
-        const int64_t x0c = cell_lo_tab(ucx, nx, bx, Lx);
-        const int64_t wx = cell_lo_tab(ucx + 1, nx, bx, Lx) - x0c;
-        const int s = __ldg(G.sub_s + gc);
-        const int sx0 = sub_idx(max(qx0 - x0c, (int64_t)0), wx, s);
-        const int sx1 = sub_idx(min(qx1 - x0c, wx - 1), wx, s);
-        const int sy0 = sub_idx(ly0, wy, s), sy1 = sub_idx(ly1, wy, s);
-        for (int row = sy0; row <= sy1; ++row) {
-          const uint32_t rb = sb0 + (uint32_t)row * (uint32_t)s;
-          const uint32_t qb = __ldg(G.sub_off + rb + sx0), qe = __ldg(G.sub_off + rb + sx1 + 1);
-          if (qe > qb) {
-            if (nrun == BoxHits<KC>::kRuns) return -1;
-            H.run[nrun++][threadIdx.x] = make_uint2(qb, (qe - qb) << 4 | code);
-          }
+  // enumeration cursor over (coarse cell, row of sub-cells): runs are listed
+  // kRuns at a time, each batch is scanned, then listing resumes
+  int ucx = ucx0, ucy = ucy0;
+  int row = 0, row_end = -1;  // rows of the current cell still to list
+  int64_t gc = 0;
+  uint32_t sb0 = 0, code = 0;
+  int s = 1, sx0 = 0, sx1 = 0;
+  bool split = false, listed_all = false;
+  int cnt = 0, merged = 0;
+  while (!listed_all) {
+    int nrun = 0;
+    while (nrun < BoxHits<KC>::kRuns) {
+      if (row > row_end) {  // next coarse cell
+        if (ucx > ucx1) {
+          ucx = ucx0;
+          ++ucy;
         }
+        if (ucy > ucy1) {
+          listed_all = true;
+          break;
+        }
+        const int cy = ucy < 0 ? ucy + ny : (ucy >= ny ? ucy - ny : ucy);
+        const int cx = ucx < 0 ? ucx + nx : (ucx >= nx ? ucx - nx : ucx);
+        // shift code per axis: 0 same image, 1 the image at -L, 2 at +L
+        code = (ucx < 0 ? 1u : (ucx >= nx ? 2u : 0u)) << 2 | (ucy < 0 ? 1u : (ucy >= ny ? 2u : 0u));
+        gc = R.c0 + (int64_t)cy * nx + cx;
+        sb0 = __ldg(G.sub_base + gc);
+        split = __ldg(G.sub_base + gc + 1) - sb0 > 1;
+        bc.cells += 1;
+        row = 0;
+        row_end = 0;
+        if (split) {
+          const int64_t y0c = cell_lo_tab(ucy, ny, by, Ly);
+          const int64_t wy = cell_lo_tab(ucy + 1, ny, by, Ly) - y0c;
+          const int64_t x0c = cell_lo_tab(ucx, nx, bx, Lx);
+          const int64_t wx = cell_lo_tab(ucx + 1, nx, bx, Lx) - x0c;
+          s = __ldg(G.sub_s + gc);
+          sx0 = sub_idx(max(qx0 - x0c, (int64_t)0), wx, s);
+          sx1 = sub_idx(min(qx1 - x0c, wx - 1), wx, s);
+          row = sub_idx(max(qy0 - y0c, (int64_t)0), wy, s);
+          row_end = sub_idx(min(qy1 - y0c, wy - 1), wy, s);
+        }
+        ++ucx;
+      }
+      uint32_t qb, qe;
+      if (split) {
+        const uint32_t rb = sb0 + (uint32_t)row * (uint32_t)s;
+        qb = __ldg(G.sub_off + rb + sx0);
+        qe = __ldg(G.sub_off + rb + sx1 + 1);
       } else {
-        const uint32_t qb = __ldg(G.off + gc), qe = __ldg(G.off + gc + 1);
-        if (qe > qb) {
-          if (nrun == BoxHits<KC>::kRuns) return -1;
-          H.run[nrun++][threadIdx.x] = make_uint2(qb, (qe - qb) << 4 | code);
-        }
+        qb = __ldg(G.off + gc);
+        qe = __ldg(G.off + gc + 1);
+      }
+      ++row;
+      if (qe > qb) H.run[nrun++][threadIdx.x] = make_uint2(qb, (qe - qb) << 4 | code);
+    }
+    bc.runs += (uint32_t)nrun;
+    // one flat loop over the listed runs; candidates go four at a time (the
+    // loads of a group are independent, so they are in flight together) and
+    // a group never crosses a run
+    constexpr int kGroup = 4;
+    int r = -1;
+    uint32_t q = 0, qe = 0, ox = 0, oy = 0;
+    for (;;) {
+      if (q == qe) {
+        if (++r == nrun) break;
+        const uint2 e = H.run[r][threadIdx.x];
+        q = e.x;
+        qe = e.x + (e.y >> 4);
+        // reference shifted into the run's periodic image: dx = x_j - ox exactly
+        const uint32_t cxd = (e.y >> 2) & 3u, cyd = e.y & 3u;
+        ox = C.px + (cxd == 1u ? (uint32_t)C.Lx : 0u) - (cxd == 2u ? (uint32_t)C.Lx : 0u);
+        oy = C.py + (cyd == 1u ? (uint32_t)C.Ly : 0u) - (cyd == 2u ? (uint32_t)C.Ly : 0u);
+        bc.cand += qe - q;
+      }
+      const uint32_t n = min(qe - q, (uint32_t)kGroup);
+      int2 pj[kGroup];
+#pragma unroll
+      for (int u = 0; u < kGroup; ++u) pj[u] = __ldg(pos + q + min((uint32_t)u, n - 1));
+      // branch-free append: every candidate is written at the next free slot,
+      // and the slot advances only for a hit
+#pragma unroll
+      for (int u = 0; u < kGroup; ++u) {
+        const int32_t dx = (int32_t)((uint32_t)pj[u].x - ox), dy = (int32_t)((uint32_t)pj[u].y - oy);
+        const uint64_t D = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy);
+        const bool hit = (uint32_t)u < n && D <= tau;
+        H.slot[cnt][threadIdx.x] = (int32_t)(q + (uint32_t)u);
+        cnt += hit ? 1 : 0;
+      }
+      q += n;
+      if (cnt > BoxHits<KC>::kCap - kGroup) {  // rare: a nearly full buffer is merged on the spot
+        box_merge<KC>(H, cnt, C, pos, T, tie);
+        merged += cnt;
+        cnt = 0;
+        if (T.d[KC - 1] < tau) tau = T.d[KC - 1];
       }
     }
   }
-  bc.runs += (uint32_t)nrun;
-  // one flat loop over the listed runs
-  int cnt = 0, hits = 0;
-  int r = -1;
-  uint32_t q = 0, qe = 0, ox = 0, oy = 0;
-  const uint32_t self = (uint32_t)C.self;
-  // candidates go four at a time (the loads of a group are independent, so
-  // they are in flight together); a group never crosses a run
-  constexpr int kGroup = 4;
-  for (;;) {
-    if (q == qe) {
-      if (++r == nrun) break;
-      const uint2 e = H.run[r][threadIdx.x];
-      q = e.x;
-      qe = e.x + (e.y >> 4);
-      // reference shifted into the run's periodic image: dx = x_j - ox exactly
-      const uint32_t cxd = (e.y >> 2) & 3u, cyd = e.y & 3u;
-      ox = C.px + (cxd == 1u ? (uint32_t)C.Lx : 0u) - (cxd == 2u ? (uint32_t)C.Lx : 0u);
-      oy = C.py + (cyd == 1u ? (uint32_t)C.Ly : 0u) - (cyd == 2u ? (uint32_t)C.Ly : 0u);
-      bc.cand += qe - q;
-    }
-    const uint32_t n = min(qe - q, (uint32_t)kGroup);
-    int2 pj[kGroup];
-#pragma unroll
-    for (int u = 0; u < kGroup; ++u) pj[u] = __ldg(pos + q + min((uint32_t)u, n - 1));
-    // branch-free append: every candidate is written at the next free slot,
-    // and the slot advances only for a hit
-#pragma unroll
-    for (int u = 0; u < kGroup; ++u) {
-      const int32_t dx = (int32_t)((uint32_t)pj[u].x - ox), dy = (int32_t)((uint32_t)pj[u].y - oy);
-      const uint64_t D = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy);
-      const uint32_t qu = q + (uint32_t)u;
-      const bool hit = (uint32_t)u < n && D <= tau && qu != self;
-      H.slot[cnt][threadIdx.x] = (int32_t)qu;
-      cnt += hit ? 1 : 0;
-      hits += hit ? 1 : 0;
-    }
-    q += n;
-    if (cnt > BoxHits<KC>::kCap - kGroup) {  // rare: a nearly full buffer is merged on the spot
-      box_merge<KC>(H, cnt, C, pos, T, tie);
-      cnt = 0;
-      if (T.d[KC - 1] < tau) tau = T.d[KC - 1];
-    }
-  }
   box_merge<KC>(H, cnt, C, pos, T, tie);  // after the loop, where the threads have reconverged
-  return hits;
+  return merged + cnt - 1;                // the particle itself was a hit
 }
 
 // search radius without a hint: a multiple of the k-th distance expected
@@ -967,37 +984,73 @@ __global__ void __launch_bounds__(kBlock, VK_KNN2_BOX_BLOCKS) knn2_box_step_kern
 }
 
 // Search + update of the deferred particles: more squares from the radius
-// the step kernel left in U_hint, then the per-particle walk.  A fixed grid
-// strides over the list (its length is read on the device, so the launch can
-// sit in a CUDA graph); each particle adds its new heading to its replica's
-// order parameter directly in FP64.
+// the step kernel left in U_hint.  A fixed grid covers a list of any length
+// (the length is read on the device, so the launch can sit in a CUDA graph);
+// particles that still cannot be served go on the walk list.  Each particle
+// adds its new heading to its replica's order parameter directly in FP64.
 template <int KC>
-__global__ void __launch_bounds__(kBlock, 2) knn2_deferred_kernel(
+__global__ void __launch_bounds__(kBlock, VK_KNN2_BOX_BLOCKS) knn2_deferred_kernel(
     const Rep* __restrict__ reps, const uint32_t* __restrict__ bounds, const int2* __restrict__ S_pos,
     const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G, int2* __restrict__ U_pos,
     float2* __restrict__ U_dir, int32_t* __restrict__ U_id, float* __restrict__ U_hint,
     uint32_t* __restrict__ counts, double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P,
-    const int2* __restrict__ defer_list, const int32_t* __restrict__ defer_count) {
+    const int2* __restrict__ defer_list, const int32_t* __restrict__ defer_count, int2* __restrict__ walk_list,
+    int32_t* __restrict__ walk_count) {
   extern __shared__ __align__(16) unsigned char box_smem[];
   BoxHits<KC>& H = *reinterpret_cast<BoxHits<KC>*>(box_smem);
-  const int total = *defer_count;
+  const int i = blockIdx.x * kBlock + (int)threadIdx.x;
+  if (i >= *defer_count) return;
+  const int64_t step = *d_step;
+  const int2 e = defer_list[i];
+  const int64_t s = e.x;
+  const Rep R = reps[e.y];
+  const int2 p = S_pos[s];
+  Ctx C;
+  init_ctx(C, R, s, p);
+  Top<KC> T;
+  BoxCount bc;
+  const float r = U_hint[s];
+  float r_next = -1.f;
+  if (!(r > 0.f && box_search<KC>(H, R, bounds, G, S_pos, C, r, P.k, kBoxTries, T, bc, &r_next))) {
+    walk_list[atomicAdd(walk_count, 1)] = e;
+    return;
+  }
+  float nnew[3] = {0.f, 0.f, 0.f};
+  knn2_update<KC>(R, P, step, s, p, S_dir[s], S_id[s], T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
+  U_hint[s] = sqrtf((float)T.d[KC - 1]) * 1.0001f + 1.f;
+  double* acc = phi_acc + ((size_t)(step % P.phi_cap) * (size_t)P.n_rep + (size_t)e.y) * 3;
+  atomicAdd(acc + 0, (double)nnew[0]);
+  atomicAdd(acc + 1, (double)nnew[1]);
+  if (P.stats) {
+    atomicAdd(P.stats + 0, (unsigned long long)bc.cand);
+    atomicAdd(P.stats + 1, (unsigned long long)bc.tries);
+    atomicMax(P.stats + 2, (unsigned long long)bc.cand);
+    atomicAdd(P.stats + 3, 1ull);
+  }
+}
+
+// Per-particle walk + update for the particles the radius-first kernels
+// could not serve (squares wider than the box allows, equal distances, no
+// fitting square).
+template <int KC>
+__global__ void __launch_bounds__(kBlock, 2) knn2_walk_list_kernel(
+    const Rep* __restrict__ reps, const uint32_t* __restrict__ bounds, const int2* __restrict__ S_pos,
+    const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G, int2* __restrict__ U_pos,
+    float2* __restrict__ U_dir, int32_t* __restrict__ U_id, float* __restrict__ U_hint,
+    uint32_t* __restrict__ counts, double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P,
+    const int2* __restrict__ walk_list, const int32_t* __restrict__ walk_count) {
+  const int total = *walk_count;
   const int64_t step = *d_step;
   for (int i = blockIdx.x * kBlock + (int)threadIdx.x; i < total; i += gridDim.x * kBlock) {
-    const int2 e = defer_list[i];
+    const int2 e = walk_list[i];
     const int64_t s = e.x;
     const Rep R = reps[e.y];
     const int2 p = S_pos[s];
     Ctx C;
     init_ctx(C, R, s, p);
     Top<KC> T;
-    BoxCount bc;
-    const float r = U_hint[s];
-    float r_next = -1.f;
-    const bool ok = r > 0.f && box_search<KC>(H, R, bounds, G, S_pos, C, r, P.k, kBoxTries, T, bc, &r_next);
-    if (!ok) {
-      top_init<KC>(T, P.k);
-      knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T, P.k);
-    }
+    top_init<KC>(T, P.k);
+    knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T, P.k);
     float nnew[3] = {0.f, 0.f, 0.f};
     knn2_update<KC>(R, P, step, s, p, S_dir[s], S_id[s], T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
     U_hint[s] = sqrtf((float)T.d[KC - 1]) * 1.0001f + 1.f;
@@ -1005,11 +1058,11 @@ __global__ void __launch_bounds__(kBlock, 2) knn2_deferred_kernel(
     atomicAdd(acc + 0, (double)nnew[0]);
     atomicAdd(acc + 1, (double)nnew[1]);
     if (P.stats) {
-      atomicAdd(P.stats + 0, (unsigned long long)(ok ? bc.cand : C.n_cand));
-      atomicAdd(P.stats + 1, (unsigned long long)(ok ? bc.tries : C.n_runs));
-      atomicMax(P.stats + 2, (unsigned long long)(ok ? bc.cand : C.n_cand));
+      atomicAdd(P.stats + 0, (unsigned long long)C.n_cand);
+      atomicAdd(P.stats + 1, (unsigned long long)C.n_runs);
+      atomicMax(P.stats + 2, (unsigned long long)C.n_cand);
       atomicAdd(P.stats + 3, 1ull);
-      if (!ok) atomicAdd(P.stats + 4, 1ull);
+      atomicAdd(P.stats + 4, 1ull);
     }
   }
 }
@@ -1080,10 +1133,23 @@ constexpr size_t box_smem_bytes() {
   return sizeof(BoxHits<KC>);
 }
 
-// blocks of the list kernels: enough threads for a list of every particle
-// (the length is known only on the device; threads past it exit at once),
-// so a long list never queues on a few threads
+// blocks of the deferred-particle kernel: enough threads for a list of every
+// particle (the length is known only on the device; threads past it exit at
+// once), so a long list never queues on a few threads
 int walk_blocks(const Geometry& g) { return (int)std::max<int64_t>(1, (g.n_total + kBlock - 1) / kBlock); }
+
+// blocks of the walk-list kernels: a small fixed grid striding over the
+// (short) list
+int walk_list_blocks(const Geometry& g) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      sms = 1;
+  }
+  return (int)std::max<int64_t>(1, std::min<int64_t>((g.n_total + kBlock - 1) / kBlock, sms));
+}
 
 template <int KC>
 cudaError_t step2(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st) {
@@ -1098,9 +1164,15 @@ cudaError_t step2(const Geometry& g, const Buffers& b, const StepParams& P, cuda
         g.reps, g.tasks, b.bounds, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id, b.S_hint, view_of(b),
         (int2*)b.U_pos, (float2*)b.U_dir, b.U_id, b.U_hint, b.counts, b.phi_acc, b.d_step, P, b.ovf_list,
         b.ovf_count);
+    // the deferred list lives in the first half of ovf_list, the walk list in the second
     knn2_deferred_kernel<KC><<<walk_blocks(g), kBlock, box_smem_bytes<KC>(), st>>>(
         g.reps, b.bounds, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id, view_of(b), (int2*)b.U_pos,
-        (float2*)b.U_dir, b.U_id, b.U_hint, b.counts, b.phi_acc, b.d_step, P, b.ovf_list, b.ovf_count);
+        (float2*)b.U_dir, b.U_id, b.U_hint, b.counts, b.phi_acc, b.d_step, P, b.ovf_list, b.ovf_count,
+        b.ovf_list + g.n_total, b.ovf_count + 1);
+    knn2_walk_list_kernel<KC><<<walk_list_blocks(g), kBlock, 0, st>>>(
+        g.reps, b.bounds, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id, view_of(b), (int2*)b.U_pos,
+        (float2*)b.U_dir, b.U_id, b.U_hint, b.counts, b.phi_acc, b.d_step, P, b.ovf_list + g.n_total,
+        b.ovf_count + 1);
   }
   return cudaGetLastError();
 }
@@ -1119,7 +1191,7 @@ cudaError_t export2(const Geometry& g, const Buffers& b, int k, int rep, int n, 
     knn2_box_export_kernel<KC><<<nb, kBlock, box_smem_bytes<KC>(), st>>>(
         g.reps, rep, b.bounds, (const int2*)b.S_pos, b.S_id, b.S_hint, view_of(b), k, P.halo_alpha, P.halo_beta,
         out, b.ovf_list, b.ovf_count);
-    knn2_walk_export_list_kernel<KC><<<walk_blocks(g), kBlock, 0, st>>>(g.reps, b.bounds, (const int2*)b.S_pos,
+    knn2_walk_export_list_kernel<KC><<<walk_list_blocks(g), kBlock, 0, st>>>(g.reps, b.bounds, (const int2*)b.S_pos,
                                                                          b.S_id, view_of(b), k, out, b.ovf_list,
                                                                          b.ovf_count);
     // leave the list empty for the next step

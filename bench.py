@@ -55,6 +55,10 @@ def parse():
                     help="2D kNN search: warp tiles (default) or the per-particle walk only")
     ap.add_argument("--halo", type=float, default=0.0,
                     help="warp-tile halo as a multiple of the previous k-th distance (0: library default)")
+    ap.add_argument("--no-replicas", action="store_true",
+                    help="skip the replica-batch block of the headline line")
+    ap.add_argument("--replica-steps", type=int, default=10,
+                    help="timed (and warm-up) steps of each arm of the replica-batch block")
     ap.add_argument("--autotune", action="store_true",
                     help="let the library's autotuner pick the occupancy on the warmed-up state instead")
     ap.add_argument("--scenario", choices=["headline", "replicas", "voronoi", "knn3d"], default="headline",
@@ -148,7 +152,7 @@ def measured_peaks():
 
 
 def kernel_source_sha() -> str:
-    """Hash of the sources the dominant kernel (knn2_step_kernel) is built from."""
+    """Hash of the sources the dominant kernel (knn2_box_step_kernel) is built from."""
     h = hashlib.sha256()
     for f in ("vk_internal.cuh", "vk_knn2d.cu"):
         h.update(open(os.path.join(CSRC, f), "rb").read())
@@ -159,7 +163,7 @@ def recorded_traffic(workload_name: str, occupancy):
     """DRAM bytes per launch of the search+update kernel from the committed
     ncu summary, if it was taken on the current kernel sources, workload and
     coarse-grid occupancy."""
-    p = os.path.join(ROOT, "profiles", "knn2_step_kernel_clustered4M.md")
+    p = os.path.join(ROOT, "profiles", "knn2_box_step_kernel_clustered4M.md")
     if not os.path.exists(p):
         return None
     txt = open(p).read()
@@ -343,9 +347,12 @@ def run_ours(args, rank, world, dist):
     ms_per_step = secs * 1e3 / args.steps
     value = units / secs
 
-    # dominant kernel: the fused search + update
+    # dominant kernel: the fused radius-first search + update of every
+    # particle (phase search_update, one launch per step); the particles it
+    # lists are finished in the search_deferred phase
     su_ms, su_launches = prof["search_update"]
     per_launch_ms = su_ms / max(1, su_launches)
+    sd_ms = prof.get("search_deferred", (0.0, 0))[0]
     alg_bytes = ALG_BYTES_PER_PARTICLE_STEP * w.n
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
@@ -383,6 +390,9 @@ def run_ours(args, rank, world, dist):
 
     info = sim.info()
     sim.close()
+    replicas = None
+    if rank == 0 and world == 1 and not args.no_replicas:
+        replicas = replica_block(stream, args.replica_steps)
     if rank != 0:
         return
     phases = {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}
@@ -394,9 +404,10 @@ def run_ours(args, rank, world, dist):
                                             l2_bytes=int(torch.cuda.get_device_properties(dev).L2_cache_size)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "knn2_step_kernel (kNN search + align + advect)",
+                     "kernel": "knn2_box_step_kernel (radius-first kNN search + align + advect)",
                      "alg_bytes_per_launch": alg_bytes, "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
-                     "kernel_ms_per_launch": per_launch_ms},
+                     "kernel_ms_per_launch": per_launch_ms,
+                     "search_phase_ms_per_step": (su_ms + sd_ms) / args.steps},
         "step_roofline": {"achieved_gbs": alg_bytes / (ms_per_step * 1e-3) / 1e9,
                           "frac": alg_bytes / (ms_per_step * 1e-3) / 1e9 / peak,
                           "note": "24 B per particle-step over the whole step"},
@@ -406,9 +417,48 @@ def run_ours(args, rank, world, dist):
                                   "achieved_gbs": 32 * w.n / (per_launch_ms * 1e-3) / 1e9,
                                   "frac": 32 * w.n / (per_launch_ms * 1e-3) / 1e9 / peak},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(info.kernels_per_step) * args.steps,
-        "clocks": clk, "phases": phases, "wall_s_timed_region": t_wall,
+        "clocks": clk, "phases": phases, "wall_s_timed_region": t_wall, "replicas": replicas,
     }
     print(json.dumps(line), flush=True)
+
+
+def replica_block(stream, steps: int) -> dict:
+    """The batched-replica pattern: 512 replicas (N_r log-uniform in
+    [1024, 65536], k = 7, F = 16) stepped together (one launch per kernel,
+    multi-step CUDA graph) against the same replicas as separate systems with
+    one launch sequence each.  Both arms start from the same states, take the
+    same number of warm-up steps, and evolve identically (each separate
+    system draws its noise with its replica index)."""
+    from paper_2103_10239_gb300 import vk
+    from paper_2103_10239_gb300 import workloads as W
+    ws = W.replica_batch()
+    total = sum(w.n for w in ws)
+    sim = vk.batch_from_workloads(ws, stream=stream)
+    sim.set_graph_steps(steps)
+    sim.step(steps)  # warm-up, also captures the graph
+    ms_b = _timed(stream, lambda: sim.step(steps)) / steps
+    pos_b, _, _, t_b = sim.state(300)
+    sim.close()
+    sims = [vk.from_workload(w, stream=stream, replica_offset=r) for r, w in enumerate(ws)]
+    for x in sims:
+        x.step(steps)  # the same warm-up
+
+    def per_rep():
+        for _ in range(steps):
+            for x in sims:
+                x.step(1)
+    ms_p = _timed(stream, per_rep) / steps
+    pos_p, _, _, t_p = sims[300].state()
+    for x in sims:
+        x.close()
+    return {"metric": "particle-steps/s, 512 replicas in one launch per kernel + multi-step graph",
+            "value": total / (ms_b * 1e-3), "unit": "particle-steps/s", "ms_per_step": ms_b,
+            "per_replica_launches": {"value": total / (ms_p * 1e-3), "ms_per_step": ms_p},
+            "speedup_vs_per_replica_launches": ms_p / ms_b,
+            "warmup_steps_each_arm": steps, "timed_steps_each_arm": steps,
+            "replica_300_identical_across_arms": bool(t_b == t_p and np.array_equal(pos_b, pos_p)),
+            "config": {"workload": "512 replicas, N_r log-uniform [1024, 65536], density 1, k=7, F=16, "
+                                   "eta 0.05-0.6", "n_total": total}}
 
 
 # ---------------------------------------------------------------------------

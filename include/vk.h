@@ -112,6 +112,9 @@ typedef struct {
                            Results never depend on it; only the speed does. */
   float search_halo_step; /* radius first: plus this multiple of the distance a particle moves
                            in one step (v0 dt); < 0 = default (0).  Speed only. */
+  int32_t replica_offset; /* noise counter index of the first replica (default 0): replica r
+                           draws with index replica_offset + r, so a single-replica sim with
+                           replica_offset = r reproduces replica r of a batch exactly */
 } vk_params;
 
 /* Fills p with the defaults: kNN, k = 7, v0 = 0.5, dt = 1, eta = 0.3, seed = 1,
@@ -196,7 +199,11 @@ vk_status vk_set_graph_steps(vk_sim* sim, int32_t steps_per_graph);
  * brackets every kernel phase with CUDA events on the sim's stream; level 2
  * also collects the search counters of vk_get_search_stats.
  * vk_get_profile returns, per phase, the summed event time in ms and the
- * launch count since profiling was enabled, plus the phase names. */
+ * launch count since profiling was enabled, plus the phase names.  Phases:
+ * 0 search_update (the search + update kernel of every particle), 1 build
+ * (grid scans), 2 scatter, 3 load_sort (init / set_state), 4 export
+ * (vk_get_neighbors), 5 search_deferred (2D kNN radius first: the particles
+ * the first kernel listed for larger squares or the walk). */
 vk_status vk_set_profiling(vk_sim* sim, int32_t enable);
 vk_status vk_get_profile(vk_sim* sim, double* ms, int64_t* launches, int32_t max_phases,
                          int32_t* n_phases);

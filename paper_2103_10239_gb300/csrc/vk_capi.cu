@@ -20,9 +20,9 @@ using namespace vk;
 
 namespace {
 
-constexpr int kPhases = 5;
+constexpr int kPhases = 6;
 constexpr int kCounters = 14;  // search counters (tracing level 2)
-const char* kPhaseNames[kPhases] = {"search_update", "build", "scatter", "load_sort", "export"};
+const char* kPhaseNames[kPhases] = {"search_update", "build", "scatter", "load_sort", "export", "search_deferred"};
 
 thread_local std::string g_init_error;
 
@@ -63,8 +63,8 @@ struct vk_sim {
   bool prof = false;
   bool prof_counters = false;  // search counters (tracing level 2)
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[kPhases];
-  double prof_ms[kPhases] = {0, 0, 0, 0, 0};
-  int64_t prof_launches[kPhases] = {0, 0, 0, 0, 0};
+  double prof_ms[kPhases] = {0, 0, 0, 0, 0, 0};
+  int64_t prof_launches[kPhases] = {0, 0, 0, 0, 0, 0};
   unsigned long long* d_stats = nullptr;  // search counters, collected while tracing
   std::string err;
 };
@@ -269,7 +269,13 @@ vk_status enqueue_step(vk_sim* s) {
   if (s->prm.rule == VK_RULE_KNN && s->dim == 2) VK_CUDA(s, launch_knn2_step(s->g, s->b, P, s->stream));
   else if (s->prm.rule == VK_RULE_KNN) VK_CUDA(s, launch_knn_step(s->g, s->b, P, s->stream));
   else VK_CUDA(s, launch_voronoi_step(s->g, s->b, P, s->stream));
-  if ((st = record_end(s, 0, e0, search_launches(s)))) return st;
+  const int deferred_launches = (s->prm.rule == VK_RULE_KNN && s->dim == 2 && s->prm.knn_search == 0) ? 2 : 0;
+  if ((st = record_end(s, 0, e0, search_launches(s) - deferred_launches))) return st;
+  if (deferred_launches) {
+    if ((st = record_begin(s, 5, &e0))) return st;
+    VK_CUDA(s, launch_knn2_finish(s->g, s->b, P, s->stream));
+    if ((st = record_end(s, 5, e0, deferred_launches))) return st;
+  }
   if ((st = record_begin(s, 1, &e0))) return st;
   VK_CUDA(s, launch_build(s->g, s->b, s->stream));
   if ((st = record_end(s, 1, e0, 7))) return st;
@@ -316,6 +322,7 @@ bool valid_params(const vk_params* p, int dim, std::string* why) {
   if (p->knn_search != 0 && p->knn_search != 1) return *why = "knn_search must be 0 or 1", false;
   if (!(p->search_halo >= 0.f) || !std::isfinite(p->search_halo)) return *why = "search_halo must be >= 0", false;
   if (!std::isfinite(p->search_halo_step)) return *why = "search_halo_step must be finite", false;
+  if (p->replica_offset < 0) return *why = "replica_offset must be >= 0", false;
   return true;
 }
 
@@ -375,7 +382,7 @@ vk_status build_sim(int32_t n_rep, const int64_t* n_r, const int32_t* pos_q, con
     s->eta_r[r] = R.eta;
     const float vdt = params->v0 * params->dt;
     R.s = (float)std::ldexp((double)vdt, boxes[r].frac_bits);
-    R.replica = (uint32_t)r;
+    R.replica = (uint32_t)(r + params->replica_offset);
     for (int first = 0; first < R.n; first += kBlock) s->tasks_h.push_back({r, first});
     p0 += n_r[r];
   }
@@ -473,6 +480,7 @@ void vk_default_params(vk_params* p) {
   p->knn_search = 0;
   p->search_halo = 0.f;
   p->search_halo_step = -1.f;
+  p->replica_offset = 0;
 }
 
 vk_status vk_init(const int32_t* pos_q, const float* heading, int32_t heading_kind, int64_t n,

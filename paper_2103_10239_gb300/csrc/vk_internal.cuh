@@ -633,7 +633,11 @@ cudaError_t launch_knn_export(const Geometry& g, const Buffers& b, int k, int re
                               cudaStream_t st);
 
 // vk_knn2d.cu (the 2D kNN hot path)
+// search + update of every particle (radius first: those it can serve; the
+// rest is listed) ...
 cudaError_t launch_knn2_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st);
+// ... and of the listed particles (deferred squares, then the walk); no-op for the walk-only search
+cudaError_t launch_knn2_finish(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st);
 cudaError_t launch_knn2_export(const Geometry& g, const Buffers& b, int k, int rep, int n, int32_t* out,
                                cudaStream_t st, const StepParams& P);
 // one-time kernel attributes (shared memory of the radius-first search)

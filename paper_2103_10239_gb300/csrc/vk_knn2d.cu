@@ -1159,11 +1159,18 @@ cudaError_t step2(const Geometry& g, const Buffers& b, const StepParams& P, cuda
                                                        (float2*)b.U_dir, b.U_id, b.counts, b.phi_acc, b.d_step, P);
     if (b.U_hint) cudaMemsetAsync(b.U_hint, 0, sizeof(float) * (size_t)g.n_total, st);
   } else {
-    // the walk list is empty here: the previous scatter (or init) cleared it
+    // the lists are empty here: the previous scatter (or init) cleared them
     knn2_box_step_kernel<KC><<<g.n_tasks, kBlock, box_smem_bytes<KC>(), st>>>(
         g.reps, g.tasks, b.bounds, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id, b.S_hint, view_of(b),
         (int2*)b.U_pos, (float2*)b.U_dir, b.U_id, b.U_hint, b.counts, b.phi_acc, b.d_step, P, b.ovf_list,
         b.ovf_count);
+  }
+  return cudaGetLastError();
+}
+
+template <int KC>
+cudaError_t finish2(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st) {
+  if (P.knn_search == 0 && b.S_hint) {
     // the deferred list lives in the first half of ovf_list, the walk list in the second
     knn2_deferred_kernel<KC><<<walk_blocks(g), kBlock, box_smem_bytes<KC>(), st>>>(
         g.reps, b.bounds, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id, view_of(b), (int2*)b.U_pos,
@@ -1227,6 +1234,12 @@ cudaError_t launch_knn2_step(const Geometry& g, const Buffers& b, const StepPara
   if (P.k <= 8) return step2<8>(g, b, P, st);
   if (P.k <= 16) return step2<16>(g, b, P, st);
   return step2<32>(g, b, P, st);
+}
+
+cudaError_t launch_knn2_finish(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st) {
+  if (P.k <= 8) return finish2<8>(g, b, P, st);
+  if (P.k <= 16) return finish2<16>(g, b, P, st);
+  return finish2<32>(g, b, P, st);
 }
 
 cudaError_t launch_knn2_export(const Geometry& g, const Buffers& b, int k, int rep, int n, int32_t* out,

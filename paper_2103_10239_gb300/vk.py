@@ -23,7 +23,7 @@ VK_RULE_KNN, VK_RULE_VORONOI = 0, 1
 VK_NOISE_ANGULAR, VK_NOISE_VECTORIAL = 0, 1
 VK_SUM_PLAIN, VK_SUM_COMPENSATED, VK_SUM_FP64 = 0, 1, 2
 VK_HEADING_DIR, VK_HEADING_THETA = 0, 1
-PHASES = ("search_update", "scan", "scatter", "load_sort", "export")
+PHASES = ("search_update", "build", "scatter", "load_sort", "export", "search_deferred")
 
 
 class VKError(RuntimeError):
@@ -43,7 +43,7 @@ class vk_params(ctypes.Structure):
                 ("advect_new", ctypes.c_int32), ("sum_mode", ctypes.c_int32),
                 ("cell_occupancy", ctypes.c_float), ("phi_capacity", ctypes.c_int32),
                 ("knn_search", ctypes.c_int32), ("search_halo", ctypes.c_float),
-                ("search_halo_step", ctypes.c_float)]
+                ("search_halo_step", ctypes.c_float), ("replica_offset", ctypes.c_int32)]
 
 
 class vk_info(ctypes.Structure):

@@ -30,6 +30,15 @@ def test_batch_equals_single_runs():
             pos, d, _, _ = sim.state(r)
         assert np.array_equal(pos, batch[r][0])
         assert np.array_equal(d, batch[r][1])
+    # and a single system created on its own with replica_offset = r (its own
+    # grid, its own launches) reproduces it too
+    for r in (3, 4, 10):
+        with vk.from_workload(ws[r], replica_offset=r) as sim:
+            sim.step(20)
+            pos, d, _, t = sim.state()
+        assert t == 20
+        assert np.array_equal(pos, batch[r][0])
+        assert np.array_equal(d, batch[r][1])
 
 
 def test_batch_teacher_forced_parity():

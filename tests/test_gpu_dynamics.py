@@ -111,8 +111,9 @@ def test_profiling_counts_phases():
         sim.step(5)
         prof = sim.profile()
         kps = sim.info().kernels_per_step
-    # 2D kNN: the radius-first, deferred-particle and walk-list kernels per step
-    assert prof["search_update"][1] == 15 and prof["build"][1] == 35 and prof["scatter"][1] == 5
+    # 2D kNN: the radius-first kernel, then the deferred-particle and walk-list kernels, per step
+    assert prof["search_update"][1] == 5 and prof["search_deferred"][1] == 10
+    assert prof["build"][1] == 35 and prof["scatter"][1] == 5
     assert prof["search_update"][0] > 0
     assert kps == 11
 

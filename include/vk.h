@@ -277,11 +277,16 @@ vk_status vk_autotune(vk_sim* sim, const float* candidates, int32_t n_candidates
  *            VK_ERR_RANGE when a point lay outside the box
  * Asynchronous on cuda_stream (NULL: the legacy default stream).  Returns
  * VK_ERR_ARG for n > VK_NOALLOC_MAX_N, n < 2, k outside [1, min(32, n-1)] or
- * a non-2D box.  The first call on each device looks up the device address
- * of the scratch array, so make that first call outside stream capture.  All
- * calls share the one scratch array and leave their intermediates in it:
- * calls that can overlap on the GPU (different streams, different host
- * threads) race and must be serialised by the caller. */
+ * a non-2D box; these checks, and the check that the intermediates fit the
+ * scratch (VK_ERR_CAPACITY, which no valid n reaches), run on the host before
+ * any device work.  An error left pending by earlier CUDA work of the caller
+ * gives VK_ERR_CUDA and stays pending.  The first call on each device looks
+ * up the device address of the scratch array and keeps it for the life of
+ * the process, so make that first call outside stream capture, and do not
+ * call this entry point again after cudaDeviceReset (the kept address is
+ * then stale).  All calls share the one scratch array and leave their
+ * intermediates in it: calls that can overlap on the GPU (different streams,
+ * different host threads) race and must be serialised by the caller. */
 #define VK_NOALLOC_MAX_N 65536
 vk_status vk_knn_lists_noalloc(const int32_t* pos_q, int64_t n, const vk_box* box, int32_t k,
                                int32_t* out_ids, int32_t* dev_status, void* cuda_stream);

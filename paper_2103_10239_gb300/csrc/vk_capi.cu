@@ -248,7 +248,7 @@ vk_status read_status(vk_sim* s) {
 }
 
 vk_status clear_phi(vk_sim* s) {
-  VK_CUDA(s, cudaMemsetAsync(s->b.phi_acc, 0, sizeof(double) * 3 * (size_t)s->phi_cap * s->n_rep, s->stream));
+  VK_CUDA(s, cudaMemsetAsync(s->b.phi_acc, 0, sizeof(PhiAcc) * 3 * (size_t)s->phi_cap * s->n_rep, s->stream));
   s->phi_first = s->step;
   return VK_OK;
 }
@@ -595,14 +595,17 @@ vk_status vk_get_order_parameter(vk_sim* s, int32_t replica, double* phi, int64_
   const int64_t nout = std::min<int64_t>(have, std::max<int64_t>(0, max_values));
   if (count) *count = nout;
   if (nout == 0) return VK_OK;
-  std::vector<double> ring(3 * (size_t)s->phi_cap * s->n_rep);
-  VK_CUDA(s, cudaMemcpy(ring.data(), s->b.phi_acc, sizeof(double) * ring.size(), cudaMemcpyDeviceToHost));
+  std::vector<long long> ring(3 * (size_t)s->phi_cap * s->n_rep);
+  VK_CUDA(s, cudaMemcpy(ring.data(), s->b.phi_acc, sizeof(long long) * ring.size(), cudaMemcpyDeviceToHost));
   std::vector<double> vals(nout);
   const double n = (double)s->reps_h[replica].n;
   for (int64_t i = 0; i < nout; ++i) {
     const int64_t t = s->step - nout + i;  // phi after the update from step t to t+1
-    const double* a = ring.data() + ((size_t)(t % s->phi_cap) * s->n_rep + replica) * 3;
-    vals[i] = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) / n;
+    const long long* a = ring.data() + ((size_t)(t % s->phi_cap) * s->n_rep + replica) * 3;
+    // fixed-point sums (2^-32 units) -> FP64
+    const double x = std::ldexp((double)a[0], -32), y = std::ldexp((double)a[1], -32),
+                 z = std::ldexp((double)a[2], -32);
+    vals[i] = std::sqrt(x * x + y * y + z * z) / n;
   }
   VK_CUDA(s, cudaMemcpy(phi, vals.data(), sizeof(double) * nout, cudaMemcpyDefault));
   return VK_OK;
@@ -822,7 +825,7 @@ vk_status vk_autotune(vk_sim* s, const float* candidates, int32_t n_candidates, 
   void* snap_pos = nullptr;
   void* snap_dir = nullptr;
   int32_t* snap_id = nullptr;
-  double* snap_phi = nullptr;
+  PhiAcc* snap_phi = nullptr;
   const size_t phin = 3 * (size_t)s->phi_cap * s->n_rep;
   cudaError_t e = cudaMalloc(&snap_pos, pv * N);
   if (e == cudaSuccess) e = cudaMalloc(&snap_dir, fv * N);
@@ -842,7 +845,7 @@ vk_status vk_autotune(vk_sim* s, const float* candidates, int32_t n_candidates, 
   if (e == cudaSuccess) e = cudaMemcpyAsync(snap_dir, s->b.S_dir, fv * N, cudaMemcpyDeviceToDevice, s->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(snap_id, s->b.S_id, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(snap_phi, s->b.phi_acc, sizeof(double) * phin, cudaMemcpyDeviceToDevice, s->stream);
+    e = cudaMemcpyAsync(snap_phi, s->b.phi_acc, sizeof(PhiAcc) * phin, cudaMemcpyDeviceToDevice, s->stream);
   const int64_t step0 = s->step, phi_first0 = s->phi_first;
   const bool prof0 = s->prof;
   s->prof = false;
@@ -856,7 +859,7 @@ vk_status vk_autotune(vk_sim* s, const float* candidates, int32_t n_candidates, 
     VK_CUDA(s, cudaMemcpyAsync(s->b.U_dir, snap_dir, fv * N, cudaMemcpyDeviceToDevice, s->stream));
     VK_CUDA(s, cudaMemcpyAsync(s->b.U_id, snap_id, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s->stream));
     VK_CUDA(s, cudaMemcpyAsync(s->b.d_step, &step0, sizeof(int64_t), cudaMemcpyHostToDevice, s->stream));
-    VK_CUDA(s, cudaMemcpyAsync(s->b.phi_acc, snap_phi, sizeof(double) * phin, cudaMemcpyDeviceToDevice, s->stream));
+    VK_CUDA(s, cudaMemcpyAsync(s->b.phi_acc, snap_phi, sizeof(PhiAcc) * phin, cudaMemcpyDeviceToDevice, s->stream));
     if ((st = sort_from_U(s))) return st;
     VK_CUDA(s, cudaStreamSynchronize(s->stream));
     s->step = step0;

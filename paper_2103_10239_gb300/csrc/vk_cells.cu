@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kBlock) scatter_kernel(const Rep* __restrict__
                                                          int32_t* __restrict__ S_id,
                                                          const float* __restrict__ U_hint,
                                                          float* __restrict__ S_hint, int advance_step,
-                                                         int64_t* d_step, double* phi_acc, int n_rep,
+                                                         int64_t* d_step, PhiAcc* phi_acc, int n_rep,
                                                          int phi_cap, int32_t* ovf_count) {
   const BlockTask t = tasks[blockIdx.x];
   const Rep R = reps[t.rep];
@@ -297,8 +297,8 @@ __global__ void __launch_bounds__(kBlock) scatter_kernel(const Rep* __restrict__
   if (advance_step && blockIdx.x == 0) {
     // clear the order-parameter slot of the next step, then advance the step
     const int64_t nxt = *d_step + 1;
-    double* slot = phi_acc + (size_t)(nxt % phi_cap) * (size_t)n_rep * 3;
-    for (int i = threadIdx.x; i < n_rep * 3; i += blockDim.x) slot[i] = 0.0;
+    PhiAcc* slot = phi_acc + (size_t)(nxt % phi_cap) * (size_t)n_rep * 3;
+    for (int i = threadIdx.x; i < n_rep * 3; i += blockDim.x) slot[i] = 0ull;
     __syncthreads();
     if (threadIdx.x == 0) {
       *d_step = nxt;

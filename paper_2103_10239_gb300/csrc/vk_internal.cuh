@@ -498,13 +498,31 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Block-wide compensated sum of v[0..DIM) without a block barrier at the end:
-// every warp reduces its lanes and parks the partial in shared memory; the
-// last warp of the block to arrive adds the block total into acc[0..DIM) with
-// FP64 atomics.  phi_block_begin() must be called by all threads first.
+// Order parameter accumulators.  Every heading component is rounded to a
+// fixed point of 2^-32 (exact scaling of the FP32 value, then round to the
+// nearest integer) and summed in int64: integer addition is exact and
+// associative, so the sums, and phi, are bit-identical from run to run
+// whatever order the particles are visited in (the order inside a cell of
+// the sorted state comes from atomic ranks).  The rounding errs by at most
+// 2^-33 per particle, about 1e-10 of phi.  N <= 2^31 keeps the sums below
+// 2^63.  The FP64 conversion happens when phi is read.
+using PhiAcc = unsigned long long;
+constexpr float kPhiScale = 4294967296.0f;  // 2^32
+
+__device__ __forceinline__ long long phi_fixed(float v) { return __float2ll_rn(v * kPhiScale); }
+
+__device__ __forceinline__ long long warp_sum_ll(long long x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Block-wide sum of v[0..DIM) without a block barrier at the end: every warp
+// reduces its lanes and parks the partial in shared memory; the last warp of
+// the block to arrive adds the block total into acc[0..DIM).
+// phi_block_begin() must be called by all threads first.
 struct PhiShared {
-  float s[kBlock / 32][3];
-  float c[kBlock / 32][3];
+  long long s[kBlock / 32][3];
   unsigned int arrived;
 };
 
@@ -514,50 +532,54 @@ __device__ __forceinline__ void phi_block_begin(PhiShared& sh) {
 }
 
 template <int DIM>
-__device__ __forceinline__ void phi_block_end(PhiShared& sh, const float* v, double* acc) {
-  float s[DIM], c[DIM];
+__device__ __forceinline__ void phi_block_end(PhiShared& sh, const float* v, PhiAcc* acc) {
+  long long s[DIM];
 #pragma unroll
-  for (int a = 0; a < DIM; ++a) { s[a] = v[a]; c[a] = 0.f; }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      const float os = __shfl_xor_sync(0xffffffffu, s[a], o);
-      const float oc = __shfl_xor_sync(0xffffffffu, c[a], o);
-      float t, e;
-      two_sum(s[a], os, t, e);
-      s[a] = t;
-      c[a] = __fadd_rn(__fadd_rn(c[a], oc), e);
-    }
-  }
+  for (int a = 0; a < DIM; ++a) s[a] = warp_sum_ll(phi_fixed(v[a]));
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      ((volatile float*)sh.s[wid])[a] = s[a];
-      ((volatile float*)sh.c[wid])[a] = c[a];
-    }
+    for (int a = 0; a < DIM; ++a) ((volatile long long*)sh.s[wid])[a] = s[a];
     __threadfence_block();
     const unsigned int before = atomicAdd(&sh.arrived, 1u);
     if (before == blockDim.x / 32 - 1) {
       __threadfence_block();
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
-        double t = 0.0;
-        for (int w2 = 0; w2 < (int)(blockDim.x / 32); ++w2)
-          t += (double)((volatile float*)sh.s[w2])[a] + (double)((volatile float*)sh.c[w2])[a];
-        atomicAdd(acc + a, t);
+        long long t = 0;
+        for (int w2 = 0; w2 < (int)(blockDim.x / 32); ++w2) t += ((volatile long long*)sh.s[w2])[a];
+        atomicAdd(acc + a, (PhiAcc)t);
       }
     }
   }
 }
 
-// (kept for kernels whose warps finish together)
+// (for kernels whose warps finish together: both halves at the end)
 template <int DIM>
-__device__ __forceinline__ void block_phi_accumulate(const float* v, double* acc) {
+__device__ __forceinline__ void block_phi_accumulate(const float* v, PhiAcc* acc) {
   __shared__ PhiShared sh;
   phi_block_begin(sh);
   phi_block_end<DIM>(sh, v, acc);
+}
+
+// Warp-wide add of the headings of the active lanes, each to its own
+// replica's accumulators step_acc + 3 * rep (lanes of one replica are summed
+// first, then one lane adds the total).  All lanes of the warp must call it.
+template <int DIM>
+__device__ __forceinline__ void phi_add_warp(PhiAcc* step_acc, int rep, const float* v, bool active) {
+  const int lane = threadIdx.x & 31;
+  unsigned rem = __ballot_sync(0xffffffffu, active);
+  while (rem) {
+    const int leader = __ffs(rem) - 1;
+    const int r = __shfl_sync(0xffffffffu, rep, leader);
+    const bool in = active && rep == r;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const long long t = warp_sum_ll(in ? phi_fixed(v[a]) : 0ll);
+      if (lane == leader) atomicAdd(step_acc + (size_t)r * 3 + a, (PhiAcc)t);
+    }
+    rem &= ~__ballot_sync(0xffffffffu, in);
+  }
 }
 
 __device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
@@ -568,6 +590,15 @@ __device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
 
 // host-side launchers (defined in the .cu files)
 namespace vk {
+
+// streaming multiprocessors of the current device (for fixed-size grids)
+inline int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms <= 0)
+    return 1;
+  return sms;
+}
 
 struct Buffers {
   // sorted current state
@@ -588,7 +619,7 @@ struct Buffers {
   uint32_t* sub_off;    // n_sub_max + 1
   uint32_t* bsum2;      // scan block sums (sub-cells)
   uint32_t* bounds;     // per replica and axis: first coordinate of every cell (nc + 1 entries)
-  double* phi_acc;    // phi_cap * n_rep * 3
+  PhiAcc* phi_acc;    // phi_cap * n_rep * 3 fixed-point heading sums (see PhiAcc)
   int64_t* d_step;
   int32_t* d_status;
   int2* ovf_list;      // 2 N entries of (slot, replica): Voronoi cells too large for the main kernel;

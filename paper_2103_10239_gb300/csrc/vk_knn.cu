@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kBlock) knn_step_kernel(
     const typename Vec<DIM>::P* __restrict__ S_pos, const typename Vec<DIM>::F* __restrict__ S_dir,
     const int32_t* __restrict__ S_id, GridView G, typename Vec<DIM>::P* __restrict__ U_pos,
     typename Vec<DIM>::F* __restrict__ U_dir, int32_t* __restrict__ U_id,
-    uint32_t* __restrict__ counts, double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P) {
+    uint32_t* __restrict__ counts, PhiAcc* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P) {
   using PV = typename Vec<DIM>::P;
   using FV = typename Vec<DIM>::F;
   const BlockTask t = tasks[blockIdx.x];

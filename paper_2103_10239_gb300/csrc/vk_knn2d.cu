@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(kBlock, VK_KNN2_MIN_BLOCKS) knn2_step_kernel(
     const Rep* __restrict__ reps, const BlockTask* __restrict__ tasks, const uint32_t* __restrict__ bounds,
     const int2* __restrict__ S_pos, const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G,
     int2* __restrict__ U_pos, float2* __restrict__ U_dir, int32_t* __restrict__ U_id, uint32_t* __restrict__ counts,
-    double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P) {
+    PhiAcc* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P) {
   __shared__ PhiShared phs;
   phi_block_begin(phs);
   const BlockTask t = tasks[blockIdx.x];
@@ -945,7 +945,7 @@ __global__ void __launch_bounds__(kBlock, VK_KNN2_BOX_BLOCKS) knn2_box_step_kern
     const int2* __restrict__ S_pos, const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id,
     const float* __restrict__ S_hint, GridView G, int2* __restrict__ U_pos, float2* __restrict__ U_dir,
     int32_t* __restrict__ U_id, float* __restrict__ U_hint, uint32_t* __restrict__ counts,
-    double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P, int2* __restrict__ defer_list,
+    PhiAcc* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P, int2* __restrict__ defer_list,
     int32_t* __restrict__ defer_count) {
   extern __shared__ __align__(16) unsigned char box_smem[];
   BoxHits<KC>& H = *reinterpret_cast<BoxHits<KC>*>(box_smem);
@@ -984,44 +984,49 @@ __global__ void __launch_bounds__(kBlock, VK_KNN2_BOX_BLOCKS) knn2_box_step_kern
 }
 
 // Search + update of the deferred particles: more squares from the radius
-// the step kernel left in U_hint.  A fixed grid covers a list of any length
-// (the length is read on the device, so the launch can sit in a CUDA graph);
-// particles that still cannot be served go on the walk list.  Each particle
-// adds its new heading to its replica's order parameter directly in FP64.
+// the step kernel left in U_hint.  A grid of one thread per particle covers
+// a list of any length (the length is read on the device, so the launch can
+// sit in a CUDA graph); particles that still cannot be served go on the walk
+// list.
 template <int KC>
 __global__ void __launch_bounds__(kBlock, VK_KNN2_BOX_BLOCKS) knn2_deferred_kernel(
     const Rep* __restrict__ reps, const uint32_t* __restrict__ bounds, const int2* __restrict__ S_pos,
     const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G, int2* __restrict__ U_pos,
     float2* __restrict__ U_dir, int32_t* __restrict__ U_id, float* __restrict__ U_hint,
-    uint32_t* __restrict__ counts, double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P,
+    uint32_t* __restrict__ counts, PhiAcc* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P,
     const int2* __restrict__ defer_list, const int32_t* __restrict__ defer_count, int2* __restrict__ walk_list,
     int32_t* __restrict__ walk_count) {
   extern __shared__ __align__(16) unsigned char box_smem[];
   BoxHits<KC>& H = *reinterpret_cast<BoxHits<KC>*>(box_smem);
+  const int total = *defer_count;
+  if ((int)(blockIdx.x * kBlock) >= total) return;  // whole block past the list
   const int i = blockIdx.x * kBlock + (int)threadIdx.x;
-  if (i >= *defer_count) return;
   const int64_t step = *d_step;
-  const int2 e = defer_list[i];
-  const int64_t s = e.x;
-  const Rep R = reps[e.y];
-  const int2 p = S_pos[s];
-  Ctx C;
-  init_ctx(C, R, s, p);
-  Top<KC> T;
-  BoxCount bc;
-  const float r = U_hint[s];
-  float r_next = -1.f;
-  if (!(r > 0.f && box_search<KC>(H, R, bounds, G, S_pos, C, r, P.k, kBoxTries, T, bc, &r_next))) {
-    walk_list[atomicAdd(walk_count, 1)] = e;
-    return;
-  }
   float nnew[3] = {0.f, 0.f, 0.f};
-  knn2_update<KC>(R, P, step, s, p, S_dir[s], S_id[s], T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
-  U_hint[s] = sqrtf((float)T.d[KC - 1]) * 1.0001f + 1.f;
-  double* acc = phi_acc + ((size_t)(step % P.phi_cap) * (size_t)P.n_rep + (size_t)e.y) * 3;
-  atomicAdd(acc + 0, (double)nnew[0]);
-  atomicAdd(acc + 1, (double)nnew[1]);
-  if (P.stats) {
+  bool served = false;
+  int rep = 0;
+  BoxCount bc;
+  if (i < total) {
+    const int2 e = defer_list[i];
+    const int64_t s = e.x;
+    rep = e.y;
+    const Rep R = reps[e.y];
+    const int2 p = S_pos[s];
+    Ctx C;
+    init_ctx(C, R, s, p);
+    Top<KC> T;
+    const float r = U_hint[s];
+    float r_next = -1.f;
+    served = r > 0.f && box_search<KC>(H, R, bounds, G, S_pos, C, r, P.k, kBoxTries, T, bc, &r_next);
+    if (served) {
+      knn2_update<KC>(R, P, step, s, p, S_dir[s], S_id[s], T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
+      U_hint[s] = sqrtf((float)T.d[KC - 1]) * 1.0001f + 1.f;
+    } else {
+      walk_list[atomicAdd(walk_count, 1)] = e;
+    }
+  }
+  phi_add_warp<2>(phi_acc + (size_t)(step % P.phi_cap) * (size_t)P.n_rep * 3, rep, nnew, served);
+  if (P.stats && served) {
     atomicAdd(P.stats + 0, (unsigned long long)bc.cand);
     atomicAdd(P.stats + 1, (unsigned long long)bc.tries);
     atomicMax(P.stats + 2, (unsigned long long)bc.cand);
@@ -1031,39 +1036,45 @@ __global__ void __launch_bounds__(kBlock, VK_KNN2_BOX_BLOCKS) knn2_deferred_kern
 
 // Per-particle walk + update for the particles the radius-first kernels
 // could not serve (squares wider than the box allows, equal distances, no
-// fitting square).
+// fitting square).  A small fixed grid strides over the (short) list; the
+// stride loop is warp-uniform so that the order-parameter add is too.
 template <int KC>
 __global__ void __launch_bounds__(kBlock, 2) knn2_walk_list_kernel(
     const Rep* __restrict__ reps, const uint32_t* __restrict__ bounds, const int2* __restrict__ S_pos,
     const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G, int2* __restrict__ U_pos,
     float2* __restrict__ U_dir, int32_t* __restrict__ U_id, float* __restrict__ U_hint,
-    uint32_t* __restrict__ counts, double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P,
+    uint32_t* __restrict__ counts, PhiAcc* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P,
     const int2* __restrict__ walk_list, const int32_t* __restrict__ walk_count) {
   const int total = *walk_count;
   const int64_t step = *d_step;
-  for (int i = blockIdx.x * kBlock + (int)threadIdx.x; i < total; i += gridDim.x * kBlock) {
-    const int2 e = walk_list[i];
-    const int64_t s = e.x;
-    const Rep R = reps[e.y];
-    const int2 p = S_pos[s];
-    Ctx C;
-    init_ctx(C, R, s, p);
-    Top<KC> T;
-    top_init<KC>(T, P.k);
-    knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T, P.k);
+  PhiAcc* step_acc = phi_acc + (size_t)(step % P.phi_cap) * (size_t)P.n_rep * 3;
+  for (int base = blockIdx.x * kBlock; base < total; base += gridDim.x * kBlock) {
+    const int i = base + (int)threadIdx.x;
     float nnew[3] = {0.f, 0.f, 0.f};
-    knn2_update<KC>(R, P, step, s, p, S_dir[s], S_id[s], T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
-    U_hint[s] = sqrtf((float)T.d[KC - 1]) * 1.0001f + 1.f;
-    double* acc = phi_acc + ((size_t)(step % P.phi_cap) * (size_t)P.n_rep + (size_t)e.y) * 3;
-    atomicAdd(acc + 0, (double)nnew[0]);
-    atomicAdd(acc + 1, (double)nnew[1]);
-    if (P.stats) {
-      atomicAdd(P.stats + 0, (unsigned long long)C.n_cand);
-      atomicAdd(P.stats + 1, (unsigned long long)C.n_runs);
-      atomicMax(P.stats + 2, (unsigned long long)C.n_cand);
-      atomicAdd(P.stats + 3, 1ull);
-      atomicAdd(P.stats + 4, 1ull);
+    int rep = 0;
+    const bool active = i < total;
+    if (active) {
+      const int2 e = walk_list[i];
+      const int64_t s = e.x;
+      rep = e.y;
+      const Rep R = reps[e.y];
+      const int2 p = S_pos[s];
+      Ctx C;
+      init_ctx(C, R, s, p);
+      Top<KC> T;
+      top_init<KC>(T, P.k);
+      knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T, P.k);
+      knn2_update<KC>(R, P, step, s, p, S_dir[s], S_id[s], T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
+      U_hint[s] = sqrtf((float)T.d[KC - 1]) * 1.0001f + 1.f;
+      if (P.stats) {
+        atomicAdd(P.stats + 0, (unsigned long long)C.n_cand);
+        atomicAdd(P.stats + 1, (unsigned long long)C.n_runs);
+        atomicMax(P.stats + 2, (unsigned long long)C.n_cand);
+        atomicAdd(P.stats + 3, 1ull);
+        atomicAdd(P.stats + 4, 1ull);
+      }
     }
+    phi_add_warp<2>(step_acc, rep, nnew, active);
   }
 }
 
@@ -1141,14 +1152,7 @@ int walk_blocks(const Geometry& g) { return (int)std::max<int64_t>(1, (g.n_total
 // blocks of the walk-list kernels: a small fixed grid striding over the
 // (short) list
 int walk_list_blocks(const Geometry& g) {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-      sms = 1;
-  }
-  return (int)std::max<int64_t>(1, std::min<int64_t>((g.n_total + kBlock - 1) / kBlock, sms));
+  return (int)std::max<int64_t>(1, std::min<int64_t>((g.n_total + kBlock - 1) / kBlock, device_sm_count()));
 }
 
 template <int KC>

@@ -57,15 +57,15 @@ cudaError_t scratch_ptr(void** out) {
   return cudaSuccess;
 }
 
+// lays out the intermediate arrays as 256-byte aligned offsets into the scratch
 struct Carver {
-  unsigned char* base;
   size_t used;
   template <class T>
-  T* take(size_t count) {
+  size_t take(size_t count) {
     used = (used + 255) & ~(size_t)255;
-    T* p = reinterpret_cast<T*>(base + used);
+    const size_t off = used;
     used += sizeof(T) * (count ? count : 1);
-    return p;
+    return off;
   }
 };
 
@@ -122,11 +122,6 @@ extern "C" vk_status vk_knn_lists_noalloc(const int32_t* pos_q, int64_t n, const
   for (int a = 0; a < 2; ++a)
     if (box->box_q[a] < 1 || box->box_q[a] > (1u << 31)) return VK_ERR_RANGE;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  void* base = nullptr;
-  if (scratch_ptr(&base) != cudaSuccess) {
-    cudaGetLastError();
-    return VK_ERR_CUDA;
-  }
 
   // grid plan (host arithmetic only)
   Rep R;
@@ -153,30 +148,50 @@ extern "C" vk_status vk_knn_lists_noalloc(const int32_t* pos_q, int64_t n, const
   const int64_t n_sub = n_cells + n / kSubTarget + 1;
   const int n_tasks = (int)((n + kBlock - 1) / kBlock);
 
-  // carve the scratch
-  Carver cv{reinterpret_cast<unsigned char*>(base), 0};
+  // carve the scratch: offsets first (host arithmetic, checked against the
+  // array's size before any device work), then the device address
+  Carver cv{0};
+  const size_t o_upos = cv.take<int2>(n), o_udir = cv.take<float2>(n), o_uid = cv.take<int32_t>(n);
+  const size_t o_urank = cv.take<uint32_t>(n);
+  const size_t o_spos = cv.take<int2>(n), o_sdir = cv.take<float2>(n), o_sid = cv.take<int32_t>(n);
+  const size_t o_counts = cv.take<uint32_t>(n_cells), o_offsets = cv.take<uint32_t>(n_cells + 1);
+  const size_t o_bsum = cv.take<uint32_t>(2 * ((n_cells + 2047) / 2048 + 1));
+  const size_t o_subs = cv.take<uint8_t>(n_cells), o_subbase = cv.take<uint32_t>(n_cells + 1);
+  const size_t o_subcount = cv.take<uint32_t>(n_sub), o_suboff = cv.take<uint32_t>(n_sub + 1);
+  const size_t o_bsum2 = cv.take<uint32_t>((n_sub + 2047) / 2048 + 1);
+  const size_t o_bounds = cv.take<uint32_t>(n_bounds);
+  const size_t o_rep = cv.take<Rep>(1), o_tasks = cv.take<BlockTask>(n_tasks), o_status = cv.take<int32_t>(1);
+  if (cv.used > kScratchBytes) return VK_ERR_CAPACITY;  // cannot happen for n <= kNoAllocMaxN
+  // an error left pending by the caller's earlier work is reported, not
+  // cleared (this call's status then says nothing about its own work)
+  if (cudaPeekAtLastError() != cudaSuccess) return VK_ERR_CUDA;
+  void* base_v = nullptr;
+  if (scratch_ptr(&base_v) != cudaSuccess) {
+    cudaGetLastError();  // the failed lookup's own error
+    return VK_ERR_CUDA;
+  }
+  unsigned char* base = reinterpret_cast<unsigned char*>(base_v);
   Buffers b;
   std::memset(&b, 0, sizeof(b));
-  b.U_pos = cv.take<int2>(n);
-  b.U_dir = cv.take<float2>(n);
-  b.U_id = cv.take<int32_t>(n);
-  b.U_rank = cv.take<uint32_t>(n);
-  b.S_pos = cv.take<int2>(n);
-  b.S_dir = cv.take<float2>(n);
-  b.S_id = cv.take<int32_t>(n);
-  b.counts = cv.take<uint32_t>(n_cells);
-  b.offsets = cv.take<uint32_t>(n_cells + 1);
-  b.bsum = cv.take<uint32_t>(2 * ((n_cells + 2047) / 2048 + 1));
-  b.sub_s = cv.take<uint8_t>(n_cells);
-  b.sub_base = cv.take<uint32_t>(n_cells + 1);
-  b.sub_count = cv.take<uint32_t>(n_sub);
-  b.sub_off = cv.take<uint32_t>(n_sub + 1);
-  b.bsum2 = cv.take<uint32_t>((n_sub + 2047) / 2048 + 1);
-  b.bounds = cv.take<uint32_t>(n_bounds);
-  Rep* rep_d = cv.take<Rep>(1);
-  BlockTask* tasks_d = cv.take<BlockTask>(n_tasks);
-  int32_t* status_d = cv.take<int32_t>(1);
-  if (cv.used > kScratchBytes) return VK_ERR_CAPACITY;  // cannot happen for n <= kNoAllocMaxN
+  b.U_pos = base + o_upos;
+  b.U_dir = base + o_udir;
+  b.U_id = reinterpret_cast<int32_t*>(base + o_uid);
+  b.U_rank = reinterpret_cast<uint32_t*>(base + o_urank);
+  b.S_pos = base + o_spos;
+  b.S_dir = base + o_sdir;
+  b.S_id = reinterpret_cast<int32_t*>(base + o_sid);
+  b.counts = reinterpret_cast<uint32_t*>(base + o_counts);
+  b.offsets = reinterpret_cast<uint32_t*>(base + o_offsets);
+  b.bsum = reinterpret_cast<uint32_t*>(base + o_bsum);
+  b.sub_s = base + o_subs;
+  b.sub_base = reinterpret_cast<uint32_t*>(base + o_subbase);
+  b.sub_count = reinterpret_cast<uint32_t*>(base + o_subcount);
+  b.sub_off = reinterpret_cast<uint32_t*>(base + o_suboff);
+  b.bsum2 = reinterpret_cast<uint32_t*>(base + o_bsum2);
+  b.bounds = reinterpret_cast<uint32_t*>(base + o_bounds);
+  Rep* rep_d = reinterpret_cast<Rep*>(base + o_rep);
+  BlockTask* tasks_d = reinterpret_cast<BlockTask*>(base + o_tasks);
+  int32_t* status_d = reinterpret_cast<int32_t*>(base + o_status);
 
   Geometry g;
   g.dim = 2;

@@ -778,7 +778,7 @@ __global__ void __launch_bounds__(kBlock) voronoi_step_kernel(
     const Rep* __restrict__ reps, const BlockTask* __restrict__ tasks, const int2* __restrict__ S_pos,
     const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G,
     int2* __restrict__ U_pos, float2* __restrict__ U_dir, int32_t* __restrict__ U_id,
-    uint32_t* __restrict__ counts, double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams Pm,
+    uint32_t* __restrict__ counts, PhiAcc* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams Pm,
     int2* __restrict__ ovf_list, int32_t* __restrict__ ovf_count, int32_t* status) {
   __shared__ PhiShared phs;
   phi_block_begin(phs);
@@ -818,7 +818,7 @@ __global__ void __launch_bounds__(32 * kOvfWarps) voronoi_overflow_kernel(
     const Rep* __restrict__ reps, const int2* __restrict__ S_pos, const float2* __restrict__ S_dir,
     const int32_t* __restrict__ S_id, GridView G, int2* __restrict__ U_pos,
     float2* __restrict__ U_dir, int32_t* __restrict__ U_id,
-    uint32_t* __restrict__ counts, double* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams Pm,
+    uint32_t* __restrict__ counts, PhiAcc* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams Pm,
     const int2* __restrict__ ovf_list, const int32_t* __restrict__ ovf_count, int32_t* status) {
   __shared__ Poly<kSlowCap> poly[kOvfWarps];
   Poly<kSlowCap>& P = poly[threadIdx.x >> 5];
@@ -841,9 +841,9 @@ __global__ void __launch_bounds__(32 * kOvfWarps) voronoi_overflow_kernel(
         const float ni[3] = {nv.x, nv.y, 0.f};
         float nnew[3] = {0.f, 0.f, 0.f};
         voronoi_update(R, Pm, step, s, P, pi, ni, id, S_dir, U_pos, U_dir, U_id, counts, nnew);
-        double* acc = phi_acc + ((size_t)(step % Pm.phi_cap) * (size_t)Pm.n_rep + (size_t)e.y) * 3;
-        atomicAdd(acc + 0, (double)nnew[0]);
-        atomicAdd(acc + 1, (double)nnew[1]);
+        PhiAcc* acc = phi_acc + ((size_t)(step % Pm.phi_cap) * (size_t)Pm.n_rep + (size_t)e.y) * 3;
+        atomicAdd(acc + 0, (PhiAcc)phi_fixed(nnew[0]));
+        atomicAdd(acc + 1, (PhiAcc)phi_fixed(nnew[1]));
       }
     }
     __syncwarp();
@@ -899,7 +899,7 @@ cudaError_t launch_voronoi_step(const Geometry& g, const Buffers& b, const StepP
                                                     b.S_id, G, (int2*)b.U_pos, (float2*)b.U_dir, b.U_id,
                                                     b.counts, b.phi_acc, b.d_step, P, b.ovf_list,
                                                     b.ovf_count, b.d_status);
-  voronoi_overflow_kernel<<<152, 32 * kOvfWarps, 0, st>>>(g.reps, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id,
+  voronoi_overflow_kernel<<<device_sm_count(), 32 * kOvfWarps, 0, st>>>(g.reps, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id,
                                               G, (int2*)b.U_pos, (float2*)b.U_dir, b.U_id,
                                               b.counts, b.phi_acc, b.d_step, P, b.ovf_list, b.ovf_count,
                                               b.d_status);
@@ -909,7 +909,7 @@ cudaError_t launch_voronoi_step(const Geometry& g, const Buffers& b, const StepP
 cudaError_t launch_voronoi_export(const Geometry& g, const Buffers& b, int rep, int n, int pass, int32_t* deg,
                                   const int64_t* out_off, int32_t* out_ids, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  const int nb = std::min((n + 63) / 64, 152 * 8);
+  const int nb = std::min((n + 63) / 64, device_sm_count() * 8);
   voronoi_export_kernel<<<nb, 64, 0, st>>>(g.reps, rep, (const int2*)b.S_pos, b.S_id, grid_view(b), pass, deg,
                                            out_off, out_ids, b.d_status);
   return cudaGetLastError();

@@ -13,6 +13,10 @@ Functions and the passages of arxiv 2103.10239 they follow:
 
 * :func:`knn` -- k nearest neighbors with no cutoff (Sec. "Metric and
   topological flocking models"), brute force over all pairs.
+* :func:`metric` -- all particles within a distance r0 (Sec. "Metric and
+  topological flocking models"), brute force over all pairs.
+* :func:`knn_fov` -- the k nearest particles inside a field of view (same
+  section), brute force over all pairs.
 * :func:`voronoi` -- Voronoi neighbors via the Delaunay triangulation's
   empty-circumcircle definition and the Delaunay/Voronoi duality (Sec.
   "Computational tools: Voronoi neighbor lists").
@@ -75,6 +79,12 @@ def _load():
         lib.orc_knn.restype = ctypes.c_int
         lib.orc_voronoi.argtypes = [ctypes.c_int64, i32p, i64p, i64p, i32p, ctypes.c_int64, i64p]
         lib.orc_voronoi.restype = ctypes.c_int
+        lib.orc_metric.argtypes = [ctypes.c_int, ctypes.c_int64, i32p, i64p, ctypes.c_int64, i64p, i32p,
+                                   ctypes.c_int64, i64p]
+        lib.orc_metric.restype = ctypes.c_int
+        lib.orc_knn_fov.argtypes = [ctypes.c_int64, i32p, ctypes.POINTER(ctypes.c_float), i64p, ctypes.c_int,
+                                    ctypes.c_float, i64p, ctypes.c_int64, i32p, i32p]
+        lib.orc_knn_fov.restype = ctypes.c_int
         lib.orc_delaunay_star_triangles.argtypes = [ctypes.c_int64, i32p, i64p, i64p, i32p,
                                                     ctypes.c_int64, i64p]
         lib.orc_delaunay_star_triangles.restype = ctypes.c_int
@@ -148,6 +158,53 @@ def knn(pos_q: np.ndarray, box_q, k: int, query: Optional[np.ndarray] = None) ->
                      None if q is None else _ptr(q, ctypes.c_int64), nq, _ptr(out, ctypes.c_int32))
     _check(rc, "knn")
     return out
+
+
+def metric(pos_q: np.ndarray, box_q, r0_q: int):
+    """Metric neighbors: every other particle at exact squared minimum-image
+    distance <= r0_q^2 (grid units).  Returns (offsets int64[n+1], ids
+    int32[nnz]), rows sorted by id."""
+    lib = _load()
+    pos = np.ascontiguousarray(pos_q, dtype=np.int32)
+    n, dim = pos.shape
+    box = _box(box_q, dim)
+    off = np.zeros(n + 1, dtype=np.int64)
+    nnz = np.zeros(1, dtype=np.int64)
+    rc = lib.orc_metric(dim, n, _ptr(pos, ctypes.c_int32), _ptr(box, ctypes.c_int64), int(r0_q),
+                        _ptr(off, ctypes.c_int64), None, 0, _ptr(nnz, ctypes.c_int64))
+    _check(rc, "metric (size)")
+    ids = np.zeros(max(1, int(nnz[0])), dtype=np.int32)
+    rc = lib.orc_metric(dim, n, _ptr(pos, ctypes.c_int32), _ptr(box, ctypes.c_int64), int(r0_q),
+                        _ptr(off, ctypes.c_int64), _ptr(ids, ctypes.c_int32), ids.shape[0],
+                        _ptr(nnz, ctypes.c_int64))
+    _check(rc, "metric")
+    return off, ids[: int(nnz[0])]
+
+
+def knn_fov(pos_q: np.ndarray, dir32: np.ndarray, box_q, k: int, fov_cos: float,
+            query: Optional[np.ndarray] = None):
+    """k nearest neighbors inside each particle's field of view (2D): the
+    offset d must satisfy d.nq >= cq |d| with the heading and the cosine of
+    the half-angle rounded to 2^-24.  Returns (ids (nq, k) int32 with -1 past
+    the count, count (nq,) int32)."""
+    lib = _load()
+    pos = np.ascontiguousarray(pos_q, dtype=np.int32)
+    d = np.ascontiguousarray(dir32, dtype=np.float32)
+    n = pos.shape[0]
+    box = _box(box_q, 2)
+    if query is None:
+        q = None
+        nq = n
+    else:
+        q = np.ascontiguousarray(query, dtype=np.int64)
+        nq = q.shape[0]
+    out = np.zeros((nq, k), dtype=np.int32)
+    cnt = np.zeros(nq, dtype=np.int32)
+    rc = lib.orc_knn_fov(n, _ptr(pos, ctypes.c_int32), _ptr(d, ctypes.c_float), _ptr(box, ctypes.c_int64), k,
+                         float(np.float32(fov_cos)), None if q is None else _ptr(q, ctypes.c_int64), nq,
+                         _ptr(out, ctypes.c_int32), _ptr(cnt, ctypes.c_int32))
+    _check(rc, "knn_fov")
+    return out, cnt
 
 
 def voronoi(pos_q: np.ndarray, box_q):

@@ -152,6 +152,105 @@ int orc_knn(int dim, int64_t n, const int32_t* pos, const int64_t* box, int k,
 /* ======================================================================== */
 
 /* orient(a,b,c) = sign of (b-a) x (c-a); |coords| < 2^37 keeps it in i128. */
+/* ------------------------------------------------------------------------
+ * Metric rule (Sec. "Metric and topological flocking models": all pairs
+ * within a distance r0 are neighbors).  Reading: j != i is a neighbor of i
+ * iff the exact squared minimum-image distance D <= r0q^2, r0q being the
+ * radius in grid units.  Rows sorted by id.  Two calls: offsets (and the
+ * count) first with ids == NULL, then the ids.
+ * ------------------------------------------------------------------------ */
+int orc_metric(int dim, int64_t n, const int32_t* pos, const int64_t* box, int64_t r0q, int64_t* offsets,
+               int32_t* ids, int64_t cap, int64_t* nnz) {
+  if (dim < 1 || dim > 3 || n < 1 || r0q < 0 || r0q > ((int64_t)1 << 31)) return ORC_ERR_ARG;
+  const uint64_t r2 = (uint64_t)r0q * (uint64_t)r0q;
+  offsets[0] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t c = 0;
+    for (int64_t j = 0; j < n; ++j)
+      if (j != i && sqdist(dim, pos + i * dim, pos + j * dim, box) <= r2) ++c;
+    offsets[i + 1] = offsets[i] + c;
+  }
+  *nnz = offsets[n];
+  if (!ids) return ORC_OK;
+  if (cap < offsets[n]) return ORC_ERR_ARG;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t w = offsets[i];
+    for (int64_t j = 0; j < n; ++j)
+      if (j != i && sqdist(dim, pos + i * dim, pos + j * dim, box) <= r2) ids[w++] = (int32_t)j;
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------
+ * k nearest neighbors inside a field of view (Sec. "Metric and topological
+ * flocking models": the k nearest neighbors within an angular field of
+ * view).  Reading: j is in i's field of view iff its offset d = r_j - r_i
+ * (minimum image) makes an angle of at most the half-angle with i's heading,
+ * i.e. d.n >= c |d| with c the cosine of the half-angle.  To be decided
+ * exactly, the heading and c are rounded to a fixed point of 2^-24:
+ * nq = rint(n * 2^24), cq = rint(c * 2^24) (round half to even), and the
+ * test is s = d.nq >= cq |d|, compared through squares in 128-bit integers.
+ * Coincident particles (d = 0) are in view, and so is everyone when c <= -1
+ * (a full circle).  Among the particles in view,
+ * the k nearest by (D, id); out[qq*k + s] = -1 past the count found.
+ * ------------------------------------------------------------------------ */
+static int64_t fix24(double v) { return (int64_t)nearbyint(v * 16777216.0); }
+
+static int in_view(int64_t dx, int64_t dy, int64_t nxq, int64_t nyq, int64_t cq) {
+  if (cq <= -((int64_t)1 << 24)) return 1; /* a full circle: every particle is in view */
+  const __int128 sdot = (__int128)dx * nxq + (__int128)dy * nyq;
+  const __int128 D = (__int128)dx * dx + (__int128)dy * dy;
+  const __int128 lhs = sdot * sdot, rhs = (__int128)cq * cq * D;
+  if (cq >= 0) return sdot >= 0 && lhs >= rhs;
+  return sdot >= 0 || lhs <= rhs;
+}
+
+int orc_knn_fov(int64_t n, const int32_t* pos, const float* dir, const int64_t* box, int k, float fov_cos,
+                const int64_t* query, int64_t nq, int32_t* out, int32_t* count) {
+  if (n < 2 || k < 1 || k > n - 1 || !(fov_cos >= -1.0f && fov_cos <= 1.0f)) return ORC_ERR_ARG;
+  if (query == NULL) nq = n;
+  const int64_t cq = fix24((double)fov_cos);
+  int bad = 0;
+#pragma omp parallel
+  {
+    uint64_t* bd = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)k);
+    int32_t* bi = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
+    if (!bd || !bi) {
+#pragma omp atomic write
+      bad = 1;
+    }
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t qq = 0; qq < nq; ++qq) {
+      if (!bd || !bi) continue;
+      int64_t i = query ? query[qq] : qq;
+      const int64_t nxq = fix24((double)dir[2 * i]), nyq = fix24((double)dir[2 * i + 1]);
+      int filled = 0;
+      for (int64_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        const int64_t dx = min_image((int64_t)pos[2 * j] - pos[2 * i], box[0]);
+        const int64_t dy = min_image((int64_t)pos[2 * j + 1] - pos[2 * i + 1], box[1]);
+        if (!in_view(dx, dy, nxq, nyq, cq)) continue;
+        const uint64_t D = (uint64_t)(dx * dx) + (uint64_t)(dy * dy);
+        if (filled == k && D >= bd[k - 1]) continue;
+        int s = filled < k ? filled++ : k - 1;
+        while (s > 0 && bd[s - 1] > D) {
+          bd[s] = bd[s - 1];
+          bi[s] = bi[s - 1];
+          --s;
+        }
+        bd[s] = D;
+        bi[s] = (int32_t)j;
+      }
+      for (int s = 0; s < k; ++s) out[qq * k + s] = s < filled ? bi[s] : -1;
+      count[qq] = filled;
+    }
+    free(bd);
+    free(bi);
+  }
+  return bad ? ORC_ERR_OOM : ORC_OK;
+}
+
 static int orient2(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t cx, int64_t cy) {
   i128 v = (i128)(bx - ax) * (i128)(cy - ay) - (i128)(by - ay) * (i128)(cx - ax);
   return (v > 0) - (v < 0);

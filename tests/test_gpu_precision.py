@@ -1,5 +1,5 @@
 """Precision study (FP32 plain vs FP32 compensated vs FP64 heading sums) on
-the density-2 uniform workload, both rules, after the flock has evolved:
+the density-2 uniform workload (N = 2^20), both rules, after the flock has evolved:
 per-step heading error against the FP64 oracle with teacher forcing, and the
 neighbor lists bit-exact.  Compensated sums and FP64 must stay within
 1e-5 rad per step; plain FP32 sums are reported (they can exceed it when the
@@ -17,7 +17,10 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("rule", ["voronoi", "knn"])
 def test_heading_error_by_sum_mode(rule):
-    w = W.precision_study(rule, n=1 << 18)
+    """At the study's size (N = 2^20, density 2): one teacher-forced check
+    after 30 free steps.  The long runs (10^4 steps, a check every 1000) are
+    tests/precision_study.py."""
+    w = W.precision_study(rule, n=1 << 20)
     rng = np.random.default_rng(3)
     report = {}
     for mode in ("plain", "compensated", "fp64"):

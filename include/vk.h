@@ -74,7 +74,11 @@ typedef enum {
   VK_ERR_STATE = 8       /* call not valid in the current state */
 } vk_status;
 
-typedef enum { VK_RULE_KNN = 0, VK_RULE_VORONOI = 1 } vk_rule;
+/* Neighbor rules (Sec. "Metric and topological flocking models"): the k
+ * nearest particles at any distance (optionally only those inside a field of
+ * view, 2D), the Voronoi neighbors (2D), or every particle within the metric
+ * radius r0 (the original Vicsek rule, 2D and 3D). */
+typedef enum { VK_RULE_KNN = 0, VK_RULE_VORONOI = 1, VK_RULE_METRIC = 2 } vk_rule;
 typedef enum { VK_NOISE_ANGULAR = 0, VK_NOISE_VECTORIAL = 1 } vk_noise;
 typedef enum { VK_SUM_PLAIN = 0, VK_SUM_COMPENSATED = 1, VK_SUM_FP64 = 2 } vk_sum_mode;
 typedef enum { VK_HEADING_DIR = 0, VK_HEADING_THETA = 1 } vk_heading_kind;
@@ -91,7 +95,7 @@ typedef struct {
  * vector in vectorial mode. */
 typedef struct {
   int32_t rule;         /* vk_rule */
-  int32_t k;            /* neighbors for VK_RULE_KNN, 1..32, k <= N-1 */
+  int32_t k;            /* neighbors for VK_RULE_KNN, 1..32, k <= N-1 (unused by the others) */
   float v0;             /* self-propulsion speed (length units per time) */
   float dt;             /* time step */
   float eta;            /* noise strength (per-replica values override in batches) */
@@ -115,6 +119,21 @@ typedef struct {
   int32_t replica_offset; /* noise counter index of the first replica (default 0): replica r
                            draws with index replica_offset + r, so a single-replica sim with
                            replica_offset = r reproduces replica r of a batch exactly */
+  float r0;             /* VK_RULE_METRIC: interaction radius in length units; the exact test is
+                           D <= r0q^2 with r0q = rint(r0 * 2^F) grid units (round half to even,
+                           per replica's F), r0q <= 2^31.  Self is not a neighbor (include_self
+                           adds it).  The heading sum of the metric rule is exact: every
+                           component is rounded to 2^-32 and summed in int64 (order-free, so
+                           bit-identical run to run), then converted to FP64; sum_mode is not
+                           used by this rule. */
+  int32_t fov;          /* VK_RULE_KNN, 2D: 1 = only particles inside the field of view count
+                           (default 0).  j is in view of i iff d.nq >= cq |d| for the minimum-
+                           image offset d = r_j - r_i, with nq = rint(n_i(t) * 2^24) and
+                           cq = rint(fov_cos * 2^24) (round half to even), decided exactly in
+                           integers; d = 0 is in view.  A particle with fewer than k particles
+                           in view aligns with those it has (its list is shorter). */
+  float fov_cos;        /* cosine of the half-angle of the field of view, in [-1, 1]; -1 is the
+                           full circle (the plain rule), 0 the half-plane ahead */
 } vk_params;
 
 /* Fills p with the defaults: kNN, k = 7, v0 = 0.5, dt = 1, eta = 0.3, seed = 1,
@@ -147,7 +166,10 @@ vk_status vk_step(vk_sim* sim, int64_t nsteps);
 /* Neighbor lists of the CURRENT positions of one replica, in id order:
  * offsets (n+1 int64, CSR) and ids (int32).  kNN rule: the k nearest other
  * particles at any distance, not reciprocal (Sec. "Metric and topological
- * flocking models"), row i ordered by (D, id).  Voronoi rule: the particles
+ * flocking models"), row i ordered by (D, id); with a field of view, the k
+ * nearest in view, so a row may be shorter than k.  Metric rule: every other
+ * particle at exact squared distance <= r0q^2 (reciprocal), row i sorted by
+ * id.  Voronoi rule: the particles
  * whose Voronoi cell shares an edge of positive length with i's, i.e. the
  * Delaunay neighbors by the empty-circumcircle property (Sec. "Computational
  * tools: Voronoi neighbor lists"), row i sorted by id.  These are the lists

@@ -94,6 +94,13 @@ cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
 }
 
+// the field of view's half-angle cosine in 2^-24 units (round half to even),
+// or the full circle
+int32_t fov_cq(const vk_params& p) {
+  if (p.rule != VK_RULE_KNN || !p.fov) return kViewAll;
+  return (int32_t)std::nearbyint((double)p.fov_cos * 16777216.0);
+}
+
 StepParams step_params(const vk_sim* s) {
   StepParams P;
   P.k = s->prm.k;
@@ -108,6 +115,7 @@ StepParams step_params(const vk_sim* s) {
   P.knn_search = s->prm.knn_search;
   P.halo_alpha = s->prm.search_halo > 0.f ? s->prm.search_halo : 1.25f;
   P.halo_beta = s->prm.search_halo_step >= 0.f ? s->prm.search_halo_step : 0.f;
+  P.fov_cq = fov_cq(s->prm);
   P.stats = (s->prof && s->prof_counters) ? s->d_stats : nullptr;
   return P;
 }
@@ -255,9 +263,11 @@ vk_status clear_phi(vk_sim* s) {
 
 // kernels of the search+update phase: for 2D kNN the radius-first kernel,
 // the deferred-particle kernel and the walk-list kernel (one kernel with the
-// walk only); one for 3D kNN; the Voronoi kernel and its overflow kernel
+// walk only); one for 3D kNN and for the metric rule; the Voronoi kernel and
+// its overflow kernel
 int search_launches(const vk_sim* s) {
   if (s->prm.rule == VK_RULE_KNN) return (s->dim == 2 && s->prm.knn_search == 0) ? 3 : 1;
+  if (s->prm.rule == VK_RULE_METRIC) return 1;
   return 2;
 }
 
@@ -268,6 +278,7 @@ vk_status enqueue_step(vk_sim* s) {
   if (st) return st;
   if (s->prm.rule == VK_RULE_KNN && s->dim == 2) VK_CUDA(s, launch_knn2_step(s->g, s->b, P, s->stream));
   else if (s->prm.rule == VK_RULE_KNN) VK_CUDA(s, launch_knn_step(s->g, s->b, P, s->stream));
+  else if (s->prm.rule == VK_RULE_METRIC) VK_CUDA(s, launch_metric_step(s->g, s->b, P, s->stream));
   else VK_CUDA(s, launch_voronoi_step(s->g, s->b, P, s->stream));
   const int deferred_launches = (s->prm.rule == VK_RULE_KNN && s->dim == 2 && s->prm.knn_search == 0) ? 2 : 0;
   if ((st = record_end(s, 0, e0, search_launches(s) - deferred_launches))) return st;
@@ -310,7 +321,8 @@ vk_status capture_graph(vk_sim* s, int steps) {
 }
 
 bool valid_params(const vk_params* p, int dim, std::string* why) {
-  if (p->rule != VK_RULE_KNN && p->rule != VK_RULE_VORONOI) return *why = "unknown rule", false;
+  if (p->rule != VK_RULE_KNN && p->rule != VK_RULE_VORONOI && p->rule != VK_RULE_METRIC)
+    return *why = "unknown rule", false;
   if (p->rule == VK_RULE_KNN && (p->k < 1 || p->k > kMaxK)) return *why = "k must be in [1, 32]", false;
   if (p->noise != VK_NOISE_ANGULAR && p->noise != VK_NOISE_VECTORIAL) return *why = "unknown noise", false;
   if (dim == 3 && p->noise != VK_NOISE_VECTORIAL) return *why = "3D needs vectorial noise", false;
@@ -323,6 +335,11 @@ bool valid_params(const vk_params* p, int dim, std::string* why) {
   if (!(p->search_halo >= 0.f) || !std::isfinite(p->search_halo)) return *why = "search_halo must be >= 0", false;
   if (!std::isfinite(p->search_halo_step)) return *why = "search_halo_step must be finite", false;
   if (p->replica_offset < 0) return *why = "replica_offset must be >= 0", false;
+  if (p->rule == VK_RULE_METRIC && !(p->r0 >= 0.f && std::isfinite(p->r0)))
+    return *why = "r0 must be finite and >= 0", false;
+  if (p->fov != 0 && p->fov != 1) return *why = "fov must be 0 or 1", false;
+  if (p->fov && (p->rule != VK_RULE_KNN || dim != 2)) return *why = "a field of view needs the 2D kNN rule", false;
+  if (p->fov && !(p->fov_cos >= -1.f && p->fov_cos <= 1.f)) return *why = "fov_cos must be in [-1, 1]", false;
   return true;
 }
 
@@ -357,6 +374,8 @@ vk_status build_sim(int32_t n_rep, const int64_t* n_r, const int32_t* pos_q, con
     if (n_r[r] < 1) return fail(nullptr, VK_ERR_ARG, "every replica needs at least one particle");
     if (params->rule == VK_RULE_KNN && params->k > n_r[r] - 1)
       return fail(nullptr, VK_ERR_ARG, "k must be smaller than the number of particles");
+    if (params->rule == VK_RULE_METRIC && !(std::nearbyint(std::ldexp((double)params->r0, B.frac_bits)) <= 2147483648.0))
+      return fail(nullptr, VK_ERR_RANGE, "r0 * 2^F must not exceed 2^31 grid units");
     total += n_r[r];
   }
   if (total >= (1ll << 31) - 1) return fail(nullptr, VK_ERR_RANGE, "too many particles (>= 2^31)");
@@ -383,6 +402,9 @@ vk_status build_sim(int32_t n_rep, const int64_t* n_r, const int32_t* pos_q, con
     const float vdt = params->v0 * params->dt;
     R.s = (float)std::ldexp((double)vdt, boxes[r].frac_bits);
     R.replica = (uint32_t)(r + params->replica_offset);
+    R.r0q = params->rule == VK_RULE_METRIC
+                ? (uint32_t)std::nearbyint(std::ldexp((double)params->r0, boxes[r].frac_bits))
+                : 0u;
     for (int first = 0; first < R.n; first += kBlock) s->tasks_h.push_back({r, first});
     p0 += n_r[r];
   }
@@ -481,6 +503,9 @@ void vk_default_params(vk_params* p) {
   p->search_halo = 0.f;
   p->search_halo_step = -1.f;
   p->replica_offset = 0;
+  p->r0 = 1.0f;
+  p->fov = 0;
+  p->fov_cos = -1.0f;
 }
 
 vk_status vk_init(const int32_t* pos_q, const float* heading, int32_t heading_kind, int64_t n,
@@ -547,14 +572,30 @@ vk_status vk_get_neighbors(vk_sim* s, int32_t replica, int64_t* offsets, int32_t
     cudaFree(out_d);
     if (e != cudaSuccess) return cuda_fail(s, e, "knn export");
     for (int64_t i = 0; i <= n; ++i) off_h[i] = i * k;
+    if (s->prm.fov) {
+      // rows with fewer than k particles in view end in -1: drop those entries
+      int64_t w = 0;
+      for (int64_t i = 0; i < n; ++i) {
+        off_h[i] = w;
+        for (int j = 0; j < k; ++j)
+          if (ids_h[(size_t)(i * k + j)] >= 0) ids_h[(size_t)w++] = ids_h[(size_t)(i * k + j)];
+      }
+      off_h[n] = w;
+      ids_h.resize((size_t)w);
+    }
   } else {
     // pass 0: degrees by id; pass 1: ids at the CSR offsets
+    const bool metric = s->prm.rule == VK_RULE_METRIC;
+    auto exporter = [&](int pass, int32_t* deg, const int64_t* off, int32_t* ids_out) {
+      return metric ? launch_metric_export(s->g, s->b, replica, (int)n, pass, deg, off, ids_out, s->stream)
+                    : launch_voronoi_export(s->g, s->b, replica, (int)n, pass, deg, off, ids_out, s->stream);
+    };
     int32_t* deg_d = nullptr;
     int64_t* off_d = nullptr;
     int32_t* ids_d = nullptr;
     VK_CUDA(s, dalloc(&deg_d, n));
     std::vector<int32_t> deg(n);
-    cudaError_t e = launch_voronoi_export(s->g, s->b, replica, (int)n, 0, deg_d, nullptr, nullptr, s->stream);
+    cudaError_t e = exporter(0, deg_d, nullptr, nullptr);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(deg.data(), deg_d, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -567,14 +608,14 @@ vk_status vk_get_neighbors(vk_sim* s, int32_t replica, int64_t* offsets, int32_t
     if (e == cudaSuccess) e = dalloc(&ids_d, std::max<int64_t>(1, off_h[n]));
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(off_d, off_h.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess) e = launch_voronoi_export(s->g, s->b, replica, (int)n, 1, deg_d, off_d, ids_d, s->stream);
+    if (e == cudaSuccess) e = exporter(1, deg_d, off_d, ids_d);
     if (e == cudaSuccess && off_h[n] > 0)
       e = cudaMemcpyAsync(ids_h.data(), ids_d, sizeof(int32_t) * off_h[n], cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     cudaFree(deg_d);
     cudaFree(off_d);
     cudaFree(ids_d);
-    if (e != cudaSuccess) return cuda_fail(s, e, "voronoi export");
+    if (e != cudaSuccess) return cuda_fail(s, e, metric ? "metric export" : "voronoi export");
   }
   if ((st = record_end(s, 4, e0, 1))) return st;
   if ((st = read_status(s))) return st;

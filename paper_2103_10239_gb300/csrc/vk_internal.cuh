@@ -40,12 +40,15 @@ struct Rep {
   uint32_t replica;
   int32_t bnd[3];  // offset of the axis' cell-boundary table in the bounds array
   float inv_w[3];  // nc / L (estimate of the cell index; corrected exactly)
+  uint32_t r0q;    // metric rule: interaction radius in grid units, rint(r0 * 2^F)
 };
 
 struct BlockTask {
   int32_t rep;
   int32_t first;  // replica-local index of the block's first particle
 };
+
+constexpr int32_t kViewAll = INT_MIN;  // fov_cq of the full circle (the plain kNN rule)
 
 struct StepParams {
   int32_t k;
@@ -62,6 +65,9 @@ struct StepParams {
   // radius-first search square: halo_alpha * (the particle's k-th distance at
   // the previous step) + halo_beta * (grid step per unit heading)
   float halo_alpha, halo_beta;
+  // 2D kNN field of view: the cosine of the half-angle in 2^-24 units, or
+  // INT_MIN for the full circle (the plain rule)
+  int32_t fov_cq;
   // tracing only (NULL = off): [candidates, runs or squares, max candidates,
   // particles, particles whose own coarse cell is split (walk) or that fell
   // back to the walk (radius first), then radius first only: squares, runs,
@@ -404,14 +410,15 @@ struct HeadSum {
 // --------------------------------------------------------------------------
 // Eq. (2) alignment + noise and Eq. (1) advection for one particle.
 // --------------------------------------------------------------------------
+// sum_mode selects which of H's sums is the total (2: H.d, FP64).
 template <int DIM>
-__device__ __forceinline__ void align_advect(const Rep& R, const StepParams& P, uint32_t step,
-                                             int32_t id, const float* ni, const HeadSum<DIM>& H,
-                                             int m, const int32_t* pi, int32_t* pout, float* nout) {
+__device__ __forceinline__ void align_advect_mode(const Rep& R, const StepParams& P, int sum_mode, uint32_t step,
+                                                  int32_t id, const float* ni, const HeadSum<DIM>& H, int m,
+                                                  const int32_t* pi, int32_t* pout, float* nout) {
   const uint4 w = philox4x32_10(make_uint4((uint32_t)id, step, R.replica, 0u),
                                 make_uint2(P.seed_lo, P.seed_hi));
   const float u = unit24(w.x);
-  if (P.sum_mode == 2) {
+  if (sum_mode == 2) {
     double S[DIM];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) S[a] = H.d[a];
@@ -450,7 +457,7 @@ __device__ __forceinline__ void align_advect(const Rep& R, const StepParams& P, 
   } else {
     float S[DIM];
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) S[a] = (P.sum_mode == 1) ? __fadd_rn(H.s[a], H.c[a]) : H.s[a];
+    for (int a = 0; a < DIM; ++a) S[a] = (sum_mode == 1) ? __fadd_rn(H.s[a], H.c[a]) : H.s[a];
     if (P.noise == 0) {
       float th = (S[0] == 0.f && S[1] == 0.f) ? atan2f(ni[1], ni[0]) : atan2f(S[1], S[0]);
       th = th + R.eta * (u - 0.5f);
@@ -487,6 +494,13 @@ __device__ __forceinline__ void align_advect(const Rep& R, const StepParams& P, 
   const float* h = P.advect_new ? nout : ni;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) pout[a] = wrap_add(pi[a], grid_step(R.s, h[a]), R.L[a]);
+}
+
+template <int DIM>
+__device__ __forceinline__ void align_advect(const Rep& R, const StepParams& P, uint32_t step,
+                                             int32_t id, const float* ni, const HeadSum<DIM>& H,
+                                             int m, const int32_t* pi, int32_t* pout, float* nout) {
+  align_advect_mode<DIM>(R, P, P.sum_mode, step, id, ni, H, m, pi, pout, nout);
 }
 
 // --------------------------------------------------------------------------
@@ -673,6 +687,12 @@ cudaError_t launch_knn2_export(const Geometry& g, const Buffers& b, int k, int r
                                cudaStream_t st, const StepParams& P);
 // one-time kernel attributes (shared memory of the radius-first search)
 cudaError_t prepare_knn2();
+
+// vk_metric.cu (metric rule, 2D and 3D)
+cudaError_t launch_metric_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st);
+// pass 0: deg[id] = neighbor count; pass 1: the ids of row id at out_off[id], sorted by id
+cudaError_t launch_metric_export(const Geometry& g, const Buffers& b, int rep, int n, int pass, int32_t* deg,
+                                 const int64_t* out_off, int32_t* out_ids, cudaStream_t st);
 
 // vk_voronoi.cu
 cudaError_t launch_voronoi_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st);

@@ -14,7 +14,7 @@
 #include <algorithm>
 #include <climits>
 
-#include "vk_internal.cuh"
+#include "vk_box2d.cuh"
 
 // resident 256-thread blocks per SM the step kernels are compiled for
 // (register budget): the per-particle walk, and the radius-first search
@@ -23,10 +23,6 @@
 #endif
 #ifndef VK_KNN2_BOX_BLOCKS
 #define VK_KNN2_BOX_BLOCKS 3
-#endif
-// slot runs one square of the radius-first search may list
-#ifndef VK_KNN2_BOX_RUNS
-#define VK_KNN2_BOX_RUNS 16
 #endif
 
 namespace vk {
@@ -80,15 +76,6 @@ __device__ __forceinline__ void top_insert(Top<KC>& T, uint64_t D, int32_t q, co
   }
 }
 
-struct Ctx {
-  int64_t self;
-  uint32_t px, py;
-  uint32_t Lx, Ly;
-  int32_t hix, lox, hiy, loy;  // minimum image: d > hi -> d - L, d <= lo -> d + L
-  uint32_t n_cand, n_runs;
-  bool split;  // the particle's own coarse cell is split (tracing)
-};
-
 template <int KC>
 __device__ __forceinline__ void scan_run(Ctx& C, const int2* __restrict__ pos, const int32_t* __restrict__ ids,
                                          uint32_t qb, uint32_t qe, Top<KC>& T) {
@@ -103,7 +90,7 @@ __device__ __forceinline__ void scan_run(Ctx& C, const int2* __restrict__ pos, c
     if (dy > C.hiy) dy = (int32_t)((uint32_t)dy - C.Ly);
     else if (dy <= C.loy) dy = (int32_t)((uint32_t)dy + C.Ly);
     const uint64_t D = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy);
-    if (D <= T.d[KC - 1] && (int64_t)q != C.self) {
+    if (D <= T.d[KC - 1] && (int64_t)q != C.self && in_view(C.view, dx, dy, D)) {
       // an exact tie with the current k-th best is decided by the ids
       if (D < T.d[KC - 1] || (T.slot[KC - 1] >= 0 && __ldg(ids + q) < __ldg(ids + T.slot[KC - 1])))
         top_insert<KC>(T, D, (int32_t)q, ids);
@@ -506,21 +493,6 @@ __device__ __forceinline__ void knn2_search(Ctx& C, const Rep& R, const uint32_t
   }
 }
 
-__device__ __forceinline__ void init_ctx(Ctx& C, const Rep& R, int64_t self, int2 p) {
-  C.self = self;
-  C.px = (uint32_t)p.x;
-  C.py = (uint32_t)p.y;
-  C.Lx = R.L[0];
-  C.Ly = R.L[1];
-  C.hix = (int32_t)(R.L[0] / 2);
-  C.lox = -(int32_t)((R.L[0] + 1) / 2);
-  C.hiy = (int32_t)(R.L[1] / 2);
-  C.loy = -(int32_t)((R.L[1] + 1) / 2);
-  C.n_cand = 0;
-  C.n_runs = 0;
-  C.split = false;
-}
-
 // the general update (vectorial noise, FP64 sums), kept out of line
 __device__ __noinline__ void align_advect_general(const Rep& R, const StepParams& P, uint32_t step, int32_t id,
                                                   const float* ni, const HeadSum<2>& H, int m, const int32_t* pi,
@@ -536,22 +508,24 @@ __device__ __forceinline__ void knn2_update(const Rep& R, const StepParams& P, i
                                             const uint32_t* __restrict__ bounds, const float2* __restrict__ S_dir,
                                             int2* __restrict__ U_pos, float2* __restrict__ U_dir,
                                             int32_t* __restrict__ U_id, uint32_t* __restrict__ counts, float* nnew) {
-  // Eq. (2): neighbor headings in (D, id) order
+  // Eq. (2): neighbor headings in (D, id) order; with a field of view the
+  // list may be shorter than k (unfilled entries have slot -1)
   HeadSum<2> H;
   H.init();
   const float ni[3] = {nv.x, nv.y, 0.f};
+  int m = P.include_self ? 1 : 0;
   if (P.include_self) H.add(ni, P.sum_mode);
 #pragma unroll
   for (int j = 0; j < KC; ++j) {
-    if (j >= KC - P.k) {
+    if (j >= KC - P.k && T.slot[j] >= 0) {
       const float2 d = __ldg(S_dir + T.slot[j]);
       const float v[2] = {d.x, d.y};
       H.add(v, P.sum_mode);
+      ++m;
     }
   }
   const int32_t pi[3] = {p.x, p.y, 0};
   int32_t pout[3] = {0, 0, 0};
-  const int m = P.k + (P.include_self ? 1 : 0);
   if (P.noise == 0 && P.sum_mode != 2) {
     // angular noise, FP32 sums (the default) inline
     const uint4 w = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)step, R.replica, 0u),
@@ -611,6 +585,7 @@ __global__ void __launch_bounds__(kBlock, VK_KNN2_MIN_BLOCKS) knn2_step_kernel(
     const float2 nv = S_dir[s];
     const int32_t id = S_id[s];
     init_ctx(C, R, s, p);
+    if (P.fov_cq != kViewAll) C.view = make_view(nv, P.fov_cq);
     Top<KC> T;
     top_init<KC>(T, P.k);
     knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T, P.k);
@@ -620,25 +595,34 @@ __global__ void __launch_bounds__(kBlock, VK_KNN2_MIN_BLOCKS) knn2_step_kernel(
   phi_block_end<2>(phs, nnew, phi_acc + ((size_t)(step % P.phi_cap) * (size_t)P.n_rep + (size_t)t.rep) * 3);
 }
 
+// row id of the export table: the ids of T in (D, id) order, -1 past the
+// count found (a field of view may hold fewer than k)
+template <int KC>
+__device__ __forceinline__ void write_row(const Top<KC>& T, const int32_t* __restrict__ S_id, int32_t id, int k,
+                                          int32_t* __restrict__ out) {
+#pragma unroll
+  for (int j = 0; j < KC; ++j)
+    if (j >= KC - k) out[(int64_t)id * k + (j - (KC - k))] = T.slot[j] >= 0 ? __ldg(S_id + T.slot[j]) : -1;
+}
+
 template <int KC>
 __global__ void __launch_bounds__(kBlock, 2) knn2_export_kernel(const Rep* __restrict__ reps, int rep,
                                                                 const uint32_t* __restrict__ bounds,
                                                                 const int2* __restrict__ S_pos,
+                                                                const float2* __restrict__ S_dir,
                                                                 const int32_t* __restrict__ S_id, GridView G, int k,
-                                                                int32_t* __restrict__ out) {
+                                                                int32_t cq, int32_t* __restrict__ out) {
   const Rep R = reps[rep];
   const int li = blockIdx.x * kBlock + (int)threadIdx.x;
   if (li >= R.n) return;
   const int64_t s = R.p0 + li;
   Ctx C;
   init_ctx(C, R, s, S_pos[s]);
+  if (cq != kViewAll) C.view = make_view(S_dir[s], cq);
   Top<KC> T;
   top_init<KC>(T, k);
   knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T, k);
-  const int32_t id = S_id[s];
-#pragma unroll
-  for (int j = 0; j < KC; ++j)
-    if (j >= KC - k) out[(int64_t)id * k + (j - (KC - k))] = __ldg(S_id + T.slot[j]);
+  write_row<KC>(T, S_id, S_id[s], k, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -670,44 +654,24 @@ struct BoxHits {
   uint2 run[kRuns][kBlock];             // (first slot, length << 4 | image shift codes)
 };
 
-// tracing counters of the radius-first search
-struct BoxCount {
-  uint32_t cand = 0;   // candidates examined
-  uint32_t tries = 0;  // squares scanned
-  uint32_t runs = 0;   // contiguous slot runs read
-  uint32_t hits = 0;   // hits merged
-  uint32_t cells = 0;  // coarse cells visited
-  uint32_t why = 0;    // fallback reason: 0 none, 1 square too wide (or too many runs), 2 too few hits, 3 tie
-};
-
-// unwrapped coarse-cell index of an unwrapped coordinate x, -L <= x < 2L
-__device__ __forceinline__ int box_ucell(int64_t x, int n, const uint32_t* __restrict__ bnd, float inv_w, int64_t L) {
-  if (x < 0) return cell_of_tab((uint32_t)(x + L), n, bnd, inv_w) - n;
-  if (x >= L) return cell_of_tab((uint32_t)(x - L), n, bnd, inv_w) + n;
-  return cell_of_tab((uint32_t)x, n, bnd, inv_w);
-}
-
-__device__ __forceinline__ uint64_t box_dist2(const Ctx& C, int2 pj) {
-  int32_t dx = (int32_t)((uint32_t)pj.x - C.px);
-  int32_t dy = (int32_t)((uint32_t)pj.y - C.py);
-  if (dx > C.hix) dx = (int32_t)((uint32_t)dx - C.Lx);
-  else if (dx <= C.lox) dx = (int32_t)((uint32_t)dx + C.Lx);
-  if (dy > C.hiy) dy = (int32_t)((uint32_t)dy - C.Ly);
-  else if (dy <= C.loy) dy = (int32_t)((uint32_t)dy + C.Ly);
-  return (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy);
-}
-
-// Merge the thread's hits into T by a branch-free insertion on D.  Sets
-// *tie if two candidates at the same distance met (their order, or which of
-// them is kept, needs the ids: the caller falls back to the walk).
+// Merge the thread's hits into T by a branch-free insertion on D and return
+// how many of them count: the particle itself is skipped, and so is a hit
+// outside the field of view (the view test runs here, per hit, not per
+// candidate in the scan).  Sets *tie if two counted candidates at the same
+// distance met (their order, or which of them is kept, needs the ids: the
+// caller falls back to the walk).
 template <int KC>
-__device__ __forceinline__ void box_merge(const BoxHits<KC>& H, int cnt, const Ctx& C, const int2* __restrict__ pos,
-                                          Top<KC>& T, bool* tie) {
+__device__ __forceinline__ int box_merge(const BoxHits<KC>& H, int cnt, const Ctx& C, const int2* __restrict__ pos,
+                                         Top<KC>& T, bool* tie) {
   bool t = false;
+  int got = 0;
   for (int b = 0; b < cnt; ++b) {
     const int32_t q = H.slot[b][threadIdx.x];
     if ((int64_t)q == C.self) continue;  // the particle is a hit of its own square
-    const uint64_t D = box_dist2(C, __ldg(pos + q));
+    int32_t dx, dy;
+    const uint64_t D = box_offset(C, __ldg(pos + q), dx, dy);
+    if (!in_view(C.view, dx, dy, D)) continue;
+    ++got;
     t |= D == T.d[KC - 1];
     if (D < T.d[KC - 1]) {
       bool lt_hi = true;
@@ -728,135 +692,55 @@ __device__ __forceinline__ void box_merge(const BoxHits<KC>& H, int cnt, const C
     }
   }
   *tie = *tie || t;
+  return got;
 }
 
+// kNN visitor of the square walk: candidates with D <= tau go to the hit
+// list, which is merged into T when nearly full (tau then shrinks to T's
+// k-th distance) and by the caller at the end.
+template <int KC>
+struct KnnVisit {
+  BoxHits<KC>& H;
+  const Ctx& C;
+  const int2* __restrict__ pos;
+  Top<KC>& T;
+  bool* tie;
+  uint64_t tau;
+  int cnt, got;
+  __device__ __forceinline__ void group(uint32_t q, uint32_t n, const int2* pj, uint32_t ox, uint32_t oy) {
+    // branch-free append: every candidate is written at the next free slot,
+    // and the slot advances only for a hit
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      const int32_t dx = (int32_t)((uint32_t)pj[u].x - ox), dy = (int32_t)((uint32_t)pj[u].y - oy);
+      const uint64_t D = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy);
+      const bool hit = (uint32_t)u < n && D <= tau;
+      H.slot[cnt][threadIdx.x] = (int32_t)(q + (uint32_t)u);
+      cnt += hit ? 1 : 0;
+    }
+    if (cnt > BoxHits<KC>::kCap - kGroup) {  // rare: a nearly full buffer is merged on the spot
+      got += box_merge<KC>(H, cnt, C, pos, T, tie);
+      cnt = 0;
+      if (T.d[KC - 1] < tau) tau = T.d[KC - 1];
+    }
+  }
+};
+
 // Scan the square [p - a, p + a] into T (initialised by the caller): every
-// slot with D <= tau = (a+1)^2 - 1 is a hit (the particle itself too; the
-// merge skips it).  The square's slot runs (the sub-cell rows of the coarse
-// cells it meets) are listed, each with the periodic image its cell lies in,
-// up to kRuns at a time; one flat loop walks each batch, so that threads of
-// a warp whose squares split into different numbers of runs still scan
-// candidates together.  Hits are buffered and merged into T at the end (and,
-// rarely, when the buffer fills, after which tau shrinks to T's k-th
-// distance).  Returns the number of hits (>= k exactly when T is full), or
-// -1 when the square is too wide for the minimum image or meets a coarse
-// cell through two periodic images.
+// slot with D <= tau = (a+1)^2 - 1 is a hit.  Nothing outside the square is
+// that close.  Hits are buffered and merged into T at the end (and, rarely,
+// when the buffer fills, after which tau shrinks to T's k-th distance).
+// Returns the number of hits that count (other particles, in view), >= k
+// exactly when T is full, or -1 when the square is too wide for the minimum
+// image or meets a coarse cell through two periodic images.
 template <int KC>
 __device__ __forceinline__ int box_scan(BoxHits<KC>& H, const Rep& R, const uint32_t* __restrict__ bounds,
                                         const GridView& G, const int2* __restrict__ pos, const Ctx& C, int64_t a,
                                         Top<KC>& T, bool* tie, BoxCount& bc) {
-  const int64_t Lx = C.Lx, Ly = C.Ly;
-  if (2 * (2 * a + 1) >= Lx || 2 * (2 * a + 1) >= Ly) return -1;
-  uint64_t tau = (uint64_t)(a + 1) * (uint64_t)(a + 1) - 1;
-  const int nx = R.nc[0], ny = R.nc[1];
-  const uint32_t* bx = bounds + R.bnd[0];
-  const uint32_t* by = bounds + R.bnd[1];
-  const int64_t qx0 = (int64_t)C.px - a, qx1 = (int64_t)C.px + a;
-  const int64_t qy0 = (int64_t)C.py - a, qy1 = (int64_t)C.py + a;
-  const int ucx0 = box_ucell(qx0, nx, bx, R.inv_w[0], Lx), ucx1 = box_ucell(qx1, nx, bx, R.inv_w[0], Lx);
-  const int ucy0 = box_ucell(qy0, ny, by, R.inv_w[1], Ly), ucy1 = box_ucell(qy1, ny, by, R.inv_w[1], Ly);
-  if (ucx1 - ucx0 + 1 > nx || ucy1 - ucy0 + 1 > ny) return -1;
-  bc.tries += 1;
-  // enumeration cursor over (coarse cell, row of sub-cells): runs are listed
-  // kRuns at a time, each batch is scanned, then listing resumes
-  int ucx = ucx0, ucy = ucy0;
-  int row = 0, row_end = -1;  // rows of the current cell still to list
-  int64_t gc = 0;
-  uint32_t sb0 = 0, code = 0;
-  int s = 1, sx0 = 0, sx1 = 0;
-  bool split = false, listed_all = false;
-  int cnt = 0, merged = 0;
-  while (!listed_all) {
-    int nrun = 0;
-    while (nrun < BoxHits<KC>::kRuns) {
-      if (row > row_end) {  // next coarse cell
-        if (ucx > ucx1) {
-          ucx = ucx0;
-          ++ucy;
-        }
-        if (ucy > ucy1) {
-          listed_all = true;
-          break;
-        }
-        const int cy = ucy < 0 ? ucy + ny : (ucy >= ny ? ucy - ny : ucy);
-        const int cx = ucx < 0 ? ucx + nx : (ucx >= nx ? ucx - nx : ucx);
-        // shift code per axis: 0 same image, 1 the image at -L, 2 at +L
-        code = (ucx < 0 ? 1u : (ucx >= nx ? 2u : 0u)) << 2 | (ucy < 0 ? 1u : (ucy >= ny ? 2u : 0u));
-        gc = R.c0 + (int64_t)cy * nx + cx;
-        sb0 = __ldg(G.sub_base + gc);
-        split = __ldg(G.sub_base + gc + 1) - sb0 > 1;
-        bc.cells += 1;
-        row = 0;
-        row_end = 0;
-        if (split) {
-          const int64_t y0c = cell_lo_tab(ucy, ny, by, Ly);
-          const int64_t wy = cell_lo_tab(ucy + 1, ny, by, Ly) - y0c;
-          const int64_t x0c = cell_lo_tab(ucx, nx, bx, Lx);
-          const int64_t wx = cell_lo_tab(ucx + 1, nx, bx, Lx) - x0c;
-          s = __ldg(G.sub_s + gc);
-          sx0 = sub_idx(max(qx0 - x0c, (int64_t)0), wx, s);
-          sx1 = sub_idx(min(qx1 - x0c, wx - 1), wx, s);
-          row = sub_idx(max(qy0 - y0c, (int64_t)0), wy, s);
-          row_end = sub_idx(min(qy1 - y0c, wy - 1), wy, s);
-        }
-        ++ucx;
-      }
-      uint32_t qb, qe;
-      if (split) {
-        const uint32_t rb = sb0 + (uint32_t)row * (uint32_t)s;
-        qb = __ldg(G.sub_off + rb + sx0);
-        qe = __ldg(G.sub_off + rb + sx1 + 1);
-      } else {
-        qb = __ldg(G.off + gc);
-        qe = __ldg(G.off + gc + 1);
-      }
-      ++row;
-      if (qe > qb) H.run[nrun++][threadIdx.x] = make_uint2(qb, (qe - qb) << 4 | code);
-    }
-    bc.runs += (uint32_t)nrun;
-    // one flat loop over the listed runs; candidates go four at a time (the
-    // loads of a group are independent, so they are in flight together) and
-    // a group never crosses a run
-    constexpr int kGroup = 4;
-    int r = -1;
-    uint32_t q = 0, qe = 0, ox = 0, oy = 0;
-    for (;;) {
-      if (q == qe) {
-        if (++r == nrun) break;
-        const uint2 e = H.run[r][threadIdx.x];
-        q = e.x;
-        qe = e.x + (e.y >> 4);
-        // reference shifted into the run's periodic image: dx = x_j - ox exactly
-        const uint32_t cxd = (e.y >> 2) & 3u, cyd = e.y & 3u;
-        ox = C.px + (cxd == 1u ? (uint32_t)C.Lx : 0u) - (cxd == 2u ? (uint32_t)C.Lx : 0u);
-        oy = C.py + (cyd == 1u ? (uint32_t)C.Ly : 0u) - (cyd == 2u ? (uint32_t)C.Ly : 0u);
-        bc.cand += qe - q;
-      }
-      const uint32_t n = min(qe - q, (uint32_t)kGroup);
-      int2 pj[kGroup];
-#pragma unroll
-      for (int u = 0; u < kGroup; ++u) pj[u] = __ldg(pos + q + min((uint32_t)u, n - 1));
-      // branch-free append: every candidate is written at the next free slot,
-      // and the slot advances only for a hit
-#pragma unroll
-      for (int u = 0; u < kGroup; ++u) {
-        const int32_t dx = (int32_t)((uint32_t)pj[u].x - ox), dy = (int32_t)((uint32_t)pj[u].y - oy);
-        const uint64_t D = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy);
-        const bool hit = (uint32_t)u < n && D <= tau;
-        H.slot[cnt][threadIdx.x] = (int32_t)(q + (uint32_t)u);
-        cnt += hit ? 1 : 0;
-      }
-      q += n;
-      if (cnt > BoxHits<KC>::kCap - kGroup) {  // rare: a nearly full buffer is merged on the spot
-        box_merge<KC>(H, cnt, C, pos, T, tie);
-        merged += cnt;
-        cnt = 0;
-        if (T.d[KC - 1] < tau) tau = T.d[KC - 1];
-      }
-    }
-  }
-  box_merge<KC>(H, cnt, C, pos, T, tie);  // after the loop, where the threads have reconverged
-  return merged + cnt - 1;                // the particle itself was a hit
+  KnnVisit<KC> v{H, C, pos, T, tie, (uint64_t)(a + 1) * (uint64_t)(a + 1) - 1, 0, 0};
+  if (!box_walk(H, R, bounds, G, pos, C, a, bc, v)) return -1;
+  // after the loop, where the threads have reconverged
+  return v.got + box_merge<KC>(H, v.cnt, C, pos, T, tie);
 }
 
 // search radius without a hint: a multiple of the k-th distance expected
@@ -965,6 +849,7 @@ __global__ void __launch_bounds__(kBlock, VK_KNN2_BOX_BLOCKS) knn2_box_step_kern
     const float hint = S_hint[s];
     Ctx C;
     init_ctx(C, R, s, p);
+    if (P.fov_cq != kViewAll) C.view = make_view(S_dir[s], P.fov_cq);
     Top<KC> T;
     const float r =
         hint > 0.f ? P.halo_alpha * hint + P.halo_beta * fabsf(R.s) : box_radius_estimate(R, bounds, G, p, P.k);
@@ -1014,6 +899,7 @@ __global__ void __launch_bounds__(kBlock, VK_KNN2_BOX_BLOCKS) knn2_deferred_kern
     const int2 p = S_pos[s];
     Ctx C;
     init_ctx(C, R, s, p);
+    if (P.fov_cq != kViewAll) C.view = make_view(S_dir[s], P.fov_cq);
     Top<KC> T;
     const float r = U_hint[s];
     float r_next = -1.f;
@@ -1061,6 +947,7 @@ __global__ void __launch_bounds__(kBlock, 2) knn2_walk_list_kernel(
       const int2 p = S_pos[s];
       Ctx C;
       init_ctx(C, R, s, p);
+      if (P.fov_cq != kViewAll) C.view = make_view(S_dir[s], P.fov_cq);
       Top<KC> T;
       top_init<KC>(T, P.k);
       knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T, P.k);
@@ -1081,8 +968,9 @@ __global__ void __launch_bounds__(kBlock, 2) knn2_walk_list_kernel(
 template <int KC>
 __global__ void __launch_bounds__(kBlock, 3) knn2_box_export_kernel(
     const Rep* __restrict__ reps, int rep, const uint32_t* __restrict__ bounds, const int2* __restrict__ S_pos,
-    const int32_t* __restrict__ S_id, const float* __restrict__ S_hint, GridView G, int k, float alpha, float beta,
-    int32_t* __restrict__ out, int2* __restrict__ walk_list, int32_t* __restrict__ walk_count) {
+    const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, const float* __restrict__ S_hint, GridView G,
+    int k, int32_t cq, float alpha, float beta, int32_t* __restrict__ out, int2* __restrict__ walk_list,
+    int32_t* __restrict__ walk_count) {
   extern __shared__ __align__(16) unsigned char box_smem[];
   BoxHits<KC>& H = *reinterpret_cast<BoxHits<KC>*>(box_smem);
   const Rep R = reps[rep];
@@ -1092,6 +980,7 @@ __global__ void __launch_bounds__(kBlock, 3) knn2_box_export_kernel(
   const int2 p = S_pos[s];
   Ctx C;
   init_ctx(C, R, s, p);
+  if (cq != kViewAll) C.view = make_view(S_dir[s], cq);
   Top<KC> T;
   BoxCount bc;
   const float hint = S_hint ? S_hint[s] : 0.f;
@@ -1101,18 +990,15 @@ __global__ void __launch_bounds__(kBlock, 3) knn2_box_export_kernel(
     walk_list[atomicAdd(walk_count, 1)] = make_int2((int)s, rep);
     return;
   }
-  const int32_t id = S_id[s];
-#pragma unroll
-  for (int j = 0; j < KC; ++j)
-    if (j >= KC - k) out[(int64_t)id * k + (j - (KC - k))] = __ldg(S_id + T.slot[j]);
+  write_row<KC>(T, S_id, S_id[s], k, out);
 }
 
 // the per-particle walk for the listed particles of an export
 template <int KC>
 __global__ void __launch_bounds__(kBlock, 2) knn2_walk_export_list_kernel(
     const Rep* __restrict__ reps, const uint32_t* __restrict__ bounds, const int2* __restrict__ S_pos,
-    const int32_t* __restrict__ S_id, GridView G, int k, int32_t* __restrict__ out,
-    const int2* __restrict__ walk_list, const int32_t* __restrict__ walk_count) {
+    const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G, int k, int32_t cq,
+    int32_t* __restrict__ out, const int2* __restrict__ walk_list, const int32_t* __restrict__ walk_count) {
   const int total = *walk_count;
   for (int i = blockIdx.x * kBlock + (int)threadIdx.x; i < total; i += gridDim.x * kBlock) {
     const int2 e = walk_list[i];
@@ -1120,13 +1006,11 @@ __global__ void __launch_bounds__(kBlock, 2) knn2_walk_export_list_kernel(
     const Rep R = reps[e.y];
     Ctx C;
     init_ctx(C, R, s, S_pos[s]);
+    if (cq != kViewAll) C.view = make_view(S_dir[s], cq);
     Top<KC> T;
     top_init<KC>(T, k);
     knn2_search<KC>(C, R, bounds, G, S_pos, S_id, T, k);
-    const int32_t id = S_id[s];
-#pragma unroll
-    for (int j = 0; j < KC; ++j)
-      if (j >= KC - k) out[(int64_t)id * k + (j - (KC - k))] = __ldg(S_id + T.slot[j]);
+    write_row<KC>(T, S_id, S_id[s], k, out);
   }
 }
 
@@ -1194,17 +1078,17 @@ cudaError_t export2(const Geometry& g, const Buffers& b, int k, int rep, int n, 
   const int nb = (n + kBlock - 1) / kBlock;
   if (nb == 0) return cudaSuccess;
   if (P.knn_search == 1 || !b.S_hint) {
-    knn2_export_kernel<KC><<<nb, kBlock, 0, st>>>(g.reps, rep, b.bounds, (const int2*)b.S_pos, b.S_id, view_of(b),
-                                                  k, out);
+    knn2_export_kernel<KC><<<nb, kBlock, 0, st>>>(g.reps, rep, b.bounds, (const int2*)b.S_pos,
+                                                  (const float2*)b.S_dir, b.S_id, view_of(b), k, P.fov_cq, out);
   } else {
     cudaError_t e = cudaMemsetAsync(b.ovf_count, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     knn2_box_export_kernel<KC><<<nb, kBlock, box_smem_bytes<KC>(), st>>>(
-        g.reps, rep, b.bounds, (const int2*)b.S_pos, b.S_id, b.S_hint, view_of(b), k, P.halo_alpha, P.halo_beta,
-        out, b.ovf_list, b.ovf_count);
-    knn2_walk_export_list_kernel<KC><<<walk_list_blocks(g), kBlock, 0, st>>>(g.reps, b.bounds, (const int2*)b.S_pos,
-                                                                         b.S_id, view_of(b), k, out, b.ovf_list,
-                                                                         b.ovf_count);
+        g.reps, rep, b.bounds, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id, b.S_hint, view_of(b), k,
+        P.fov_cq, P.halo_alpha, P.halo_beta, out, b.ovf_list, b.ovf_count);
+    knn2_walk_export_list_kernel<KC><<<walk_list_blocks(g), kBlock, 0, st>>>(
+        g.reps, b.bounds, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id, view_of(b), k, P.fov_cq, out,
+        b.ovf_list, b.ovf_count);
     // leave the list empty for the next step
     e = cudaMemsetAsync(b.ovf_count, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;

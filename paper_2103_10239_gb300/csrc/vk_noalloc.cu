@@ -209,6 +209,7 @@ extern "C" vk_status vk_knn_lists_noalloc(const int32_t* pos_q, int64_t n, const
   P.n_rep = 1;
   P.phi_cap = 2;
   P.knn_search = 1;  // the per-particle walk: no hint buffers, no shared-memory attribute to set
+  P.fov_cq = kViewAll;
 
   noalloc_setup_kernel<<<64, 256, 0, st>>>(R, tasks_d, n_tasks, rep_d, b.bounds, b.counts, n_cells, b.sub_count,
                                            n_sub, status_d);

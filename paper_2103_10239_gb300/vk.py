@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libvk_nm.so")
 
 VK_OK, VK_ERR_ARG, VK_ERR_CUDA, VK_ERR_OOM, VK_ERR_CAPACITY, VK_ERR_RANGE, VK_ERR_DEGENERATE, \
     VK_ERR_TIMEOUT, VK_ERR_STATE = range(9)
-VK_RULE_KNN, VK_RULE_VORONOI = 0, 1
+VK_RULE_KNN, VK_RULE_VORONOI, VK_RULE_METRIC = 0, 1, 2
 VK_NOISE_ANGULAR, VK_NOISE_VECTORIAL = 0, 1
 VK_SUM_PLAIN, VK_SUM_COMPENSATED, VK_SUM_FP64 = 0, 1, 2
 VK_HEADING_DIR, VK_HEADING_THETA = 0, 1
@@ -43,7 +43,8 @@ class vk_params(ctypes.Structure):
                 ("advect_new", ctypes.c_int32), ("sum_mode", ctypes.c_int32),
                 ("cell_occupancy", ctypes.c_float), ("phi_capacity", ctypes.c_int32),
                 ("knn_search", ctypes.c_int32), ("search_halo", ctypes.c_float),
-                ("search_halo_step", ctypes.c_float), ("replica_offset", ctypes.c_int32)]
+                ("search_halo_step", ctypes.c_float), ("replica_offset", ctypes.c_int32),
+                ("r0", ctypes.c_float), ("fov", ctypes.c_int32), ("fov_cos", ctypes.c_float)]
 
 
 class vk_info(ctypes.Structure):
@@ -143,7 +144,7 @@ def default_params(**kw) -> vk_params:
     load().vk_default_params(ctypes.byref(p))
     for key, val in kw.items():
         if key == "rule" and isinstance(val, str):
-            val = {"knn": VK_RULE_KNN, "voronoi": VK_RULE_VORONOI}[val]
+            val = {"knn": VK_RULE_KNN, "voronoi": VK_RULE_VORONOI, "metric": VK_RULE_METRIC}[val]
         if key == "noise" and isinstance(val, str):
             val = {"angular": VK_NOISE_ANGULAR, "vectorial": VK_NOISE_VECTORIAL}[val]
         if key == "sum_mode" and isinstance(val, str):

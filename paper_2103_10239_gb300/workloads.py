@@ -42,7 +42,7 @@ class Workload:
     theta: Optional[np.ndarray]  # (N,) float32 angles in [0, 2pi) (2D only)
     box_q: tuple               # L_q per axis (python ints)
     frac_bits: int
-    rule: str = "knn"          # "knn" | "voronoi"
+    rule: str = "knn"          # "knn" | "voronoi" | "metric"
     k: int = 7
     v0: float = 0.5
     dt: float = 1.0

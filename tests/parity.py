@@ -31,10 +31,15 @@ def oracle_neighbors(pos, box, rule, k):
     return oracle.voronoi(pos, box)
 
 
-def check_step(sim, w, rule, *, replica=0, check_neighbors=True, **step_kw):
-    """Compare neighbor lists of the current state, then one step."""
+def check_step(sim, w, rule, *, replica=0, check_neighbors=True, lists=None, **step_kw):
+    """Compare neighbor lists of the current state, then one step.
+    ``lists(pos, dir) -> (offsets, ids)`` gives the oracle's lists for rules
+    other than plain kNN and Voronoi."""
     pos0, d0, _, t0 = sim.state(replica)
-    off_o, ids_o = oracle_neighbors(pos0, w.box_q, rule, w.k)
+    if lists is not None:
+        off_o, ids_o = lists(pos0, d0)
+    else:
+        off_o, ids_o = oracle_neighbors(pos0, w.box_q, rule, w.k)
     if check_neighbors:
         off_g, ids_g = sim.neighbors(replica)
         assert np.array_equal(off_g, off_o), "neighbor counts differ"

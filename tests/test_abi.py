@@ -62,3 +62,36 @@ def test_product_path_does_not_import_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "vk_oracle" not in txt, f
+
+
+def test_rule_variant_argument_errors_without_gpu():
+    """The metric radius and the field of view are validated on the host."""
+    import numpy as np
+    from paper_2103_10239_gb300 import vk
+    pos = np.zeros((4, 2), dtype=np.int32)
+    d = np.ones((4, 2), dtype=np.float32)
+    p3 = np.zeros((4, 3), dtype=np.int32)
+    d3 = np.ones((4, 3), dtype=np.float32)
+    bad = [
+        (dict(rule="metric", r0=-1.0), vk.VK_ERR_ARG),
+        (dict(rule="metric", r0=float("inf")), vk.VK_ERR_ARG),
+        (dict(k=2, fov=1, fov_cos=1.5), vk.VK_ERR_ARG),
+        (dict(k=2, fov=1, fov_cos=float("nan")), vk.VK_ERR_ARG),
+        (dict(k=2, fov=2), vk.VK_ERR_ARG),
+        (dict(rule="voronoi", fov=1, fov_cos=0.0), vk.VK_ERR_ARG),
+        (dict(rule="metric", r0=1e6), vk.VK_ERR_RANGE),  # r0 * 2^16 above 2^31
+    ]
+    for kw, status in bad:
+        with pytest.raises(vk.VKError) as e:
+            vk.Sim.create(pos, d, (100, 100), 16, **kw)
+        assert e.value.status == status, kw
+    with pytest.raises(vk.VKError) as e:
+        vk.Sim.create(p3, d3, (100, 100, 100), 16, k=2, noise="vectorial", fov=1, fov_cos=0.0)
+    assert e.value.status == vk.VK_ERR_ARG
+
+
+def test_rule_variant_defaults():
+    from paper_2103_10239_gb300 import vk
+    p = vk.default_params()
+    assert (p.fov, p.r0, p.fov_cos) == (0, 1.0, -1.0)
+    assert vk.default_params(rule="metric").rule == vk.VK_RULE_METRIC

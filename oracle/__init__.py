@@ -104,6 +104,10 @@ def _load():
         lib.orc_order_parameter_f64.argtypes = [ctypes.c_int, ctypes.c_int64,
                                                 ctypes.POINTER(ctypes.c_double)]
         lib.orc_order_parameter_f64.restype = ctypes.c_double
+        f64p = ctypes.POINTER(ctypes.c_double)
+        lib.orc_tissue.argtypes = [ctypes.c_int64, i32p, i64p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, f64p, f64p, f64p, f64p]
+        lib.orc_tissue.restype = ctypes.c_int
         lib.orc_num_threads.argtypes = []
         lib.orc_num_threads.restype = ctypes.c_int
         _lib = lib
@@ -245,6 +249,27 @@ def delaunay_star_triangles(pos_q: np.ndarray, box_q):
     _check(rc, "delaunay_star_triangles")
     t = int(nt[0])
     return coords[:t], tids[:t]
+
+
+def tissue(pos_q: np.ndarray, box_q, frac_bits: int, KA: float, KP: float, A0: float, P0: float,
+           forces: bool = True):
+    """Voronoi tissue model in length units (grid unit = 2^-F): cell areas
+    and perimeters, the energy of Eq. (vmEnergy) and the forces -dE/dr_i.
+    Returns (area (n,), perimeter (n,), energy, force (n, 2) or None)."""
+    lib = _load()
+    pos = np.ascontiguousarray(pos_q, dtype=np.int32)
+    n = pos.shape[0]
+    box = _box(box_q, 2)
+    area = np.zeros(n, dtype=np.float64)
+    perim = np.zeros(n, dtype=np.float64)
+    force = np.zeros((n, 2), dtype=np.float64) if forces else None
+    e = np.zeros(1, dtype=np.float64)
+    f64 = ctypes.POINTER(ctypes.c_double)
+    rc = lib.orc_tissue(n, _ptr(pos, ctypes.c_int32), _ptr(box, ctypes.c_int64), 2.0 ** -frac_bits, float(KA),
+                        float(KP), float(A0), float(P0), _ptr(area, ctypes.c_double), _ptr(perim, ctypes.c_double),
+                        _ptr(force, ctypes.c_double) if forces else ctypes.cast(None, f64), _ptr(e, ctypes.c_double))
+    _check(rc, "tissue")
+    return area, perim, float(e[0]), force
 
 
 def orient2d(a, b, c) -> int:

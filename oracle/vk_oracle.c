@@ -22,7 +22,12 @@
  *   - one Vicsek update: the position step of Eq. (1) and the alignment rule of
  *     Eq. (2), in FP64, with the noise drawn from Philox4x32-10 (Salmon, Moraes,
  *     Dror & Shaw, SC'11) keyed by (seed) and countered by (id, step, replica);
- *   - the polar order parameter |sum_i n_i| / N.
+ *   - the polar order parameter |sum_i n_i| / N;
+ *   - the k nearest neighbors inside a field of view and the metric (r0)
+ *     neighbors (Sec. "Metric and topological flocking models");
+ *   - the Voronoi tissue model (Sec. "Geometric models of dense tissue"):
+ *     cell areas and perimeters, the energy of Eq. (vmEnergy) and the forces
+ *     of Sec. "Voronoi model forces" by the chain rule through the vertices.
  *
  * Readings where the paper is silent (documented in the design notes):
  *   - minimum image maps a difference into (-L/2, L/2];
@@ -830,6 +835,213 @@ int orc_delaunay_star_triangles(int64_t n, const int32_t* pos, const int64_t* bo
   *ntri = c;
   vtess_free(&V);
   return c > cap ? ORC_ERR_ARG : ORC_OK;
+}
+
+/* ======================================================================== */
+/* Voronoi tissue model: cell areas, perimeters, energy and forces            */
+/* ======================================================================== */
+
+/* Circumcenter of (0, a, b) (a, b relative to the first point), FP64. */
+static void circum_rel(double ax, double ay, double bx, double by, double* ux, double* uy) {
+  const double D = 2.0 * (ax * by - ay * bx);
+  const double a2 = ax * ax + ay * ay, b2 = bx * bx + by * by;
+  *ux = (by * a2 - ay * b2) / D;
+  *uy = (ax * b2 - bx * a2) / D;
+}
+
+/* Jacobian J[mu][lam] = d h_mu / d r_lam of the circumcenter h of the
+ * triangle (r, r + a, r + b) with respect to its first point r: h = r + u(a, b)
+ * with a = r_a - r, b = r_b - r, so dh/dr = I - du/da - du/db.  Obtained by
+ * differentiating the closed form of circum_rel (quotient rule). */
+static void circum_jac_first(double ax, double ay, double bx, double by, double J[2][2]) {
+  const double D = 2.0 * (ax * by - ay * bx);
+  const double a2 = ax * ax + ay * ay, b2 = bx * bx + by * by;
+  const double Nx = by * a2 - ay * b2, Ny = ax * b2 - bx * a2;
+  /* partial derivatives of Nx, Ny, D with respect to (ax, ay, bx, by) */
+  const double dNx[4] = {2.0 * ax * by, 2.0 * ay * by - b2, -2.0 * bx * ay, a2 - 2.0 * by * ay};
+  const double dNy[4] = {b2 - 2.0 * ax * bx, -2.0 * ay * bx, 2.0 * bx * ax - a2, 2.0 * by * ax};
+  const double dD[4] = {2.0 * by, -2.0 * bx, -2.0 * ay, 2.0 * ax};
+  double du[2][4];
+  for (int v = 0; v < 4; ++v) {
+    du[0][v] = (dNx[v] * D - Nx * dD[v]) / (D * D);
+    du[1][v] = (dNy[v] * D - Ny * dD[v]) / (D * D);
+  }
+  for (int mu = 0; mu < 2; ++mu)
+    for (int lam = 0; lam < 2; ++lam) J[mu][lam] = (mu == lam ? 1.0 : 0.0) - du[mu][lam] - du[mu][2 + lam];
+}
+
+/* dE_c/dh for the vertex h of cell c whose polygon neighbors (counter-
+ * clockwise order) are prev and next, all relative to the same origin:
+ * A = (1/2) sum cross(h_k, h_k+1) gives dA/dh = (1/2)(y_next - y_prev,
+ * x_prev - x_next); P = sum |h_k+1 - h_k| gives dP/dh = (h - prev)/|h - prev|
+ * + (h - next)/|h - next|. */
+static int cell_grad(double hx, double hy, double px, double py, double nx, double ny, double gA, double gP,
+                     double* gx, double* gy) {
+  const double l1 = hypot(hx - px, hy - py), l2 = hypot(hx - nx, hy - ny);
+  if (!(l1 > 0.0) || !(l2 > 0.0)) return ORC_ERR_DEGENERATE;
+  *gx = gA * 0.5 * (ny - py) + gP * ((hx - px) / l1 + (hx - nx) / l2);
+  *gy = gA * 0.5 * (px - nx) + gP * ((hy - py) / l1 + (hy - ny) / l2);
+  return ORC_OK;
+}
+
+/* Voronoi tissue model (Sec. "Geometric models of dense tissue"): every
+ * particle is the generator of its Voronoi cell, of area A_i and perimeter
+ * P_i; the energy is Eq. (vmEnergy), E = sum_i KA (A_i - A0)^2 +
+ * KP (P_i - P0)^2, and the force on particle i is F_i = -dE/dr_i (Sec.
+ * "Voronoi model forces"): moving r_i moves the vertices of cell i, the
+ * circumcenters h of the Delaunay triangles (i, a, b) around it, and each
+ * such vertex is shared by the cells i, a and b, so
+ *   F_i = - sum_{h of cell i} (dh/dr_i)^T (dE_i/dh + dE_a/dh + dE_b/dh).
+ * Positions are grid units scaled by `unit` (the length of one grid unit)
+ * into length units; everything is FP64.  Needs distinct particles and a
+ * cell polygon without zero-length edges (no four cocircular particles),
+ * else ORC_ERR_DEGENERATE.  force: 2 n doubles (may be NULL). */
+int orc_tissue(int64_t n, const int32_t* pos, const int64_t* box, double unit, double KA, double KP, double A0,
+               double P0, double* area, double* perim, double* force, double* energy) {
+  if (n < 3 || box[0] < 2 || box[1] < 2 || !(unit > 0.0)) return ORC_ERR_ARG;
+  /* distinct particles */
+  {
+    pidx_t* srt = (pidx_t*)malloc(sizeof(pidx_t) * (size_t)n);
+    if (!srt) return ORC_ERR_OOM;
+    for (int64_t i = 0; i < n; ++i) {
+      srt[i].x = pos[2 * i];
+      srt[i].y = pos[2 * i + 1];
+      srt[i].id = (int32_t)i;
+    }
+    qsort(srt, (size_t)n, sizeof(pidx_t), cmp_pidx);
+    int dup = 0;
+    for (int64_t i = 1; i < n; ++i) dup |= srt[i].x == srt[i - 1].x && srt[i].y == srt[i - 1].y;
+    free(srt);
+    if (dup) return ORC_ERR_DEGENERATE;
+  }
+  vtess_t V;
+  int rc = vtess_build_auto(&V, n, pos, box);
+  if (rc) return rc;
+  /* stars of the originals: triangles (i, a, b), counter-clockwise, i first */
+  int64_t* beg = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  if (!beg) { vtess_free(&V); return ORC_ERR_OOM; }
+  for (int32_t t = 0; t < V.D.nt; ++t) {
+    const tri_t* T = &V.D.t[t];
+    if (!T->alive) continue;
+    for (int e = 0; e < 3; ++e)
+      if (T->v[e] < n) beg[T->v[e] + 1] += 1;
+  }
+  for (int64_t i = 0; i < n; ++i) beg[i + 1] += beg[i];
+  const int64_t ns = beg[n];
+  int32_t* sa = (int32_t*)malloc(sizeof(int32_t) * (size_t)ns);
+  int32_t* sb = (int32_t*)malloc(sizeof(int32_t) * (size_t)ns);
+  int32_t* ord = (int32_t*)malloc(sizeof(int32_t) * (size_t)ns);  /* star entries in fan order */
+  double* hx = (double*)malloc(sizeof(double) * (size_t)ns);     /* vertices relative to the owner */
+  double* hy = (double*)malloc(sizeof(double) * (size_t)ns);
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  if (!sa || !sb || !ord || !hx || !hy || !fill) {
+    free(beg); free(sa); free(sb); free(ord); free(hx); free(hy); free(fill);
+    vtess_free(&V);
+    return ORC_ERR_OOM;
+  }
+  for (int64_t i = 0; i < n; ++i) fill[i] = beg[i];
+  for (int32_t t = 0; t < V.D.nt; ++t) {
+    const tri_t* T = &V.D.t[t];
+    if (!T->alive) continue;
+    for (int e = 0; e < 3; ++e)
+      if (T->v[e] < n) {
+        const int64_t w = fill[T->v[e]]++;
+        sa[w] = T->v[(e + 1) % 3];
+        sb[w] = T->v[(e + 2) % 3];
+      }
+  }
+  rc = ORC_OK;
+  /* chain every star into a fan: entry k is followed by the entry whose a is
+   * its b; then the vertices (circumcenters) in counter-clockwise order */
+  for (int64_t i = 0; i < n && rc == ORC_OK; ++i) {
+    const int64_t b0 = beg[i], m = beg[i + 1] - beg[i];
+    if (m < 3) { rc = ORC_ERR_DEGENERATE; break; }
+    int64_t cur = b0;
+    for (int64_t k = 0; k < m; ++k) {
+      ord[b0 + k] = (int32_t)(cur - b0);
+      int64_t nxt = -1;
+      for (int64_t q = b0; q < b0 + m; ++q)
+        if (sa[q] == sb[cur]) { nxt = q; break; }
+      if (nxt < 0) { rc = ORC_ERR_INTERNAL; break; }
+      cur = nxt;
+    }
+    if (rc == ORC_OK && cur != b0) rc = ORC_ERR_INTERNAL;  /* the fan must close after m triangles */
+    const double xi = (double)V.xy[2 * i], yi = (double)V.xy[2 * i + 1];
+    double A = 0.0, Pm = 0.0;
+    for (int64_t k = 0; k < m && rc == ORC_OK; ++k) {
+      const int64_t q = b0 + ord[b0 + k];
+      circum_rel(((double)V.xy[2 * (int64_t)sa[q]] - xi) * unit, ((double)V.xy[2 * (int64_t)sa[q] + 1] - yi) * unit,
+                 ((double)V.xy[2 * (int64_t)sb[q]] - xi) * unit, ((double)V.xy[2 * (int64_t)sb[q] + 1] - yi) * unit,
+                 &hx[b0 + k], &hy[b0 + k]);
+    }
+    for (int64_t k = 0; k < m && rc == ORC_OK; ++k) {
+      const int64_t k1 = (k + 1) % m;
+      A += 0.5 * (hx[b0 + k] * hy[b0 + k1] - hx[b0 + k1] * hy[b0 + k]);
+      Pm += hypot(hx[b0 + k1] - hx[b0 + k], hy[b0 + k1] - hy[b0 + k]);
+    }
+    area[i] = A;
+    perim[i] = Pm;
+  }
+  double E = 0.0;
+  for (int64_t i = 0; i < n && rc == ORC_OK; ++i)
+    E += KA * (area[i] - A0) * (area[i] - A0) + KP * (perim[i] - P0) * (perim[i] - P0);
+  if (rc == ORC_OK) *energy = E;
+  /* forces: for vertex k of cell i (triangle (i, a, b)), the same vertex in
+   * the fans of the originals of a and b is found by the integer offsets of
+   * the triangle's other two points */
+  for (int64_t i = 0; force && i < n && rc == ORC_OK; ++i) {
+    const int64_t b0 = beg[i], m = beg[i + 1] - beg[i];
+    const int64_t xi = V.xy[2 * i], yi = V.xy[2 * i + 1];
+    double Fx = 0.0, Fy = 0.0;
+    for (int64_t k = 0; k < m && rc == ORC_OK; ++k) {
+      const int64_t q = b0 + ord[b0 + k];
+      const int32_t va = sa[q], vb = sb[q];
+      double gx = 0.0, gy = 0.0, cx, cy;
+      /* cell i itself */
+      const int64_t kp = (k + m - 1) % m, kn = (k + 1) % m;
+      rc = cell_grad(hx[b0 + k], hy[b0 + k], hx[b0 + kp], hy[b0 + kp], hx[b0 + kn], hy[b0 + kn],
+                     2.0 * KA * (area[i] - A0), 2.0 * KP * (perim[i] - P0), &cx, &cy);
+      gx += cx;
+      gy += cy;
+      /* cells a and b: the triangle is (a, b, i) around a and (b, i, a) around b */
+      for (int side = 0; side < 2 && rc == ORC_OK; ++side) {
+        const int32_t vc = side == 0 ? va : vb;          /* the cell's point (tiled) */
+        const int32_t v1 = side == 0 ? vb : (int32_t)i;  /* next point around it */
+        const int32_t v2 = side == 0 ? (int32_t)i : va;
+        const int32_t c = V.orig[vc];
+        const int64_t d1x = V.xy[2 * (int64_t)v1] - V.xy[2 * (int64_t)vc], d1y = V.xy[2 * (int64_t)v1 + 1] - V.xy[2 * (int64_t)vc + 1];
+        const int64_t d2x = V.xy[2 * (int64_t)v2] - V.xy[2 * (int64_t)vc], d2y = V.xy[2 * (int64_t)v2 + 1] - V.xy[2 * (int64_t)vc + 1];
+        const int64_t cb = beg[c], cm = beg[c + 1] - beg[c];
+        const int64_t cxo = V.xy[2 * (int64_t)c], cyo = V.xy[2 * (int64_t)c + 1];
+        int64_t at = -1;
+        for (int64_t kk = 0; kk < cm; ++kk) {
+          const int64_t qq = cb + ord[cb + kk];
+          if (V.xy[2 * (int64_t)sa[qq]] - cxo == d1x && V.xy[2 * (int64_t)sa[qq] + 1] - cyo == d1y &&
+              V.xy[2 * (int64_t)sb[qq]] - cxo == d2x && V.xy[2 * (int64_t)sb[qq] + 1] - cyo == d2y) {
+            at = kk;
+            break;
+          }
+        }
+        if (at < 0) { rc = ORC_ERR_INTERNAL; break; }
+        const int64_t ap = (at + cm - 1) % cm, an = (at + 1) % cm;
+        rc = cell_grad(hx[cb + at], hy[cb + at], hx[cb + ap], hy[cb + ap], hx[cb + an], hy[cb + an],
+                       2.0 * KA * (area[c] - A0), 2.0 * KP * (perim[c] - P0), &cx, &cy);
+        gx += cx;
+        gy += cy;
+      }
+      if (rc != ORC_OK) break;
+      double J[2][2];
+      circum_jac_first(((double)(V.xy[2 * (int64_t)va] - xi)) * unit, ((double)(V.xy[2 * (int64_t)va + 1] - yi)) * unit,
+                       ((double)(V.xy[2 * (int64_t)vb] - xi)) * unit, ((double)(V.xy[2 * (int64_t)vb + 1] - yi)) * unit, J);
+      Fx -= gx * J[0][0] + gy * J[1][0];
+      Fy -= gx * J[0][1] + gy * J[1][1];
+    }
+    force[2 * i] = Fx;
+    force[2 * i + 1] = Fy;
+  }
+  free(beg); free(sa); free(sb); free(ord); free(hx); free(hy); free(fill);
+  vtess_free(&V);
+  return rc;
 }
 
 /* ======================================================================== */

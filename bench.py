@@ -57,6 +57,8 @@ def parse():
                     help="warp-tile halo as a multiple of the previous k-th distance (0: library default)")
     ap.add_argument("--no-replicas", action="store_true",
                     help="skip the replica-batch block of the headline line")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the short secondary measurements (other rules and dimensions)")
     ap.add_argument("--replica-steps", type=int, default=10,
                     help="timed (and warm-up) steps of each arm of the replica-batch block")
     ap.add_argument("--autotune", action="store_true",
@@ -393,6 +395,9 @@ def run_ours(args, rank, world, dist):
     replicas = None
     if rank == 0 and world == 1 and not args.no_replicas:
         replicas = replica_block(stream, args.replica_steps)
+    secondary = None
+    if rank == 0 and world == 1 and not args.no_secondary:
+        secondary = secondary_block(stream)
     if rank != 0:
         return
     phases = {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}
@@ -418,6 +423,7 @@ def run_ours(args, rank, world, dist):
                                   "frac": 32 * w.n / (per_launch_ms * 1e-3) / 1e9 / peak},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(info.kernels_per_step) * args.steps,
         "clocks": clk, "phases": phases, "wall_s_timed_region": t_wall, "replicas": replicas,
+        "secondary": secondary,
     }
     print(json.dumps(line), flush=True)
 
@@ -459,6 +465,42 @@ def replica_block(stream, steps: int) -> dict:
             "replica_300_identical_across_arms": bool(t_b == t_p and np.array_equal(pos_b, pos_p)),
             "config": {"workload": "512 replicas, N_r log-uniform [1024, 65536], density 1, k=7, F=16, "
                                    "eta 0.05-0.6", "n_total": total}}
+
+
+def _rate(stream, sim, n: int, warmup: int, steps: int) -> dict:
+    sim.step(warmup)
+    ms = _timed(stream, lambda: sim.step(steps)) / steps
+    return {"value": n / (ms * 1e-3), "unit": "particle-steps/s", "ms_per_step": ms, "warmup": warmup,
+            "steps": steps}
+
+
+def secondary_block(stream) -> dict:
+    """Short measurements of the other rules and dimensions, each from its
+    own seeded synthetic state, timed with CUDA events on the sim's stream
+    over consecutive steps after a warm-up (inputs resident, no L2 flush
+    between steps).  Labelled secondary: not the benchmark configuration."""
+    from paper_2103_10239_gb300 import vk
+    from paper_2103_10239_gb300 import workloads as W
+    out = {}
+    wv = W.voronoi_mixed(eta=0.1)
+    for name, rebuild in (("voronoi_mixed65k_reuse", 0), ("voronoi_mixed65k_rebuild", 1)):
+        with vk.from_workload(wv, stream=stream, voronoi_rebuild=rebuild) as sim:
+            out[name] = dict(_rate(stream, sim, wv.n, 20, 50),
+                             config={"workload": wv.name, "rule": "voronoi", "eta": 0.1,
+                                     "voronoi_rebuild": rebuild})
+    wc = W.clustered_large()
+    with vk.from_workload(wc, stream=stream, rule="metric", r0=1.0, cell_occupancy=512.0) as sim:
+        out["metric_clustered4M_r1"] = dict(_rate(stream, sim, wc.n, 5, 20),
+                                            config={"workload": wc.name, "rule": "metric", "r0": 1.0})
+    with vk.from_workload(wc, stream=stream, fov=1, fov_cos=0.0, cell_occupancy=2048.0) as sim:
+        out["knn_fov_clustered4M_halfplane"] = dict(_rate(stream, sim, wc.n, 5, 20),
+                                                    config={"workload": wc.name, "rule": "knn", "k": 7,
+                                                            "fov_cos": 0.0})
+    w3 = W.knn_3d()
+    with vk.from_workload(w3, stream=stream) as sim:
+        out["knn3d_1M"] = dict(_rate(stream, sim, w3.n, 5, 20), config={"workload": w3.name, "rule": "knn",
+                                                                        "k": 7, "dim": 3})
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -134,6 +134,11 @@ typedef struct {
                            in view aligns with those it has (its list is shorter). */
   float fov_cos;        /* cosine of the half-angle of the field of view, in [-1, 1]; -1 is the
                            full circle (the plain rule), 0 the half-plane ahead */
+  int32_t voronoi_rebuild; /* VK_RULE_VORONOI: 0 (default) = start every cell from last step's
+                           neighbors and re-check it (Sec. "Computational tools: Voronoi neighbor
+                           lists": the old triangulation is kept where every circumcircle is still
+                           empty and repaired where it is not); 1 = build every cell from scratch.
+                           Results never depend on it; only the speed does. */
 } vk_params;
 
 /* Fills p with the defaults: kNN, k = 7, v0 = 0.5, dt = 1, eta = 0.3, seed = 1,

@@ -235,8 +235,10 @@ vk_status sort_from_U(vk_sim* s) {
   cudaEvent_t e0 = nullptr;
   vk_status st = record_begin(s, 3, &e0);
   if (st) return st;
-  // a new state: the previous k-th distances no longer describe it
+  // a new state: the previous k-th distances and neighbors no longer describe it
   if (s->b.U_hint) VK_CUDA(s, cudaMemsetAsync(s->b.U_hint, 0, sizeof(float) * (size_t)s->n_total, s->stream));
+  if (s->b.vor_seed_n)
+    VK_CUDA(s, cudaMemsetAsync(s->b.vor_seed_n, 0, sizeof(int32_t) * (size_t)s->n_total, s->stream));
   VK_CUDA(s, launch_count(s->g, s->b, s->stream));
   VK_CUDA(s, launch_build(s->g, s->b, s->stream));
   VK_CUDA(s, launch_scatter(s->g, s->b, step_params(s), 0, s->stream));
@@ -338,6 +340,7 @@ bool valid_params(const vk_params* p, int dim, std::string* why) {
   if (p->rule == VK_RULE_METRIC && !(p->r0 >= 0.f && std::isfinite(p->r0)))
     return *why = "r0 must be finite and >= 0", false;
   if (p->fov != 0 && p->fov != 1) return *why = "fov must be 0 or 1", false;
+  if (p->voronoi_rebuild != 0 && p->voronoi_rebuild != 1) return *why = "voronoi_rebuild must be 0 or 1", false;
   if (p->fov && (p->rule != VK_RULE_KNN || dim != 2)) return *why = "a field of view needs the 2D kNN rule", false;
   if (p->fov && !(p->fov_cos >= -1.f && p->fov_cos <= 1.f)) return *why = "fov_cos must be in [-1, 1]", false;
   return true;
@@ -446,6 +449,11 @@ vk_status build_sim(int32_t n_rep, const int64_t* n_r, const int32_t* pos_q, con
   if (params->rule == VK_RULE_KNN && dim == 2) {
     if ((e = dalloc(&s->b.S_hint, N)) || (e = dalloc(&s->b.U_hint, N)) || (e = prepare_knn2()))
       return bail(cuda_fail(s, e, "kNN search buffers"));
+  }
+  if (params->rule == VK_RULE_VORONOI && !params->voronoi_rebuild) {
+    if ((e = dalloc(&s->b.vor_seed, N * kVorSeed)) || (e = dalloc(&s->b.vor_seed_n, N)) ||
+        (e = dalloc(&s->b.slot_of, N)))
+      return bail(cuda_fail(s, e, "Voronoi seed buffers"));
   }
   if (ensure_cells_capacity(s)) return bail(VK_ERR_OOM);
   if ((e = cudaMemsetAsync(s->b.d_step, 0, sizeof(int64_t), s->stream)) ||
@@ -756,7 +764,8 @@ void vk_destroy(vk_sim* s) {
                   s->b.counts, s->b.offsets, s->b.bsum, s->b.phi_acc, s->b.d_step, s->b.d_status,
                   s->b.ovf_list, s->b.ovf_count, s->reps_d, s->tasks_d, s->b.sub_s, s->b.sub_base,
                   s->b.sub_count, s->b.sub_off, s->b.bsum2, s->d_stats, s->b.bounds,
-                  s->st_pos, s->st_dir, s->st_theta, s->b.S_hint, s->b.U_hint};
+                  s->st_pos, s->st_dir, s->st_theta, s->b.S_hint, s->b.U_hint, s->b.vor_seed,
+                  s->b.vor_seed_n, s->b.slot_of};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);

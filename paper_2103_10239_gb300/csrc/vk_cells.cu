@@ -288,7 +288,8 @@ __global__ void __launch_bounds__(kBlock) scatter_kernel(const Rep* __restrict__
                                                          typename Vec<DIM>::F* __restrict__ S_dir,
                                                          int32_t* __restrict__ S_id,
                                                          const float* __restrict__ U_hint,
-                                                         float* __restrict__ S_hint, int advance_step,
+                                                         float* __restrict__ S_hint,
+                                                         int32_t* __restrict__ slot_of, int advance_step,
                                                          int64_t* d_step, PhiAcc* phi_acc, int n_rep,
                                                          int phi_cap, int32_t* ovf_count) {
   const BlockTask t = tasks[blockIdx.x];
@@ -316,8 +317,10 @@ __global__ void __launch_bounds__(kBlock) scatter_kernel(const Rep* __restrict__
   const uint32_t dst = G.sub_off[g] + U_rank[s];
   S_pos[dst] = pv;
   S_dir[dst] = U_dir[s];
-  S_id[dst] = U_id[s];
+  const int32_t id = U_id[s];
+  S_id[dst] = id;
   if (S_hint) S_hint[dst] = U_hint[s];
+  if (slot_of) slot_of[R.p0 + id] = (int32_t)dst;
 }
 
 template <int DIM>
@@ -430,12 +433,12 @@ cudaError_t launch_scatter(const Geometry& g, const Buffers& b, const StepParams
   if (g.dim == 2)
     scatter_kernel<2><<<g.n_tasks, kBlock, 0, st>>>(
         g.reps, g.tasks, (const int2*)b.U_pos, (const float2*)b.U_dir, b.U_id, b.U_rank, b.bounds, G,
-        (int2*)b.S_pos, (float2*)b.S_dir, b.S_id, b.U_hint, b.S_hint, advance_step, b.d_step, b.phi_acc,
+        (int2*)b.S_pos, (float2*)b.S_dir, b.S_id, b.U_hint, b.S_hint, b.slot_of, advance_step, b.d_step, b.phi_acc,
         P.n_rep, P.phi_cap, b.ovf_count);
   else
     scatter_kernel<3><<<g.n_tasks, kBlock, 0, st>>>(
         g.reps, g.tasks, (const int4*)b.U_pos, (const float4*)b.U_dir, b.U_id, b.U_rank, b.bounds, G,
-        (int4*)b.S_pos, (float4*)b.S_dir, b.S_id, nullptr, nullptr, advance_step, b.d_step, b.phi_acc,
+        (int4*)b.S_pos, (float4*)b.S_dir, b.S_id, nullptr, nullptr, nullptr, advance_step, b.d_step, b.phi_acc,
         P.n_rep, P.phi_cap, b.ovf_count);
   return cudaGetLastError();
 }

@@ -644,7 +644,19 @@ struct Buffers {
   // only a search hint, results never depend on it (NULL for other rules)
   float* S_hint;
   float* U_hint;
+  // Voronoi rule (Sec. "Computational tools: Voronoi neighbor lists": last
+  // step's triangulation is re-checked rather than rebuilt): every
+  // particle's neighbor ids of the last step, indexed by (replica's first
+  // slot + id), up to kVorSeed each (count in vor_seed_n), and the sorted
+  // slot of every particle by the same index (written by the scatter).  A
+  // cell is clipped by these sites first; only the order of the work
+  // depends on them, never the result (NULL: build every cell from scratch).
+  int32_t* vor_seed;
+  int32_t* vor_seed_n;
+  int32_t* slot_of;
 };
+
+constexpr int kVorSeed = 12;
 
 struct Geometry {
   int dim;

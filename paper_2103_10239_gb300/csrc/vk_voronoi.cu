@@ -491,16 +491,33 @@ __device__ __noinline__ void far_images(const Rep& R, int64_t self, const int32_
 // internal inconsistencies (kStRange); capacity overflow is returned.
 // Returns false (and leaves the cell unusable) if the polygon or the twin list
 // outgrew its capacity.
+//
+// Seeds (last step's neighbors, the lazy re-check of Sec. "Computational
+// tools: Voronoi neighbor lists"): when given, the cell is first clipped by
+// those sites, so it starts close to its final shape and with a tight
+// relevance box; the walk then checks every site that could still cut it
+// (a site inside a vertex disk is a site inside the circumcircle of one of
+// the old Delaunay triangles) and clips by it, which repairs the cell where
+// the triangulation changed.  The half-plane intersection does not depend
+// on the order of the sites, so the cell is the same as without seeds.
+struct Seeds {
+  const int32_t* ids;      // replica-local ids of last step's neighbors (NULL: none)
+  int n;
+  const int32_t* slot_of;  // sorted slot by (replica's first slot + id)
+};
+
 template <int CAP>
 __device__ bool voronoi_cell(const Rep& R, int64_t self, const int32_t* pi, int32_t self_id,
                              const int2* __restrict__ pos, const int32_t* __restrict__ ids,
-                             const GridView& G, Poly<CAP>& P, int32_t* status, uint32_t budget,
+                             const GridView& G, Poly<CAP>& P, int32_t* status, uint32_t budget, const Seeds& sd,
                              uint32_t* n_cand = nullptr, uint32_t* n_runs = nullptr) {
   bool bad = false, overflow = false;
   uint32_t seen = 0;
   poly_init(P, self_id, R.L[0], R.L[1], &bad);
   const int64_t Lx = R.L[0], Ly = R.L[1];
   auto add_twin = [&](int32_t slot, int32_t jid, int32_t of) {
+    for (int t = 0; t < P.nt; ++t)
+      if (P.tw_slot[t] == slot) return;  // met again (a seed is visited twice)
     if (P.nt == Poly<CAP>::TW) {
       overflow = true;
       return;
@@ -529,7 +546,7 @@ __device__ bool voronoi_cell(const Rep& R, int64_t self, const int32_t* pi, int3
       // no vertex cut but some vertex on the bisector: a twin of an edge site?
       for (int a = 0; a < P.m; ++a)
         if (P.qx[a] == qx && P.qy[a] == qy && P.slot[a] >= 0) {
-          add_twin(slot, jid, P.slot[a]);
+          if (P.slot[a] != slot) add_twin(slot, jid, P.slot[a]);  // not the edge site itself, met again
           break;
         }
     }
@@ -549,6 +566,13 @@ __device__ bool voronoi_cell(const Rep& R, int64_t self, const int32_t* pi, int3
       visit(qx, qy, ids[q], (int32_t)q);
     }
   };
+  for (int j = 0; j < sd.n && !overflow; ++j) {
+    const int32_t jid = sd.ids[j];
+    const int32_t q = sd.slot_of[R.p0 + jid];
+    if ((int64_t)q == self) continue;
+    const int2 pj = pos[q];
+    visit((int32_t)min_image((int64_t)pj.x - pi[0], Lx), (int32_t)min_image((int64_t)pj.y - pi[1], Ly), jid, q);
+  }
   auto box = [&](int64_t* b) {
     poly_refresh_box(P);
     // after an overflow nothing more is needed: an empty box ends the walk
@@ -597,13 +621,15 @@ __device__ __forceinline__ int site_effect(const Poly<CAP>& P, int32_t mx, int32
 template <int CAP>
 __device__ bool voronoi_cell_warp(const Rep& R, int64_t self, const int32_t* pi, int32_t self_id,
                                   const int2* __restrict__ pos, const int32_t* __restrict__ ids, const GridView& G,
-                                  Poly<CAP>& P, int32_t* status) {
+                                  Poly<CAP>& P, int32_t* status, const Seeds& sd) {
   const int lane = threadIdx.x & 31;
   bool bad = false, overflow = false;  // kept by lane 0, broadcast after every serial part
   if (lane == 0) poly_init(P, self_id, R.L[0], R.L[1], &bad);
   __syncwarp();
   const int64_t Lx = R.L[0], Ly = R.L[1];
   auto add_twin = [&](int32_t slot, int32_t jid, int32_t of) {
+    for (int t = 0; t < P.nt; ++t)
+      if (P.tw_slot[t] == slot) return;  // met again (a seed is visited twice)
     if (P.nt == Poly<CAP>::TW) {
       overflow = true;
       return;
@@ -632,7 +658,7 @@ __device__ bool voronoi_cell_warp(const Rep& R, int64_t self, const int32_t* pi,
     if (touch) {
       for (int a = 0; a < P.m; ++a)
         if (P.qx[a] == qx && P.qy[a] == qy && P.slot[a] >= 0) {
-          add_twin(slot, jid, P.slot[a]);
+          if (P.slot[a] != slot) add_twin(slot, jid, P.slot[a]);  // not the edge site itself, met again
           break;
         }
     }
@@ -673,6 +699,17 @@ __device__ bool voronoi_cell_warp(const Rep& R, int64_t self, const int32_t* pi,
       process(flag, qx, qy, jid, (int32_t)q);
     }
   };
+  if (lane == 0) {
+    for (int j = 0; j < sd.n && !overflow; ++j) {
+      const int32_t jid = sd.ids[j];
+      const int32_t q = sd.slot_of[R.p0 + jid];
+      if ((int64_t)q == self) continue;
+      const int2 pj = pos[q];
+      visit0((int32_t)min_image((int64_t)pj.x - pi[0], Lx), (int32_t)min_image((int64_t)pj.y - pi[1], Ly), jid, q);
+    }
+  }
+  __syncwarp();
+  overflow = __shfl_sync(0xffffffffu, overflow, 0);
   auto box = [&](int64_t* b) {
     if (lane == 0) poly_refresh_box(P);
     __syncwarp();
@@ -753,9 +790,16 @@ __device__ __forceinline__ void voronoi_update(const Rep& R, const StepParams& P
                                                int32_t id, const float2* __restrict__ S_dir,
                                                int2* __restrict__ U_pos, float2* __restrict__ U_dir,
                                                int32_t* __restrict__ U_id, uint32_t* __restrict__ counts,
-                                               float* nnew) {
+                                               float* nnew, int32_t* __restrict__ seed_out,
+                                               int32_t* __restrict__ seed_n_out) {
   int32_t nid[CAP + Poly<CAP>::TW], nslot[CAP + Poly<CAP>::TW];
   const int cnt = voronoi_neighbors(P, id, nid, nslot);
+  if (seed_out) {
+    // the next step's seeds (any subset of sites would do)
+    const int ns = min(cnt, kVorSeed);
+    for (int j = 0; j < ns; ++j) seed_out[j] = nid[j];
+    *seed_n_out = ns;
+  }
   HeadSum<2> H;
   H.init();
   if (Pm.include_self) H.add(ni, Pm.sum_mode);
@@ -779,7 +823,8 @@ __global__ void __launch_bounds__(kBlock) voronoi_step_kernel(
     const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G,
     int2* __restrict__ U_pos, float2* __restrict__ U_dir, int32_t* __restrict__ U_id,
     uint32_t* __restrict__ counts, PhiAcc* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams Pm,
-    int2* __restrict__ ovf_list, int32_t* __restrict__ ovf_count, int32_t* status) {
+    int2* __restrict__ ovf_list, int32_t* __restrict__ ovf_count, int32_t* status, int32_t* __restrict__ vor_seed,
+    int32_t* __restrict__ vor_seed_n, const int32_t* __restrict__ slot_of) {
   __shared__ PhiShared phs;
   phi_block_begin(phs);
   const BlockTask t = tasks[blockIdx.x];
@@ -795,11 +840,14 @@ __global__ void __launch_bounds__(kBlock) voronoi_step_kernel(
     const int32_t pi[3] = {p.x, p.y, 0};
     const float ni[3] = {nv.x, nv.y, 0.f};
     const int32_t id = S_id[s];
+    const int64_t gi = R.p0 + id;
+    const Seeds sd{vor_seed ? vor_seed + gi * kVorSeed : nullptr, vor_seed ? vor_seed_n[gi] : 0, slot_of};
     Poly<kFastCap> P;
-    const bool ok = Pm.stats ? voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status, kHeavy, &n_cand, &n_runs)
-                             : voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status, kHeavy);
+    const bool ok = Pm.stats ? voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status, kHeavy, sd, &n_cand, &n_runs)
+                             : voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status, kHeavy, sd);
     if (ok) {
-      voronoi_update(R, Pm, step, s, P, pi, ni, id, S_dir, U_pos, U_dir, U_id, counts, nnew);
+      voronoi_update(R, Pm, step, s, P, pi, ni, id, S_dir, U_pos, U_dir, U_id, counts, nnew,
+                     vor_seed ? vor_seed + gi * kVorSeed : nullptr, vor_seed_n + gi);
     } else {
       const int q = atomicAdd(ovf_count, 1);
       ovf_list[q] = make_int2((int)s, t.rep);
@@ -819,7 +867,8 @@ __global__ void __launch_bounds__(32 * kOvfWarps) voronoi_overflow_kernel(
     const int32_t* __restrict__ S_id, GridView G, int2* __restrict__ U_pos,
     float2* __restrict__ U_dir, int32_t* __restrict__ U_id,
     uint32_t* __restrict__ counts, PhiAcc* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams Pm,
-    const int2* __restrict__ ovf_list, const int32_t* __restrict__ ovf_count, int32_t* status) {
+    const int2* __restrict__ ovf_list, const int32_t* __restrict__ ovf_count, int32_t* status,
+    int32_t* __restrict__ vor_seed, int32_t* __restrict__ vor_seed_n, const int32_t* __restrict__ slot_of) {
   __shared__ Poly<kSlowCap> poly[kOvfWarps];
   Poly<kSlowCap>& P = poly[threadIdx.x >> 5];
   const int total = *ovf_count;
@@ -832,7 +881,9 @@ __global__ void __launch_bounds__(32 * kOvfWarps) voronoi_overflow_kernel(
     const int2 p = S_pos[s];
     const int32_t pi[3] = {p.x, p.y, 0};
     const int32_t id = S_id[s];
-    const bool ok = voronoi_cell_warp(R, s, pi, id, S_pos, S_id, G, P, status);
+    const int64_t gi = R.p0 + id;
+    const Seeds sd{vor_seed ? vor_seed + gi * kVorSeed : nullptr, vor_seed ? vor_seed_n[gi] : 0, slot_of};
+    const bool ok = voronoi_cell_warp(R, s, pi, id, S_pos, S_id, G, P, status, sd);
     if ((threadIdx.x & 31) == 0) {
       if (!ok) {
         set_status(status, kStCapacity);
@@ -840,7 +891,8 @@ __global__ void __launch_bounds__(32 * kOvfWarps) voronoi_overflow_kernel(
         const float2 nv = S_dir[s];
         const float ni[3] = {nv.x, nv.y, 0.f};
         float nnew[3] = {0.f, 0.f, 0.f};
-        voronoi_update(R, Pm, step, s, P, pi, ni, id, S_dir, U_pos, U_dir, U_id, counts, nnew);
+        voronoi_update(R, Pm, step, s, P, pi, ni, id, S_dir, U_pos, U_dir, U_id, counts, nnew,
+                       vor_seed ? vor_seed + gi * kVorSeed : nullptr, vor_seed_n + gi);
         PhiAcc* acc = phi_acc + ((size_t)(step % Pm.phi_cap) * (size_t)Pm.n_rep + (size_t)e.y) * 3;
         atomicAdd(acc + 0, (PhiAcc)phi_fixed(nnew[0]));
         atomicAdd(acc + 1, (PhiAcc)phi_fixed(nnew[1]));
@@ -858,15 +910,20 @@ __global__ void __launch_bounds__(64) voronoi_export_kernel(const Rep* __restric
                                                             GridView G, int pass,
                                                             int32_t* __restrict__ deg,
                                                             const int64_t* __restrict__ out_off,
-                                                            int32_t* __restrict__ out_ids, int32_t* status) {
+                                                            int32_t* __restrict__ out_ids, int32_t* status,
+                                                            const int32_t* __restrict__ vor_seed,
+                                                            const int32_t* __restrict__ vor_seed_n,
+                                                            const int32_t* __restrict__ slot_of) {
   const Rep R = reps[rep];
   for (int li = blockIdx.x * blockDim.x + threadIdx.x; li < R.n; li += gridDim.x * blockDim.x) {
     const int64_t s = R.p0 + li;
     const int2 p = S_pos[s];
     const int32_t pi[3] = {p.x, p.y, 0};
     const int32_t id = S_id[s];
+    const int64_t gi = R.p0 + id;
+    const Seeds sd{vor_seed ? vor_seed + gi * kVorSeed : nullptr, vor_seed ? vor_seed_n[gi] : 0, slot_of};
     Poly<kSlowCap> P;
-    if (!voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status, 0u)) {
+    if (!voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status, 0u, sd)) {
       set_status(status, kStCapacity);
       if (pass == 0) deg[id] = 0;
       continue;
@@ -898,11 +955,12 @@ cudaError_t launch_voronoi_step(const Geometry& g, const Buffers& b, const StepP
   voronoi_step_kernel<<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int2*)b.S_pos, (const float2*)b.S_dir,
                                                     b.S_id, G, (int2*)b.U_pos, (float2*)b.U_dir, b.U_id,
                                                     b.counts, b.phi_acc, b.d_step, P, b.ovf_list,
-                                                    b.ovf_count, b.d_status);
+                                                    b.ovf_count, b.d_status, b.vor_seed, b.vor_seed_n,
+                                                    b.slot_of);
   voronoi_overflow_kernel<<<device_sm_count(), 32 * kOvfWarps, 0, st>>>(g.reps, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id,
                                               G, (int2*)b.U_pos, (float2*)b.U_dir, b.U_id,
                                               b.counts, b.phi_acc, b.d_step, P, b.ovf_list, b.ovf_count,
-                                              b.d_status);
+                                              b.d_status, b.vor_seed, b.vor_seed_n, b.slot_of);
   return cudaGetLastError();
 }
 
@@ -911,7 +969,7 @@ cudaError_t launch_voronoi_export(const Geometry& g, const Buffers& b, int rep, 
   if (n == 0) return cudaSuccess;
   const int nb = std::min((n + 63) / 64, device_sm_count() * 8);
   voronoi_export_kernel<<<nb, 64, 0, st>>>(g.reps, rep, (const int2*)b.S_pos, b.S_id, grid_view(b), pass, deg,
-                                           out_off, out_ids, b.d_status);
+                                           out_off, out_ids, b.d_status, b.vor_seed, b.vor_seed_n, b.slot_of);
   return cudaGetLastError();
 }
 

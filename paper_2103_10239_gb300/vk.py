@@ -44,7 +44,8 @@ class vk_params(ctypes.Structure):
                 ("cell_occupancy", ctypes.c_float), ("phi_capacity", ctypes.c_int32),
                 ("knn_search", ctypes.c_int32), ("search_halo", ctypes.c_float),
                 ("search_halo_step", ctypes.c_float), ("replica_offset", ctypes.c_int32),
-                ("r0", ctypes.c_float), ("fov", ctypes.c_int32), ("fov_cos", ctypes.c_float)]
+                ("r0", ctypes.c_float), ("fov", ctypes.c_int32), ("fov_cos", ctypes.c_float),
+                ("voronoi_rebuild", ctypes.c_int32)]
 
 
 class vk_info(ctypes.Structure):

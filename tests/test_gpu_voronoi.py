@@ -94,20 +94,23 @@ def test_density_two_large_sampled():
         _same(sim, pos, w.box_q)
 
 
-def test_coincident_particles_share_a_site():
+@pytest.mark.parametrize("rebuild", [0, 1])
+def test_coincident_particles_share_a_site(rebuild):
     """Reading: coincident particles form one Voronoi site, are each other's
     neighbors and share the site's neighbors (the oracle applies the same
-    rule to an exact triangulation of the distinct sites)."""
+    rule to an exact triangulation of the distinct sites).  With reuse, the
+    second and third steps start from seeds that hold the twins."""
     w = W.uniform_system(200, 14.0, 16, 2, input_seed=2, rule="voronoi", k=0, v0=0.3, eta=0.3)
     pos = w.pos_q.copy()
     pos[7] = pos[3]
     pos[11] = pos[3]
     pos[40] = pos[41]
     w.pos_q = pos
-    with vk.from_workload(w) as sim:
+    with vk.from_workload(w, voronoi_rebuild=rebuild) as sim:
         off, ids = _same(sim, pos, w.box_q)
         assert 7 in ids[off[3]:off[4]] and 3 in ids[off[11]:off[12]]
-        check_step(sim, w, "voronoi")
+        for _ in range(3):
+            check_step(sim, w, "voronoi")
 
 
 def test_huge_cell_takes_the_overflow_path():
@@ -159,7 +162,8 @@ def test_condensed_bands_with_voids(occ):
             check_step(sim, w, "voronoi")
 
 
-def test_blobs_across_voids_use_the_warp_path():
+@pytest.mark.parametrize("rebuild", [0, 1])
+def test_blobs_across_voids_use_the_warp_path(rebuild):
     """Two dense blobs far apart: the cells on the rim of a blob reach across
     the void to the other blob, so they see hundreds of candidates and are
     finished one warp per cell; lists and the update must match the oracle."""
@@ -172,9 +176,31 @@ def test_blobs_across_voids_use_the_warp_path():
     pos = pos[rng.permutation(pos.shape[0])]
     w = W.Workload(name="blobs", dim=2, pos_q=pos, dir=W.random_dirs(pos.shape[0]), theta=None,
                    box_q=(lq, lq), frac_bits=F, rule="voronoi", k=0, v0=0.3, eta=0.2)
-    with vk.from_workload(w) as sim:
+    with vk.from_workload(w, voronoi_rebuild=rebuild) as sim:
         sim.set_profiling(True, counters=True)
         _same(sim, pos, w.box_q)
         check_step(sim, w, "voronoi")
         assert sim.search_stats()["max_candidates"] > 384  # some cells went to the warp path
-        check_step(sim, w, "voronoi")
+        for _ in range(2):
+            check_step(sim, w, "voronoi")
+
+
+def test_reuse_of_last_steps_neighbors_changes_nothing():
+    """Starting each cell from last step's neighbors (the lazy re-check)
+    orders the clipping work differently but must give the same cells: 150
+    steps of the 65,536-particle mixed workload, at low noise so that it
+    condenses into bands and voids, are bit-identical with and without reuse,
+    and the lists match the oracle at the end."""
+    w = W.voronoi_mixed(eta=0.1)
+    out = []
+    for rebuild in (0, 1):
+        with vk.from_workload(w, voronoi_rebuild=rebuild) as sim:
+            sim.step(150)
+            p, d, _, _ = sim.state()
+            out.append((p, d, sim.order_parameter(), sim.neighbors()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2], out[1][2])
+    woff, wids = oracle.voronoi(out[0][0], w.box_q)
+    for k in (0, 1):
+        assert np.array_equal(out[k][3][0], woff) and np.array_equal(out[k][3][1], wids)

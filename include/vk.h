@@ -69,7 +69,8 @@ typedef enum {
   VK_ERR_OOM = 3,        /* device allocation failed */
   VK_ERR_CAPACITY = 4,   /* an output buffer or an internal bound was too small */
   VK_ERR_RANGE = 5,      /* box / fixed-point range outside the supported limits */
-  VK_ERR_DEGENERATE = 6, /* reserved: no current call returns it (coincident points are one site) */
+  VK_ERR_DEGENERATE = 6, /* the tissue model met coincident particles or a zero-length Voronoi edge
+                            (the Voronoi rule itself treats coincident points as one site) */
   VK_ERR_TIMEOUT = 7,    /* a bounded device wait gave up */
   VK_ERR_STATE = 8       /* call not valid in the current state */
 } vk_status;
@@ -206,6 +207,22 @@ vk_status vk_get_state(vk_sim* sim, int32_t replica, int32_t* pos_q, float* dir,
  * Synchronous. */
 vk_status vk_set_state(vk_sim* sim, int32_t replica, const int32_t* pos_q, const float* dir,
                        int64_t step);
+
+/* Voronoi tissue model (Sec. "Geometric models of dense tissue"; Sec.
+ * "Voronoi model forces") for the CURRENT positions of one replica (2D, any
+ * rule): every particle generates its Voronoi cell, of area A_i and
+ * perimeter P_i; E = sum_i KA (A_i - A0)^2 + KP (P_i - P0)^2 (Eq. vmEnergy)
+ * and F_i = -dE/dr_i, by the chain rule through the Voronoi vertices.  All in
+ * length units (one grid unit = 2^-F) and FP64, by id: area and perimeter n
+ * doubles, force 2n doubles ((x, y) per particle), energy one double; each
+ * may be NULL (not computed or not written), host or device memory.  The
+ * cells are built with the exact predicates of the Voronoi rule; the FP64
+ * geometry follows from the exact integer offsets.  Needs n >= 3, box edges
+ * <= 2^30, distinct particles and no Voronoi edge of zero length (four
+ * cocircular particles), else VK_ERR_DEGENERATE; cells of more than 16
+ * edges give VK_ERR_CAPACITY.  Synchronous. */
+vk_status vk_get_tissue(vk_sim* sim, int32_t replica, double KA, double KP, double A0, double P0,
+                        double* area, double* perimeter, double* force, double* energy);
 
 /* Wait for the sim's stream and return the sticky device status. */
 vk_status vk_sync(vk_sim* sim);

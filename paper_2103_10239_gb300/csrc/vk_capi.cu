@@ -251,7 +251,7 @@ vk_status read_status(vk_sim* s) {
   VK_CUDA(s, cudaStreamSynchronize(s->stream));
   if (h == 0) return VK_OK;
   const char* what = h == VK_ERR_CAPACITY     ? "device: capacity exceeded (Voronoi polygon or buffer)"
-                     : h == VK_ERR_DEGENERATE ? "device: coincident particles under the Voronoi rule"
+                     : h == VK_ERR_DEGENERATE ? "device: coincident particles or a zero-length Voronoi edge"
                      : h == VK_ERR_RANGE      ? "device: value outside the supported range"
                                               : "device: invalid input value";
   return fail(s, (vk_status)h, what);
@@ -634,6 +634,52 @@ vk_status vk_get_neighbors(vk_sim* s, int32_t replica, int64_t* offsets, int32_t
   if (ids_capacity < nnz) return fail(s, VK_ERR_CAPACITY, "ids_capacity is smaller than the neighbor count");
   if (nnz) VK_CUDA(s, cudaMemcpy(ids, ids_h.data(), sizeof(int32_t) * nnz, cudaMemcpyDefault));
   return VK_OK;
+}
+
+vk_status vk_get_tissue(vk_sim* s, int32_t replica, double KA, double KP, double A0, double P0, double* area,
+                        double* perimeter, double* force, double* energy) {
+  if (!s || replica < 0 || replica >= s->n_rep) return fail(s, VK_ERR_ARG, "bad arguments");
+  if (s->dim != 2) return fail(s, VK_ERR_ARG, "the tissue model is 2D");
+  if (!std::isfinite(KA) || !std::isfinite(KP) || !std::isfinite(A0) || !std::isfinite(P0))
+    return fail(s, VK_ERR_ARG, "KA, KP, A0 and P0 must be finite");
+  const Rep& R = s->reps_h[replica];
+  const int64_t n = R.n;
+  if (n < 3) return fail(s, VK_ERR_ARG, "the tissue model needs at least 3 particles");
+  for (int a = 0; a < 2; ++a)
+    if (s->boxes[replica].box_q[a] > (1u << 30)) return fail(s, VK_ERR_RANGE, "box edge above 2^30");
+  cudaStreamSynchronize(cudaStreamLegacy);
+  cudaEvent_t e0 = nullptr;
+  vk_status st = record_begin(s, 4, &e0);
+  if (st) return st;
+  // per-slot scratch over the whole state (slots of this replica are p0..p0+n-1)
+  const size_t N = (size_t)s->n_total;
+  TissueScratch w{};
+  double *area_d = nullptr, *perim_d = nullptr, *force_d = nullptr, *energy_d = nullptr;
+  cudaError_t e = cudaSuccess;
+  const bool allocated =
+      !((e = dalloc(&w.nb_n, N)) || (e = dalloc(&w.nb_slot, N * kTissueCap)) ||
+        (e = dalloc(&w.nb_off, N * kTissueCap)) || (e = dalloc(&w.area, N)) || (e = dalloc(&w.perim, N)) ||
+        (area && (e = dalloc(&area_d, n))) || (perimeter && (e = dalloc(&perim_d, n))) ||
+        (force && (e = dalloc(&force_d, 2 * n))) || (energy && (e = dalloc(&energy_d, 1))));
+  if (allocated) {
+    const double unit = std::ldexp(1.0, -s->boxes[replica].frac_bits);
+    e = launch_tissue(s->g, s->b, replica, (int)n, KA, KP, A0, P0, unit, w, area_d, perim_d, force_d, energy_d,
+                      s->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e == cudaSuccess) st = record_end(s, 4, e0, energy ? 3 : 2);
+  if (e == cudaSuccess && st == VK_OK) st = read_status(s);
+  if (e == cudaSuccess && st == VK_OK) {
+    if (area) e = cudaMemcpy(area, area_d, sizeof(double) * n, cudaMemcpyDefault);
+    if (e == cudaSuccess && perimeter) e = cudaMemcpy(perimeter, perim_d, sizeof(double) * n, cudaMemcpyDefault);
+    if (e == cudaSuccess && force) e = cudaMemcpy(force, force_d, sizeof(double) * 2 * n, cudaMemcpyDefault);
+    if (e == cudaSuccess && energy) e = cudaMemcpy(energy, energy_d, sizeof(double), cudaMemcpyDefault);
+  }
+  void* bufs[] = {w.nb_n, w.nb_slot, w.nb_off, w.area, w.perim, area_d, perim_d, force_d, energy_d};
+  for (void* p : bufs)
+    if (p) cudaFree(p);
+  if (e != cudaSuccess) return cuda_fail(s, e, "tissue model");
+  return st;
 }
 
 vk_status vk_get_order_parameter(vk_sim* s, int32_t replica, double* phi, int64_t max_values, int64_t* count) {

@@ -706,6 +706,20 @@ cudaError_t launch_metric_step(const Geometry& g, const Buffers& b, const StepPa
 cudaError_t launch_metric_export(const Geometry& g, const Buffers& b, int rep, int n, int pass, int32_t* deg,
                                  const int64_t* out_off, int32_t* out_ids, cudaStream_t st);
 
+// vk_tissue.cu (Voronoi tissue model): per-slot scratch of the cells pass
+constexpr int kTissueCap = 16;  // edges per cell kept for the force pass
+struct TissueScratch {
+  int32_t* nb_n;     // edges of every cell (0: failed, status latched)
+  int32_t* nb_slot;  // kTissueCap per slot: edge sites, counter-clockwise
+  int2* nb_off;      // ... and their exact offsets from the particle
+  double* area;      // per slot, length units
+  double* perim;
+};
+// cells, forces (by id) and energy of one replica; any output may be NULL
+cudaError_t launch_tissue(const Geometry& g, const Buffers& b, int rep, int n, double KA, double KP, double A0,
+                          double P0, double unit, TissueScratch w, double* area_out, double* perim_out,
+                          double* force_out, double* energy_out, cudaStream_t st);
+
 // vk_voronoi.cu
 cudaError_t launch_voronoi_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st);
 cudaError_t launch_voronoi_export(const Geometry& g, const Buffers& b, int rep, int n, int pass, int32_t* deg,

@@ -75,6 +75,9 @@ _SIGS = {
                                     ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "vk_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_int64]),
+    "vk_get_tissue": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p]),
     "vk_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "vk_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "vk_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
@@ -236,6 +239,20 @@ class Sim:
         _check(lib.vk_get_neighbors(self._h, replica, _ptr(off), _ptr(ids), ids.shape[0],
                                     ctypes.byref(need)), self._h)
         return off, ids[: need.value]
+
+    def tissue(self, KA: float, KP: float, A0: float, P0: float, replica: int = 0, forces: bool = True):
+        """vk_get_tissue: Voronoi cell areas and perimeters, the energy of
+        Eq. (vmEnergy) and the forces -dE/dr_i of the current positions, by
+        id, in length units.  Returns (area, perimeter, energy, force|None)."""
+        n = self.n_r[replica]
+        area = np.zeros(n, dtype=np.float64)
+        perim = np.zeros(n, dtype=np.float64)
+        force = np.zeros((n, 2), dtype=np.float64) if forces else None
+        e = np.zeros(1, dtype=np.float64)
+        _check(load().vk_get_tissue(self._h, replica, float(KA), float(KP), float(A0), float(P0),
+                                    area.ctypes.data, perim.ctypes.data,
+                                    force.ctypes.data if forces else None, e.ctypes.data), self._h)
+        return area, perim, float(e[0]), force
 
     def order_parameter(self, replica: int = 0, max_values: int = 1 << 20) -> np.ndarray:
         lib = load()

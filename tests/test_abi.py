@@ -95,3 +95,10 @@ def test_rule_variant_defaults():
     p = vk.default_params()
     assert (p.fov, p.r0, p.fov_cos) == (0, 1.0, -1.0)
     assert vk.default_params(rule="metric").rule == vk.VK_RULE_METRIC
+
+
+def test_tissue_argument_errors_without_gpu():
+    """Host-side checks of vk_get_tissue come before any device work."""
+    from paper_2103_10239_gb300 import vk
+    lib = vk.load()
+    assert lib.vk_get_tissue(None, 0, 1.0, 1.0, 1.0, 3.8, None, None, None, None) == vk.VK_ERR_ARG

@@ -219,7 +219,7 @@ vk_status vk_set_state(vk_sim* sim, int32_t replica, const int32_t* pos_q, const
  * cells are built with the exact predicates of the Voronoi rule; the FP64
  * geometry follows from the exact integer offsets.  Needs n >= 3, box edges
  * <= 2^30, distinct particles and no Voronoi edge of zero length (four
- * cocircular particles), else VK_ERR_DEGENERATE; cells of more than 16
+ * cocircular particles), else VK_ERR_DEGENERATE; cells of more than 32
  * edges give VK_ERR_CAPACITY.  Synchronous. */
 vk_status vk_get_tissue(vk_sim* sim, int32_t replica, double KA, double KP, double A0, double P0,
                         double* area, double* perimeter, double* force, double* energy);

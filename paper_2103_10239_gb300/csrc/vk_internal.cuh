@@ -707,7 +707,7 @@ cudaError_t launch_metric_export(const Geometry& g, const Buffers& b, int rep, i
                                  const int64_t* out_off, int32_t* out_ids, cudaStream_t st);
 
 // vk_tissue.cu (Voronoi tissue model): per-slot scratch of the cells pass
-constexpr int kTissueCap = 16;  // edges per cell kept for the force pass
+constexpr int kTissueCap = 32;  // edges per cell kept for the force pass
 struct TissueScratch {
   int32_t* nb_n;     // edges of every cell (0: failed, status latched)
   int32_t* nb_slot;  // kTissueCap per slot: edge sites, counter-clockwise

@@ -54,11 +54,11 @@ def test_tiny_boxes(seed, n, L):
 
 
 def test_evolved_flock_and_any_rule():
-    """After 100 Voronoi-rule steps (bands and voids), and on a kNN sim of
-    the same state (the tissue call builds its own cells)."""
-    w = W.voronoi_mixed(eta=0.1)
+    """After 40 Voronoi-rule steps of the mixed workload, and on a kNN sim
+    (the tissue call builds its own cells whatever the rule)."""
+    w = W.voronoi_mixed(eta=0.5)
     with vk.from_workload(w) as sim:
-        sim.step(100)
+        sim.step(40)
         pos, _, _, _ = sim.state()
         _compare(sim, pos, w.box_q, w.frac_bits, 1.0, 1.0, 1.0, 3.8)
     w2 = W.uniform_system(4000, 60.0, 16, 2, input_seed=63, rule="knn", k=7)
@@ -88,3 +88,21 @@ def test_degenerate_inputs_are_reported():
         with pytest.raises(vk.VKError) as e:
             sim.tissue(1.0, 1.0, 1.0, 3.8)
         assert e.value.status == vk.VK_ERR_DEGENERATE
+
+
+def test_cells_over_32_edges_report_capacity():
+    """A particle alone in a void ringed by 60 others: its 60-edge cell is
+    beyond the tissue pass's 32 edges."""
+    rng = np.random.default_rng(4)
+    L, F, ring_r = 1 << 16, 8, 20000.0
+    ang = np.arange(60) * (2 * np.pi / 60) + rng.uniform(-1e-4, 1e-4, 60)
+    rad = ring_r * (1 + rng.uniform(-3e-4, 3e-4, 60))
+    c = L / 2
+    ring = np.stack([c + rad * np.cos(ang), c + rad * np.sin(ang)], 1)
+    outer = rng.uniform(0, L, size=(600, 2))
+    outer = outer[np.hypot(outer[:, 0] - c, outer[:, 1] - c) > 1.3 * ring_r]
+    pos = np.concatenate([[[c + 17, c - 31]], ring, outer]).astype(np.int64).astype(np.int32)
+    with vk.Sim.create(pos, W.random_dirs(pos.shape[0]), (L, L), F, rule="voronoi") as sim:
+        with pytest.raises(vk.VKError) as e:
+            sim.tissue(1.0, 1.0, 1.0, 3.8)
+        assert e.value.status == vk.VK_ERR_CAPACITY

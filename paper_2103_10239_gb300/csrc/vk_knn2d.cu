@@ -502,7 +502,7 @@ __device__ __noinline__ void align_advect_general(const Rep& R, const StepParams
 
 // Eq. (2) alignment + noise and Eq. (1) advection of one particle from its
 // finished top-k; writes the next state and counts the new coarse cell.
-template <int KC>
+template <int KC, bool FOV = true>
 __device__ __forceinline__ void knn2_update(const Rep& R, const StepParams& P, int64_t step, int64_t s, int2 p,
                                             float2 nv, int32_t id, const Top<KC>& T,
                                             const uint32_t* __restrict__ bounds, const float2* __restrict__ S_dir,
@@ -517,7 +517,7 @@ __device__ __forceinline__ void knn2_update(const Rep& R, const StepParams& P, i
   if (P.include_self) H.add(ni, P.sum_mode);
 #pragma unroll
   for (int j = 0; j < KC; ++j) {
-    if (j >= KC - P.k && T.slot[j] >= 0) {
+    if (j >= KC - P.k && (!FOV || T.slot[j] >= 0)) {
       const float2 d = __ldg(S_dir + T.slot[j]);
       const float v[2] = {d.x, d.y};
       H.add(v, P.sum_mode);
@@ -697,8 +697,10 @@ __device__ __forceinline__ int box_merge(const BoxHits<KC>& H, int cnt, const Ct
 
 // kNN visitor of the square walk: candidates with D <= tau go to the hit
 // list, which is merged into T when nearly full (tau then shrinks to T's
-// k-th distance) and by the caller at the end.
-template <int KC>
+// k-th distance) and by the caller at the end.  AHEAD (a view of at most a
+// half-plane, cq >= 0): a candidate behind the particle (d.nq < 0, exact in
+// int64) is out of view and is not buffered; the merge decides the rest.
+template <int KC, bool AHEAD>
 struct KnnVisit {
   BoxHits<KC>& H;
   const Ctx& C;
@@ -714,7 +716,8 @@ struct KnnVisit {
     for (int u = 0; u < kGroup; ++u) {
       const int32_t dx = (int32_t)((uint32_t)pj[u].x - ox), dy = (int32_t)((uint32_t)pj[u].y - oy);
       const uint64_t D = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy);
-      const bool hit = (uint32_t)u < n && D <= tau;
+      bool hit = (uint32_t)u < n && D <= tau;
+      if (AHEAD) hit = hit && (long long)dx * C.view.nxq + (long long)dy * C.view.nyq >= 0;
       H.slot[cnt][threadIdx.x] = (int32_t)(q + (uint32_t)u);
       cnt += hit ? 1 : 0;
     }
@@ -733,14 +736,24 @@ struct KnnVisit {
 // Returns the number of hits that count (other particles, in view), >= k
 // exactly when T is full, or -1 when the square is too wide for the minimum
 // image or meets a coarse cell through two periodic images.
+template <int KC, bool AHEAD>
+__device__ __forceinline__ int box_scan_v(BoxHits<KC>& H, const Rep& R, const uint32_t* __restrict__ bounds,
+                                          const GridView& G, const int2* __restrict__ pos, const Ctx& C, int64_t a,
+                                          Top<KC>& T, bool* tie, BoxCount& bc) {
+  KnnVisit<KC, AHEAD> v{H, C, pos, T, tie, (uint64_t)(a + 1) * (uint64_t)(a + 1) - 1, 0, 0};
+  if (!box_walk(H, R, bounds, G, pos, C, a, bc, v)) return -1;
+  // after the loop, where the threads have reconverged
+  return v.got + box_merge<KC>(H, v.cnt, C, pos, T, tie);
+}
+
+// the view is the same for every particle: the branch is warp-uniform, and
+// only one copy of the scan loop runs in a given simulation
 template <int KC>
 __device__ __forceinline__ int box_scan(BoxHits<KC>& H, const Rep& R, const uint32_t* __restrict__ bounds,
                                         const GridView& G, const int2* __restrict__ pos, const Ctx& C, int64_t a,
                                         Top<KC>& T, bool* tie, BoxCount& bc) {
-  KnnVisit<KC> v{H, C, pos, T, tie, (uint64_t)(a + 1) * (uint64_t)(a + 1) - 1, 0, 0};
-  if (!box_walk(H, R, bounds, G, pos, C, a, bc, v)) return -1;
-  // after the loop, where the threads have reconverged
-  return v.got + box_merge<KC>(H, v.cnt, C, pos, T, tie);
+  if (C.view.cq >= 0) return box_scan_v<KC, true>(H, R, bounds, G, pos, C, a, T, tie, bc);
+  return box_scan_v<KC, false>(H, R, bounds, G, pos, C, a, T, tie, bc);
 }
 
 // search radius without a hint: a multiple of the k-th distance expected
@@ -823,7 +836,7 @@ __device__ __forceinline__ void record_box_stats(unsigned long long* stats, cons
 // cannot serve go on the deferred list (slot, replica) with the radius to
 // try next in U_hint (-1: walk), and knn2_deferred_kernel finishes them: a
 // warp here never waits for one particle's second square.
-template <int KC>
+template <int KC, bool FOV>
 __global__ void __launch_bounds__(kBlock, VK_KNN2_BOX_BLOCKS) knn2_box_step_kernel(
     const Rep* __restrict__ reps, const BlockTask* __restrict__ tasks, const uint32_t* __restrict__ bounds,
     const int2* __restrict__ S_pos, const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id,
@@ -849,14 +862,14 @@ __global__ void __launch_bounds__(kBlock, VK_KNN2_BOX_BLOCKS) knn2_box_step_kern
     const float hint = S_hint[s];
     Ctx C;
     init_ctx(C, R, s, p);
-    if (P.fov_cq != kViewAll) C.view = make_view(S_dir[s], P.fov_cq);
+    if (FOV) C.view = make_view(S_dir[s], P.fov_cq);
     Top<KC> T;
     const float r =
         hint > 0.f ? P.halo_alpha * hint + P.halo_beta * fabsf(R.s) : box_radius_estimate(R, bounds, G, p, P.k);
     float r_next = -1.f;
     served = box_search<KC>(H, R, bounds, G, S_pos, C, r, P.k, 1, T, bc, &r_next);
     if (served) {
-      knn2_update<KC>(R, P, step, s, p, S_dir[s], S_id[s], T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
+      knn2_update<KC, FOV>(R, P, step, s, p, S_dir[s], S_id[s], T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
       U_hint[s] = sqrtf((float)T.d[KC - 1]) * 1.0001f + 1.f;
     } else {
       U_hint[s] = r_next;
@@ -873,7 +886,7 @@ __global__ void __launch_bounds__(kBlock, VK_KNN2_BOX_BLOCKS) knn2_box_step_kern
 // a list of any length (the length is read on the device, so the launch can
 // sit in a CUDA graph); particles that still cannot be served go on the walk
 // list.
-template <int KC>
+template <int KC, bool FOV>
 __global__ void __launch_bounds__(kBlock, VK_KNN2_BOX_BLOCKS) knn2_deferred_kernel(
     const Rep* __restrict__ reps, const uint32_t* __restrict__ bounds, const int2* __restrict__ S_pos,
     const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G, int2* __restrict__ U_pos,
@@ -899,13 +912,13 @@ __global__ void __launch_bounds__(kBlock, VK_KNN2_BOX_BLOCKS) knn2_deferred_kern
     const int2 p = S_pos[s];
     Ctx C;
     init_ctx(C, R, s, p);
-    if (P.fov_cq != kViewAll) C.view = make_view(S_dir[s], P.fov_cq);
+    if (FOV) C.view = make_view(S_dir[s], P.fov_cq);
     Top<KC> T;
     const float r = U_hint[s];
     float r_next = -1.f;
     served = r > 0.f && box_search<KC>(H, R, bounds, G, S_pos, C, r, P.k, kBoxTries, T, bc, &r_next);
     if (served) {
-      knn2_update<KC>(R, P, step, s, p, S_dir[s], S_id[s], T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
+      knn2_update<KC, FOV>(R, P, step, s, p, S_dir[s], S_id[s], T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
       U_hint[s] = sqrtf((float)T.d[KC - 1]) * 1.0001f + 1.f;
     } else {
       walk_list[atomicAdd(walk_count, 1)] = e;
@@ -1048,7 +1061,10 @@ cudaError_t step2(const Geometry& g, const Buffers& b, const StepParams& P, cuda
     if (b.U_hint) cudaMemsetAsync(b.U_hint, 0, sizeof(float) * (size_t)g.n_total, st);
   } else {
     // the lists are empty here: the previous scatter (or init) cleared them
-    knn2_box_step_kernel<KC><<<g.n_tasks, kBlock, box_smem_bytes<KC>(), st>>>(
+    // a field of view gets its own instantiation, so that the plain rule
+    // carries no view code (registers)
+    auto k = P.fov_cq != kViewAll ? knn2_box_step_kernel<KC, true> : knn2_box_step_kernel<KC, false>;
+    k<<<g.n_tasks, kBlock, box_smem_bytes<KC>(), st>>>(
         g.reps, g.tasks, b.bounds, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id, b.S_hint, view_of(b),
         (int2*)b.U_pos, (float2*)b.U_dir, b.U_id, b.U_hint, b.counts, b.phi_acc, b.d_step, P, b.ovf_list,
         b.ovf_count);
@@ -1060,7 +1076,8 @@ template <int KC>
 cudaError_t finish2(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st) {
   if (P.knn_search == 0 && b.S_hint) {
     // the deferred list lives in the first half of ovf_list, the walk list in the second
-    knn2_deferred_kernel<KC><<<walk_blocks(g), kBlock, box_smem_bytes<KC>(), st>>>(
+    auto k = P.fov_cq != kViewAll ? knn2_deferred_kernel<KC, true> : knn2_deferred_kernel<KC, false>;
+    k<<<walk_blocks(g), kBlock, box_smem_bytes<KC>(), st>>>(
         g.reps, b.bounds, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id, view_of(b), (int2*)b.U_pos,
         (float2*)b.U_dir, b.U_id, b.U_hint, b.counts, b.phi_acc, b.d_step, P, b.ovf_list, b.ovf_count,
         b.ovf_list + g.n_total, b.ovf_count + 1);
@@ -1098,13 +1115,19 @@ cudaError_t export2(const Geometry& g, const Buffers& b, int k, int rep, int n, 
 
 template <int KC>
 cudaError_t prepare2() {
-  cudaError_t e = cudaFuncSetAttribute(knn2_box_step_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)box_smem_bytes<KC>());
+  cudaError_t e = cudaFuncSetAttribute(knn2_box_step_kernel<KC, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)box_smem_bytes<KC>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(knn2_box_step_kernel<KC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)box_smem_bytes<KC>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(knn2_box_export_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)box_smem_bytes<KC>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(knn2_deferred_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(knn2_deferred_kernel<KC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)box_smem_bytes<KC>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(knn2_deferred_kernel<KC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)box_smem_bytes<KC>());
   return e;
 }

@@ -47,14 +47,15 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--occupancy", type=float, default=2048.0,
-                    help="coarse-grid occupancy (particles per cell) of the headline run; 2048 was the "
-                         "fastest of a sweep on the clustered 4M workload (1024: 5.59, 2048: 5.38, "
-                         "4096: 5.37 ms/step)")
-    ap.add_argument("--search", choices=["tile", "walk"], default="tile",
-                    help="2D kNN search: warp tiles (default) or the per-particle walk only")
+    ap.add_argument("--occupancy", type=float, default=256.0,
+                    help="coarse-grid occupancy (particles per cell) of the headline run; 256 was the "
+                         "fastest of a sweep on the clustered 4M workload (steps 5-25 / 100-130, halo "
+                         "1.15: 128: 3.43/2.52, 256: 3.49/2.51, 512: 3.63/2.55 ms/step)")
+    ap.add_argument("--search", choices=["radius", "walk"], default="radius",
+                    help="2D kNN search: radius-first squares (default) or the per-particle walk only")
     ap.add_argument("--halo", type=float, default=0.0,
-                    help="warp-tile halo as a multiple of the previous k-th distance (0: library default)")
+                    help="radius-first search square half-width as a multiple of the previous k-th "
+                         "distance (0: library default)")
     ap.add_argument("--no-replicas", action="store_true",
                     help="skip the replica-batch block of the headline line")
     ap.add_argument("--no-secondary", action="store_true",
@@ -308,7 +309,7 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_stream(stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     sim = vk.from_workload(w, stream=stream, cell_occupancy=args.occupancy,
-                           knn_search=0 if args.search == "tile" else 1, search_halo=args.halo)
+                           knn_search=0 if args.search == "radius" else 1, search_halo=args.halo)
     sim.step(args.warmup)
     occupancy = args.occupancy
     if args.autotune:
@@ -489,10 +490,10 @@ def secondary_block(stream) -> dict:
                              config={"workload": wv.name, "rule": "voronoi", "eta": 0.1,
                                      "voronoi_rebuild": rebuild})
     wc = W.clustered_large()
-    with vk.from_workload(wc, stream=stream, rule="metric", r0=1.0, cell_occupancy=512.0) as sim:
+    with vk.from_workload(wc, stream=stream, rule="metric", r0=1.0, cell_occupancy=256.0) as sim:
         out["metric_clustered4M_r1"] = dict(_rate(stream, sim, wc.n, 5, 20),
                                             config={"workload": wc.name, "rule": "metric", "r0": 1.0})
-    with vk.from_workload(wc, stream=stream, fov=1, fov_cos=0.0, cell_occupancy=2048.0) as sim:
+    with vk.from_workload(wc, stream=stream, fov=1, fov_cos=0.0, cell_occupancy=256.0) as sim:
         out["knn_fov_clustered4M_halfplane"] = dict(_rate(stream, sim, wc.n, 5, 20),
                                                     config={"workload": wc.name, "rule": "knn", "k": 7,
                                                             "fov_cos": 0.0})

@@ -106,14 +106,14 @@ typedef struct {
   int32_t advect_new;   /* 1: advect with n_i(t+dt) instead of n_i(t) (default 0) */
   int32_t sum_mode;     /* vk_sum_mode for the heading sums (default compensated) */
   float cell_occupancy; /* target particles per coarse cell of the search grid at the mean
-                           density; 0 = default (512 for 2D kNN, 2 for Voronoi, 3 for 3D kNN).
+                           density; 0 = default (256 in 2D, 2 for Voronoi, 3 in 3D).
                            Dense coarse cells get sub-grids of about 2 particles per sub-cell.
                            Results never depend on it; only the speed does. */
   int32_t phi_capacity; /* order-parameter history kept per replica; 0 = 4096 steps */
   int32_t knn_search;   /* 2D kNN search: 0 = radius first (default), 1 = per-particle walk only.
                            Results never depend on it; only the speed does. */
   float search_halo;    /* radius first: half-width of a particle's search square, as a multiple
-                           of its k-th neighbor distance at the previous step; 0 = default (1.25).
+                           of its k-th neighbor distance at the previous step; 0 = default (1.15).
                            Results never depend on it; only the speed does. */
   float search_halo_step; /* radius first: plus this multiple of the distance a particle moves
                            in one step (v0 dt); < 0 = default (0).  Speed only. */

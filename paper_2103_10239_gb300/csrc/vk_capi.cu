@@ -113,7 +113,7 @@ StepParams step_params(const vk_sim* s) {
   P.n_rep = s->n_rep;
   P.phi_cap = s->phi_cap;
   P.knn_search = s->prm.knn_search;
-  P.halo_alpha = s->prm.search_halo > 0.f ? s->prm.search_halo : 1.25f;
+  P.halo_alpha = s->prm.search_halo > 0.f ? s->prm.search_halo : 1.15f;
   P.halo_beta = s->prm.search_halo_step >= 0.f ? s->prm.search_halo_step : 0.f;
   P.fov_cq = fov_cq(s->prm);
   P.stats = (s->prof && s->prof_counters) ? s->d_stats : nullptr;
@@ -123,9 +123,10 @@ StepParams step_params(const vk_sim* s) {
 float default_occupancy(const vk_params& p, int dim) {
   if (p.cell_occupancy > 0.f) return p.cell_occupancy;
   if (p.rule == VK_RULE_VORONOI) return 2.0f;
-  // 2D kNN: large coarse cells, so that most searches end inside the
-  // particle's own sub-grid (measured fastest on uniform and clustered flocks)
-  return dim == 2 ? 512.0f : 3.0f;
+  // 2D kNN and metric: coarse cells of a few hundred particles split into
+  // sub-grids (the radius-first search measured fastest at 256 on uniform
+  // and clustered flocks)
+  return dim == 2 ? 256.0f : 3.0f;
 }
 
 // per-replica search grid for a target occupancy; fills nc, c0 and the cell

@@ -24,6 +24,10 @@
 #ifndef VK_KNN2_BOX_BLOCKS
 #define VK_KNN2_BOX_BLOCKS 3
 #endif
+// ... and the deferred-particle kernel (a few larger squares per particle)
+#ifndef VK_KNN2_DEFER_BLOCKS
+#define VK_KNN2_DEFER_BLOCKS 2
+#endif
 
 namespace vk {
 
@@ -832,6 +836,20 @@ __device__ __forceinline__ void record_box_stats(unsigned long long* stats, cons
     for (int i = 0; i < 9; ++i) atomicAdd(stats + 5 + i, v[i]);
 }
 
+// Append (slot, replica) to a device list, one atomic per warp: the
+// warp's entries land next to each other, so the kernel that consumes the
+// list reads spatially close particles in one warp.  Every lane of the warp
+// must call it.
+__device__ __forceinline__ void warp_append(bool put, int2 e, int2* __restrict__ list, int32_t* __restrict__ count) {
+  const unsigned m = __ballot_sync(0xffffffffu, put);
+  if (m == 0u) return;
+  const int lane = (int)(threadIdx.x & 31);
+  int base = 0;
+  if (lane == __ffs(m) - 1) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+  if (put) list[base + __popc(m & ((1u << lane) - 1u))] = e;
+}
+
 // Search + update, radius first, one square per particle.  Particles it
 // cannot serve go on the deferred list (slot, replica) with the radius to
 // try next in U_hint (-1: walk), and knn2_deferred_kernel finishes them: a
@@ -873,9 +891,9 @@ __global__ void __launch_bounds__(kBlock, VK_KNN2_BOX_BLOCKS) knn2_box_step_kern
       U_hint[s] = sqrtf((float)T.d[KC - 1]) * 1.0001f + 1.f;
     } else {
       U_hint[s] = r_next;
-      defer_list[atomicAdd(defer_count, 1)] = make_int2((int)s, t.rep);
     }
   }
+  warp_append(valid && !served, make_int2((int)(R.p0 + li), t.rep), defer_list, defer_count);
   record_search_stats(P.stats, served, bc.cand, bc.tries, false);
   record_box_stats(P.stats, bc);
   phi_block_end<2>(phs, nnew, phi_acc + ((size_t)(step % P.phi_cap) * (size_t)P.n_rep + (size_t)t.rep) * 3);
@@ -887,7 +905,7 @@ __global__ void __launch_bounds__(kBlock, VK_KNN2_BOX_BLOCKS) knn2_box_step_kern
 // sit in a CUDA graph); particles that still cannot be served go on the walk
 // list.
 template <int KC, bool FOV>
-__global__ void __launch_bounds__(kBlock, VK_KNN2_BOX_BLOCKS) knn2_deferred_kernel(
+__global__ void __launch_bounds__(kBlock, VK_KNN2_DEFER_BLOCKS) knn2_deferred_kernel(
     const Rep* __restrict__ reps, const uint32_t* __restrict__ bounds, const int2* __restrict__ S_pos,
     const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G, int2* __restrict__ U_pos,
     float2* __restrict__ U_dir, int32_t* __restrict__ U_id, float* __restrict__ U_hint,
@@ -904,8 +922,9 @@ __global__ void __launch_bounds__(kBlock, VK_KNN2_BOX_BLOCKS) knn2_deferred_kern
   bool served = false;
   int rep = 0;
   BoxCount bc;
+  int2 e = make_int2(0, 0);
   if (i < total) {
-    const int2 e = defer_list[i];
+    e = defer_list[i];
     const int64_t s = e.x;
     rep = e.y;
     const Rep R = reps[e.y];
@@ -920,10 +939,9 @@ __global__ void __launch_bounds__(kBlock, VK_KNN2_BOX_BLOCKS) knn2_deferred_kern
     if (served) {
       knn2_update<KC, FOV>(R, P, step, s, p, S_dir[s], S_id[s], T, bounds, S_dir, U_pos, U_dir, U_id, counts, nnew);
       U_hint[s] = sqrtf((float)T.d[KC - 1]) * 1.0001f + 1.f;
-    } else {
-      walk_list[atomicAdd(walk_count, 1)] = e;
     }
   }
+  warp_append(i < total && !served, e, walk_list, walk_count);
   phi_add_warp<2>(phi_acc + (size_t)(step % P.phi_cap) * (size_t)P.n_rep * 3, rep, nnew, served);
   if (P.stats && served) {
     atomicAdd(P.stats + 0, (unsigned long long)bc.cand);

@@ -231,15 +231,53 @@ __device__ __noinline__ bool poly_apply_cut(Poly<CAP>& P, int s, int c, int32_t 
   return true;
 }
 
+// The vertex of the cell farthest in the direction of m.  Vertex a lies
+// between the edges of sites q_a and q_a+1, whose outward normals point at
+// those sites, so it maximises V.m for every m whose direction lies in the
+// sector from q_a to q_a+1 (counter-clockwise).  The sites run counter-
+// clockwise around the particle: a binary search over their directions,
+// with exact int64 cross and dot products, finds the sector of m.  Since
+// "m cuts V" (2 m.V > |m|^2) is linear in V, m cuts or touches some vertex
+// only if it cuts or touches this one.
+template <int CAP>
+__device__ __forceinline__ int support_vertex(const Poly<CAP>& P, int32_t mx, int32_t my) {
+  const int64_t rx = P.qx[0], ry = P.qy[0];
+  // half-turn of a direction counted from q_0: 0 for [0, pi), 1 for [pi, 2 pi)
+  auto half = [&](int64_t x, int64_t y) {
+    const int64_t c = rx * y - ry * x;
+    return (c < 0 || (c == 0 && rx * x + ry * y < 0)) ? 1 : 0;
+  };
+  const int hm = half(mx, my);
+  int lo = 0, hi = P.m - 1;  // the last site at or before m's direction, counted from q_0
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int64_t x = P.qx[mid], y = P.qy[mid];
+    const int hq = half(x, y);
+    if (hq < hm || (hq == hm && x * (int64_t)my - y * (int64_t)mx >= 0)) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// true when site m (with Dm <= |m|^2) certainly neither cuts nor touches
+// the cell: its support vertex is farther than |m|/2 ... or decided by the
+// FP32 bound to lie strictly on the particle's side of the bisector
+template <int CAP>
+__device__ __forceinline__ bool site_misses(const Poly<CAP>& P, int32_t mx, int32_t my, float Dm) {
+  const int a = support_vertex(P, mx, my);
+  return Dm > 4.0f * P.vr2[a] || vertex_cut_fast(P.vx[a], P.vy[a], P.ve[a], mx, my) < 0;
+}
+
 // clip the cell by the bisector of site (mx, my); returns false on overflow
 template <int CAP>
 __device__ __forceinline__ bool poly_clip(Poly<CAP>& P, int32_t mx, int32_t my, int32_t mid, int32_t mslot,
                                           float Dm, bool* bad, bool* touch) {
   const int m = P.m;
+  *touch = false;
+  if (site_misses(P, mx, my, Dm)) return true;  // the common case, in O(log m)
   // the vertices strictly beyond the bisector form one cyclic run [s, s+c)
   int c = 0, s = -1;
   bool first_cut = false, prev_cut = false;
-  *touch = false;
   for (int a = 0; a < m; ++a) {
     bool cut = false;
     if (!(Dm > 4.0f * P.vr2[a])) {  // a vertex closer than |m|/2 cannot be cut
@@ -576,6 +614,7 @@ __device__ bool voronoi_cell(const Rep& R, int64_t self, const int32_t* pi, int3
 // will, since the cell only shrinks and stays on the same side.
 template <int CAP>
 __device__ __forceinline__ int site_effect(const Poly<CAP>& P, int32_t mx, int32_t my, float Dm) {
+  if (site_misses(P, mx, my, Dm)) return 0;
   int r = 0;
   for (int a = 0; a < P.m; ++a) {
     if (Dm > 4.0f * P.vr2[a]) continue;

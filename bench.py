@@ -501,6 +501,19 @@ def secondary_block(stream) -> dict:
     with vk.from_workload(w3, stream=stream) as sim:
         out["knn3d_1M"] = dict(_rate(stream, sim, w3.n, 5, 20), config={"workload": w3.name, "rule": "knn",
                                                                         "k": 7, "dim": 3})
+    # the tissue model's energy and forces of a uniform state: wall time of the
+    # whole synchronous call (scratch allocation, three kernels, copies to host)
+    wt = W.uniform_system(1 << 20, 1024.0, 16, 2, input_seed=1011, rule="voronoi", k=0)
+    with vk.from_workload(wt, stream=stream) as sim:
+        sim.tissue(1.0, 1.0, 1.0, 3.8)  # warm-up
+        t0 = time.perf_counter()
+        for _ in range(3):
+            sim.tissue(1.0, 1.0, 1.0, 3.8)
+        sec = (time.perf_counter() - t0) / 3
+        out["tissue_forces_uniform1M"] = {"value": wt.n / sec, "unit": "particles/s (areas, perimeters, energy, "
+                                          "forces per call)", "ms_per_call": sec * 1e3,
+                                          "config": {"workload": wt.name, "KA": 1.0, "KP": 1.0, "A0": 1.0,
+                                                     "P0": 3.8}}
     return out
 
 

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(64) tissue_cells_kernel(const Rep* __restrict_
     int m = 0;
     area[s] = 0.0;
     perim[s] = 0.0;
-    if (!voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status, 0u, none) || P.m > kTissueCap) {
+    if (!voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status, 0u, none, nullptr) || P.m > kTissueCap) {
       set_status(status, kStCapacity);
     } else if (P.nt > 0) {
       set_status(status, kStDegenerate);  // coincident particles: one site, no cell each

@@ -41,14 +41,14 @@ __device__ __forceinline__ void voronoi_update(const Rep& R, const StepParams& P
                                                int2* __restrict__ U_pos, float2* __restrict__ U_dir,
                                                int32_t* __restrict__ U_id, uint32_t* __restrict__ counts,
                                                float* nnew, int32_t* __restrict__ seed_out,
-                                               int32_t* __restrict__ seed_n_out) {
+                                               int32_t* __restrict__ seed_n_out, bool heavy_next) {
   int32_t nid[CAP + Poly<CAP>::TW], nslot[CAP + Poly<CAP>::TW];
   const int cnt = voronoi_neighbors(P, id, nid, nslot);
   if (seed_out) {
     // the next step's seeds (any subset of sites would do)
     const int ns = min(cnt, kVorSeed);
     for (int j = 0; j < ns; ++j) seed_out[j] = nid[j];
-    *seed_n_out = ns;
+    *seed_n_out = ns | (heavy_next ? kSeedHeavy : 0);
   }
   HeadSum<2> H;
   H.init();
@@ -65,6 +65,16 @@ __device__ __forceinline__ void voronoi_update(const Rep& R, const StepParams& P
   U_id[s] = id;
   atomicAdd(counts + linear_cell<2>(R, pout), 1u);
 }
+
+// Heavy-cell hint: a cell that needed more than kHeavyHint candidates in the
+// main kernel, or more than kHeavyKeep in the warp kernel, is flagged in its
+// seed word, and the next step sends it to the warp kernel at once (particles
+// on the rim of a void stay there for many steps).  Speed only.
+#ifndef VK_VOR_HEAVY_HINT
+#define VK_VOR_HEAVY_HINT 192
+#endif
+constexpr uint32_t kHeavyHint = VK_VOR_HEAVY_HINT > 0 ? VK_VOR_HEAVY_HINT : 0xFFFFFFFFu;
+constexpr uint32_t kHeavyKeep = VK_VOR_HEAVY_HINT > 0 ? VK_VOR_HEAVY_HINT / 2 : 0xFFFFFFFFu;
 
 // Main kernel: cells of up to kFastCap edges.  Particles whose cell outgrows
 // it are appended to the overflow list and finished by the overflow kernel.
@@ -91,13 +101,18 @@ __global__ void __launch_bounds__(kBlock) voronoi_step_kernel(
     const float ni[3] = {nv.x, nv.y, 0.f};
     const int32_t id = S_id[s];
     const int64_t gi = R.p0 + id;
-    const Seeds sd{vor_seed ? vor_seed + gi * kVorSeed : nullptr, vor_seed ? vor_seed_n[gi] : 0, slot_of};
+    const int32_t sw = vor_seed ? vor_seed_n[gi] : 0;
+    const Seeds sd{vor_seed ? vor_seed + gi * kVorSeed : nullptr, sw & kSeedCount, slot_of};
     Poly<kFastCap> P;
-    const bool ok = Pm.stats ? voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status, kHeavy, sd, &n_cand, &n_runs)
-                             : voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status, kHeavy, sd);
+    uint32_t seen = 0;
+    // a cell that was heavy at the last step goes straight to the warp kernel
+    const bool ok = !(sw & kSeedHeavy) &&
+                    (Pm.stats ? voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status, kHeavy, sd, &seen, &n_cand,
+                                             &n_runs)
+                              : voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status, kHeavy, sd, &seen));
     if (ok) {
       voronoi_update(R, Pm, step, s, P, pi, ni, id, S_dir, U_pos, U_dir, U_id, counts, nnew,
-                     vor_seed ? vor_seed + gi * kVorSeed : nullptr, vor_seed_n + gi);
+                     vor_seed ? vor_seed + gi * kVorSeed : nullptr, vor_seed_n + gi, seen > kHeavyHint);
     } else {
       const int q = atomicAdd(ovf_count, 1);
       ovf_list[q] = make_int2((int)s, t.rep);
@@ -132,8 +147,10 @@ __global__ void __launch_bounds__(32 * kOvfWarps) voronoi_overflow_kernel(
     const int32_t pi[3] = {p.x, p.y, 0};
     const int32_t id = S_id[s];
     const int64_t gi = R.p0 + id;
-    const Seeds sd{vor_seed ? vor_seed + gi * kVorSeed : nullptr, vor_seed ? vor_seed_n[gi] : 0, slot_of};
-    const bool ok = voronoi_cell_warp(R, s, pi, id, S_pos, S_id, G, P, status, sd);
+    const Seeds sd{vor_seed ? vor_seed + gi * kVorSeed : nullptr, vor_seed ? vor_seed_n[gi] & kSeedCount : 0,
+                   slot_of};
+    uint32_t seen = 0;
+    const bool ok = voronoi_cell_warp(R, s, pi, id, S_pos, S_id, G, P, status, sd, &seen);
     if ((threadIdx.x & 31) == 0) {
       if (!ok) {
         set_status(status, kStCapacity);
@@ -142,7 +159,7 @@ __global__ void __launch_bounds__(32 * kOvfWarps) voronoi_overflow_kernel(
         const float ni[3] = {nv.x, nv.y, 0.f};
         float nnew[3] = {0.f, 0.f, 0.f};
         voronoi_update(R, Pm, step, s, P, pi, ni, id, S_dir, U_pos, U_dir, U_id, counts, nnew,
-                       vor_seed ? vor_seed + gi * kVorSeed : nullptr, vor_seed_n + gi);
+                       vor_seed ? vor_seed + gi * kVorSeed : nullptr, vor_seed_n + gi, seen > kHeavyKeep);
         PhiAcc* acc = phi_acc + ((size_t)(step % Pm.phi_cap) * (size_t)Pm.n_rep + (size_t)e.y) * 3;
         atomicAdd(acc + 0, (PhiAcc)phi_fixed(nnew[0]));
         atomicAdd(acc + 1, (PhiAcc)phi_fixed(nnew[1]));
@@ -171,9 +188,10 @@ __global__ void __launch_bounds__(64) voronoi_export_kernel(const Rep* __restric
     const int32_t pi[3] = {p.x, p.y, 0};
     const int32_t id = S_id[s];
     const int64_t gi = R.p0 + id;
-    const Seeds sd{vor_seed ? vor_seed + gi * kVorSeed : nullptr, vor_seed ? vor_seed_n[gi] : 0, slot_of};
+    const Seeds sd{vor_seed ? vor_seed + gi * kVorSeed : nullptr, vor_seed ? vor_seed_n[gi] & kSeedCount : 0,
+                   slot_of};
     Poly<kSlowCap> P;
-    if (!voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status, 0u, sd)) {
+    if (!voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status, 0u, sd, nullptr)) {
       set_status(status, kStCapacity);
       if (pass == 0) deg[id] = 0;
       continue;

@@ -259,6 +259,11 @@ __device__ __forceinline__ int support_vertex(const Poly<CAP>& P, int32_t mx, in
   return lo;
 }
 
+// cells of at least this many edges test a candidate's support vertex first
+#ifndef VK_VOR_SUPPORT_MIN
+#define VK_VOR_SUPPORT_MIN 3
+#endif
+
 // true when site m (with Dm <= |m|^2) certainly neither cuts nor touches
 // the cell: its support vertex is farther than |m|/2 ... or decided by the
 // FP32 bound to lie strictly on the particle's side of the bisector
@@ -274,7 +279,8 @@ __device__ __forceinline__ bool poly_clip(Poly<CAP>& P, int32_t mx, int32_t my, 
                                           float Dm, bool* bad, bool* touch) {
   const int m = P.m;
   *touch = false;
-  if (site_misses(P, mx, my, Dm)) return true;  // the common case, in O(log m)
+  // large cells: the common case (no cut) in O(log m)
+  if (m >= VK_VOR_SUPPORT_MIN && site_misses(P, mx, my, Dm)) return true;
   // the vertices strictly beyond the bisector form one cyclic run [s, s+c)
   int c = 0, s = -1;
   bool first_cut = false, prev_cut = false;
@@ -522,11 +528,17 @@ struct Seeds {
   const int32_t* slot_of;  // sorted slot by (replica's first slot + id)
 };
 
+// a particle's seed word: the number of seeds in the low byte, and a flag
+// for a cell that needed many candidates at the last step (a particle on the
+// rim of a void), which goes straight to the warp-cooperative kernel
+constexpr int32_t kSeedCount = 0xFF;
+constexpr int32_t kSeedHeavy = 0x100;
+
 template <int CAP>
 __device__ bool voronoi_cell(const Rep& R, int64_t self, const int32_t* pi, int32_t self_id,
                              const int2* __restrict__ pos, const int32_t* __restrict__ ids,
                              const GridView& G, Poly<CAP>& P, int32_t* status, uint32_t budget, const Seeds& sd,
-                             uint32_t* n_cand = nullptr, uint32_t* n_runs = nullptr) {
+                             uint32_t* seen_out, uint32_t* n_cand = nullptr, uint32_t* n_runs = nullptr) {
   bool bad = false, overflow = false;
   uint32_t seen = 0;
   poly_init(P, self_id, R.L[0], R.L[1], &bad);
@@ -606,6 +618,7 @@ __device__ bool voronoi_cell(const Rep& R, int64_t self, const int32_t* pi, int3
     if (!within_half(b, Lx, Ly)) far_images(R, self, pi, pos, ids, visit);
   }
   if (bad) set_status(status, kStRange);
+  if (seen_out) *seen_out = seen;
   return !overflow;
 }
 
@@ -638,7 +651,7 @@ __device__ __forceinline__ int site_effect(const Poly<CAP>& P, int32_t mx, int32
 template <int CAP>
 __device__ bool voronoi_cell_warp(const Rep& R, int64_t self, const int32_t* pi, int32_t self_id,
                                   const int2* __restrict__ pos, const int32_t* __restrict__ ids, const GridView& G,
-                                  Poly<CAP>& P, int32_t* status, const Seeds& sd) {
+                                  Poly<CAP>& P, int32_t* status, const Seeds& sd, uint32_t* seen_out) {
   const int lane = threadIdx.x & 31;
   bool bad = false, overflow = false;  // kept by lane 0, broadcast after every serial part
   if (lane == 0) poly_init(P, self_id, R.L[0], R.L[1], &bad);
@@ -701,7 +714,9 @@ __device__ bool voronoi_cell_warp(const Rep& R, int64_t self, const int32_t* pi,
     }
     overflow = __shfl_sync(0xffffffffu, overflow, 0);
   };
+  uint32_t seen = 0;
   auto run = [&](uint32_t qb, uint32_t qe) {
+    seen += qe - qb;
     for (uint32_t q0 = qb; q0 < qe; q0 += 32) {
       const uint32_t q = q0 + (uint32_t)lane;
       bool flag = false;
@@ -763,6 +778,7 @@ __device__ bool voronoi_cell_warp(const Rep& R, int64_t self, const int32_t* pi,
   }
   bad = __shfl_sync(0xffffffffu, bad, 0);
   if (bad && lane == 0) set_status(status, kStRange);
+  if (seen_out) *seen_out = seen;
   return !overflow;
 }
 

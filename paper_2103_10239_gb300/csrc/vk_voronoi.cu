@@ -71,7 +71,7 @@ __device__ __forceinline__ void voronoi_update(const Rep& R, const StepParams& P
 // seed word, and the next step sends it to the warp kernel at once (particles
 // on the rim of a void stay there for many steps).  Speed only.
 #ifndef VK_VOR_HEAVY_HINT
-#define VK_VOR_HEAVY_HINT 192
+#define VK_VOR_HEAVY_HINT 320
 #endif
 constexpr uint32_t kHeavyHint = VK_VOR_HEAVY_HINT > 0 ? VK_VOR_HEAVY_HINT : 0xFFFFFFFFu;
 constexpr uint32_t kHeavyKeep = VK_VOR_HEAVY_HINT > 0 ? VK_VOR_HEAVY_HINT / 2 : 0xFFFFFFFFu;

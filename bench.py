@@ -157,7 +157,7 @@ def measured_peaks():
 def kernel_source_sha() -> str:
     """Hash of the sources the dominant kernel (knn2_box_step_kernel) is built from."""
     h = hashlib.sha256()
-    for f in ("vk_internal.cuh", "vk_knn2d.cu"):
+    for f in ("vk_internal.cuh", "vk_box2d.cuh", "vk_knn2d.cu"):
         h.update(open(os.path.join(CSRC, f), "rb").read())
     return h.hexdigest()[:16]
 

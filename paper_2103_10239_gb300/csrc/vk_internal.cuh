@@ -227,7 +227,10 @@ __device__ __forceinline__ int32_t wrap_add(int32_t p, int32_t d, uint32_t L) {
 #define VK_SUB_MAX 64
 #endif
 constexpr int kSubMax = VK_SUB_MAX;  // largest sub-grid side (sub_s is 8 bits: at most 255)
-constexpr int kSubTarget = 2;    // target particles per sub-cell
+#ifndef VK_SUB_TARGET
+#define VK_SUB_TARGET 2
+#endif
+constexpr int kSubTarget = VK_SUB_TARGET;  // target particles per sub-cell
 
 __device__ __host__ __forceinline__ int sub_side(uint32_t m) {
   int s = 1;

@@ -537,9 +537,18 @@ __device__ __forceinline__ void knn2_update(const Rep& R, const StepParams& P, i
     const float u = unit24(w.x);
     const float Sx = P.sum_mode == 1 ? __fadd_rn(H.s[0], H.c[0]) : H.s[0];
     const float Sy = P.sum_mode == 1 ? __fadd_rn(H.s[1], H.c[1]) : H.s[1];
-    float th = (Sx == 0.f && Sy == 0.f) ? atan2f(nv.y, nv.x) : atan2f(Sy, Sx);
-    th = th + R.eta * (u - 0.5f);
-    sincosf(th, &nnew[1], &nnew[0]);
+    // Eq. (2) with angular noise: the direction of S (the own heading when
+    // S = 0) turned by eta (u - 1/2), as a rotation of the unit vector
+    float ex = nv.x, ey = nv.y;
+    if (Sx != 0.f || Sy != 0.f) {
+      const float inv = rsqrtf(Sx * Sx + Sy * Sy);
+      ex = Sx * inv;
+      ey = Sy * inv;
+    }
+    float sn, cs;
+    sincosf(R.eta * (u - 0.5f), &sn, &cs);
+    nnew[0] = cs * ex - sn * ey;
+    nnew[1] = sn * ex + cs * ey;
     const float hx = P.advect_new ? nnew[0] : nv.x, hy = P.advect_new ? nnew[1] : nv.y;
     int64_t qx = (int64_t)p.x + grid_step(R.s, hx), qy = (int64_t)p.y + grid_step(R.s, hy);
     if (qx < 0 || qx >= (int64_t)R.L[0]) {
@@ -649,6 +658,7 @@ __global__ void __launch_bounds__(kBlock, 2) knn2_export_kernel(const Rep* __res
 // warp never waits for one particle's rescan.
 // ---------------------------------------------------------------------------
 constexpr int kBoxTries = 4;  // square sizes tried before the walk takes over
+
 
 template <int KC>
 struct BoxHits {

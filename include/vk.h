@@ -203,8 +203,11 @@ vk_status vk_get_state(vk_sim* sim, int32_t replica, int32_t* pos_q, float* dir,
 /* Overwrite the state (r_i, n_i) of Eq. (1)-(2) of one replica (id order,
  * same layout as vk_get_state) and, if step >= 0, the step counter of the
  * whole simulation (teacher forcing, checkpoint resume).  Positions outside
- * [0, L_q) give VK_ERR_RANGE and non-finite headings VK_ERR_ARG.
- * Synchronous. */
+ * [0, L_q) give VK_ERR_RANGE and non-finite headings VK_ERR_ARG.  The
+ * per-particle search state (2D kNN: last step's k-th distance; Voronoi: last
+ * step's neighbors) stays attached to each id, so a state read and written
+ * back steps at full speed; it only guides the search, so results are the
+ * same for any state.  Synchronous. */
 vk_status vk_set_state(vk_sim* sim, int32_t replica, const int32_t* pos_q, const float* dir,
                        int64_t step);
 

@@ -232,14 +232,18 @@ vk_status upload_reps(vk_sim* s) {
 }
 
 // U (+ ranks from a fresh histogram) -> S, sorted by the current grid
-vk_status sort_from_U(vk_sim* s) {
+// keep_search_state: the search hints (already moved into U's order) and the
+// Voronoi seeds (kept by id) follow their particles through the re-sort;
+// otherwise they are cleared.  Results never depend on them, only the speed.
+vk_status sort_from_U(vk_sim* s, bool keep_search_state = false) {
   cudaEvent_t e0 = nullptr;
   vk_status st = record_begin(s, 3, &e0);
   if (st) return st;
-  // a new state: the previous k-th distances and neighbors no longer describe it
-  if (s->b.U_hint) VK_CUDA(s, cudaMemsetAsync(s->b.U_hint, 0, sizeof(float) * (size_t)s->n_total, s->stream));
-  if (s->b.vor_seed_n)
-    VK_CUDA(s, cudaMemsetAsync(s->b.vor_seed_n, 0, sizeof(int32_t) * (size_t)s->n_total, s->stream));
+  if (!keep_search_state) {
+    if (s->b.U_hint) VK_CUDA(s, cudaMemsetAsync(s->b.U_hint, 0, sizeof(float) * (size_t)s->n_total, s->stream));
+    if (s->b.vor_seed_n)
+      VK_CUDA(s, cudaMemsetAsync(s->b.vor_seed_n, 0, sizeof(int32_t) * (size_t)s->n_total, s->stream));
+  }
   VK_CUDA(s, launch_count(s->g, s->b, s->stream));
   VK_CUDA(s, launch_build(s->g, s->b, s->stream));
   VK_CUDA(s, launch_scatter(s->g, s->b, step_params(s), 0, s->stream));
@@ -755,6 +759,11 @@ vk_status vk_set_state(vk_sim* s, int32_t replica, const int32_t* pos_q, const f
   float* dd = s->st_dir;
   cudaError_t e = cudaMemcpyAsync(pd, pos_q, sizeof(int32_t) * n * d, cudaMemcpyDefault, s->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dd, dir, sizeof(float) * n * d, cudaMemcpyDefault, s->stream);
+  // the search state follows the particles (by id): a state read with
+  // vk_get_state and set again steps as fast as it would have
+  if (e == cudaSuccess && s->b.S_hint && s->n_rep > 1)
+    e = cudaMemcpyAsync(s->b.U_hint, s->b.S_hint, sizeof(float) * N, cudaMemcpyDeviceToDevice, s->stream);
+  if (e == cudaSuccess) e = launch_hints_by_id(s->b, R.p0, R.n, s->stream);
   // every other replica keeps its state: S -> U, then overwrite this replica
   if (s->n_rep > 1) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->b.U_pos, s->b.S_pos, pv * N, cudaMemcpyDeviceToDevice, s->stream);
@@ -768,7 +777,7 @@ vk_status vk_set_state(vk_sim* s, int32_t replica, const int32_t* pos_q, const f
   if (e == cudaSuccess) e = launch_import_state(s->g, s->b, replica, R.p0, R.n, pd, dd, s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "set_state");
   vk_status st;
-  if ((st = sort_from_U(s))) return st;
+  if ((st = sort_from_U(s, true))) return st;
   if (step >= 0) {
     s->step = step;
     VK_CUDA(s, cudaMemcpyAsync(s->b.d_step, &s->step, sizeof(int64_t), cudaMemcpyHostToDevice, s->stream));

@@ -377,6 +377,18 @@ __global__ void __launch_bounds__(kBlock) import_state_kernel(
   U_id[p0 + li] = li;
 }
 
+// the search hints of one replica, from sorted order into id order (the
+// order vk_set_state imports a state in), so that they follow their
+// particles through the re-sort
+__global__ void __launch_bounds__(kBlock) hints_by_id_kernel(const int32_t* __restrict__ S_id,
+                                                             const float* __restrict__ S_hint, int64_t p0, int32_t n,
+                                                             float* __restrict__ U_hint) {
+  const int li = blockIdx.x * kBlock + (int)threadIdx.x;
+  if (li >= n) return;
+  const int64_t s = p0 + li;
+  U_hint[p0 + S_id[s]] = S_hint[s];
+}
+
 }  // namespace
 
 cudaError_t launch_load(const Geometry& g, const Buffers& b, const int32_t* pos_in, const float* head_in,
@@ -469,6 +481,12 @@ cudaError_t launch_import_state(const Geometry& g, const Buffers& b, int rep, in
   else
     import_state_kernel<3><<<nb, kBlock, 0, st>>>(pos_in, dir_in, p0, n, L, (int4*)b.U_pos, (float4*)b.U_dir,
                                                    b.U_id, b.d_status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hints_by_id(const Buffers& b, int64_t p0, int32_t n, cudaStream_t st) {
+  if (!b.S_hint || n == 0) return cudaSuccess;
+  hints_by_id_kernel<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(b.S_id, b.S_hint, p0, n, b.U_hint);
   return cudaGetLastError();
 }
 

@@ -684,6 +684,8 @@ cudaError_t launch_scatter(const Geometry& g, const Buffers& b, const StepParams
                            cudaStream_t st);
 cudaError_t launch_export_state(const Geometry& g, const Buffers& b, int rep, int64_t p0, int32_t n,
                                 int32_t* pos_out, float* dir_out, float* theta_out, cudaStream_t st);
+// 2D kNN: the search hints of one replica into id order in U (before an import)
+cudaError_t launch_hints_by_id(const Buffers& b, int64_t p0, int32_t n, cudaStream_t st);
 cudaError_t launch_import_state(const Geometry& g, const Buffers& b, int rep, int64_t p0, int32_t n,
                                 const int32_t* pos_in, const float* dir_in, cudaStream_t st);
 

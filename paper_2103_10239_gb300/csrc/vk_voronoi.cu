@@ -78,7 +78,12 @@ constexpr uint32_t kHeavyKeep = VK_VOR_HEAVY_HINT > 0 ? VK_VOR_HEAVY_HINT / 2 : 
 
 // Main kernel: cells of up to kFastCap edges.  Particles whose cell outgrows
 // it are appended to the overflow list and finished by the overflow kernel.
-__global__ void __launch_bounds__(kBlock) voronoi_step_kernel(
+// resident 256-thread blocks per SM the main kernel is compiled for
+#ifndef VK_VOR_MIN_BLOCKS
+#define VK_VOR_MIN_BLOCKS 2
+#endif
+
+__global__ void __launch_bounds__(kBlock, VK_VOR_MIN_BLOCKS) voronoi_step_kernel(
     const Rep* __restrict__ reps, const BlockTask* __restrict__ tasks, const int2* __restrict__ S_pos,
     const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G,
     int2* __restrict__ U_pos, float2* __restrict__ U_dir, int32_t* __restrict__ U_id,

@@ -534,92 +534,124 @@ struct Seeds {
 constexpr int32_t kSeedCount = 0xFF;
 constexpr int32_t kSeedHeavy = 0x100;
 
+// flags of one cell build
+struct CellFlags {
+  bool bad;       // an internal inconsistency (latched as kStRange)
+  bool overflow;  // the polygon or the twin list outgrew its capacity
+};
+
+template <int CAP>
+__device__ __forceinline__ void cell_add_twin(Poly<CAP>& P, CellFlags& F, int32_t slot, int32_t jid, int32_t of) {
+  for (int t = 0; t < P.nt; ++t)
+    if (P.tw_slot[t] == slot) return;  // met again (a seed is visited twice)
+  if (P.nt == Poly<CAP>::TW) {
+    F.overflow = true;
+    return;
+  }
+  P.tw_slot[P.nt] = slot;
+  P.tw_id[P.nt] = jid;
+  P.tw_of[P.nt] = of;
+  ++P.nt;
+}
+
+// one candidate site at offset (qx, qy) from the particle
+template <int CAP>
+__device__ __forceinline__ void cell_visit(Poly<CAP>& P, CellFlags& F, int32_t qx, int32_t qy, int32_t jid,
+                                           int32_t slot) {
+  if (F.overflow) return;
+  const uint64_t D = (uint64_t)((int64_t)qx * qx) + (uint64_t)((int64_t)qy * qy);
+  if (D == 0) {
+    cell_add_twin(P, F, slot, jid, -2);  // coincident with the particle itself
+    return;
+  }
+  const float Df = (float)D * (1.0f - 2.384185791015625e-07f);  // rounded down
+  if (Df > 4.0f * P.max_r2) return;
+  if (qx < P.bx0 || qx > P.bx1 || qy < P.by0 || qy > P.by1) return;  // outside the relevance box
+  bool touch = false;
+  if (!poly_clip(P, qx, qy, jid, slot, Df, &F.bad, &touch)) {
+    F.overflow = true;
+    return;
+  }
+  if (touch) {
+    // no vertex cut but some vertex on the bisector: a twin of an edge site?
+    for (int a = 0; a < P.m; ++a)
+      if (P.qx[a] == qx && P.qy[a] == qy && P.slot[a] >= 0) {
+        if (P.slot[a] != slot) cell_add_twin(P, F, slot, jid, P.slot[a]);  // not the edge site itself, met again
+        break;
+      }
+  }
+}
+
+// The candidates of slots [qb, qe), or of the slots list[qb..qe), at their
+// minimum image.  Out of line, so that the candidate loop and the clipping
+// exist once in the kernel whichever part of the walk (or the seeds) feeds
+// them: divergent warps then share one stretch of instruction cache.
+template <int CAP>
+__device__ __noinline__ void cell_visit_slots(Poly<CAP>& P, CellFlags& F, const int2* __restrict__ pos,
+                                              const int32_t* __restrict__ ids, int64_t self, int32_t px,
+                                              int32_t py, int64_t Lx, int64_t Ly, const int32_t* list,
+                                              uint32_t qb, uint32_t qe) {
+  for (uint32_t j = qb; j < qe; ++j) {
+    const int32_t q = list ? list[j] : (int32_t)j;
+    if ((int64_t)q == self) continue;
+    const int2 pj = pos[q];
+    cell_visit(P, F, (int32_t)min_image((int64_t)pj.x - px, Lx), (int32_t)min_image((int64_t)pj.y - py, Ly),
+               ids[q], q);
+  }
+}
+
+// the same for one candidate at an explicit offset (far periodic images)
+template <int CAP>
+__device__ __noinline__ void cell_visit_one(Poly<CAP>& P, CellFlags& F, int32_t qx, int32_t qy, int32_t jid,
+                                            int32_t slot) {
+  cell_visit(P, F, qx, qy, jid, slot);
+}
+
 template <int CAP>
 __device__ bool voronoi_cell(const Rep& R, int64_t self, const int32_t* pi, int32_t self_id,
                              const int2* __restrict__ pos, const int32_t* __restrict__ ids,
                              const GridView& G, Poly<CAP>& P, int32_t* status, uint32_t budget, const Seeds& sd,
                              uint32_t* seen_out, uint32_t* n_cand = nullptr, uint32_t* n_runs = nullptr) {
-  bool bad = false, overflow = false;
+  CellFlags F{false, false};
   uint32_t seen = 0;
-  poly_init(P, self_id, R.L[0], R.L[1], &bad);
+  poly_init(P, self_id, R.L[0], R.L[1], &F.bad);
   const int64_t Lx = R.L[0], Ly = R.L[1];
-  auto add_twin = [&](int32_t slot, int32_t jid, int32_t of) {
-    for (int t = 0; t < P.nt; ++t)
-      if (P.tw_slot[t] == slot) return;  // met again (a seed is visited twice)
-    if (P.nt == Poly<CAP>::TW) {
-      overflow = true;
-      return;
-    }
-    P.tw_slot[P.nt] = slot;
-    P.tw_id[P.nt] = jid;
-    P.tw_of[P.nt] = of;
-    ++P.nt;
-  };
-  auto visit = [&](int32_t qx, int32_t qy, int32_t jid, int32_t slot) {
-    if (overflow) return;
-    const uint64_t D = (uint64_t)((int64_t)qx * qx) + (uint64_t)((int64_t)qy * qy);
-    if (D == 0) {
-      add_twin(slot, jid, -2);  // coincident with the particle itself
-      return;
-    }
-    const float Df = (float)D * (1.0f - 2.384185791015625e-07f);  // rounded down
-    if (Df > 4.0f * P.max_r2) return;
-    if (qx < P.bx0 || qx > P.bx1 || qy < P.by0 || qy > P.by1) return;  // outside the relevance box
-    bool touch = false;
-    if (!poly_clip(P, qx, qy, jid, slot, Df, &bad, &touch)) {
-      overflow = true;
-      return;
-    }
-    if (touch) {
-      // no vertex cut but some vertex on the bisector: a twin of an edge site?
-      for (int a = 0; a < P.m; ++a)
-        if (P.qx[a] == qx && P.qy[a] == qy && P.slot[a] >= 0) {
-          if (P.slot[a] != slot) add_twin(slot, jid, P.slot[a]);  // not the edge site itself, met again
-          break;
-        }
-    }
-  };
+  // the seeds first: their slots, then one pass of the candidate loop
+  if (sd.n > 0) {
+    int32_t ss[kVorSeed];
+    const int n = min(sd.n, kVorSeed);
+    for (int j = 0; j < n; ++j) ss[j] = sd.slot_of[R.p0 + sd.ids[j]];
+    cell_visit_slots(P, F, pos, ids, self, pi[0], pi[1], Lx, Ly, ss, 0u, (uint32_t)n);
+  }
   auto run = [&](uint32_t qb, uint32_t qe) {
     if (n_cand) {
       *n_cand += qe - qb;
       *n_runs += 1;
     }
     seen += qe - qb;
-    if (budget && seen > budget) overflow = true;  // a heavy cell: left to the warp-cooperative kernel
-    for (uint32_t q = qb; q < qe; ++q) {
-      if ((int64_t)q == self) continue;
-      const int2 pj = pos[q];
-      const int32_t qx = (int32_t)min_image((int64_t)pj.x - pi[0], Lx);
-      const int32_t qy = (int32_t)min_image((int64_t)pj.y - pi[1], Ly);
-      visit(qx, qy, ids[q], (int32_t)q);
-    }
+    if (budget && seen > budget) F.overflow = true;  // a heavy cell: left to the warp-cooperative kernel
+    if (!F.overflow) cell_visit_slots(P, F, pos, ids, self, pi[0], pi[1], Lx, Ly, nullptr, qb, qe);
   };
-  for (int j = 0; j < sd.n && !overflow; ++j) {
-    const int32_t jid = sd.ids[j];
-    const int32_t q = sd.slot_of[R.p0 + jid];
-    if ((int64_t)q == self) continue;
-    const int2 pj = pos[q];
-    visit((int32_t)min_image((int64_t)pj.x - pi[0], Lx), (int32_t)min_image((int64_t)pj.y - pi[1], Ly), jid, q);
-  }
   auto box = [&](int64_t* b) {
     poly_refresh_box(P);
     // after an overflow nothing more is needed: an empty box ends the walk
-    b[0] = overflow ? 0 : P.bx0;
-    b[1] = overflow ? 0 : P.bx1;
-    b[2] = overflow ? 0 : P.by0;
-    b[3] = overflow ? 0 : P.by1;
+    b[0] = F.overflow ? 0 : P.bx0;
+    b[1] = F.overflow ? 0 : P.bx1;
+    b[2] = F.overflow ? 0 : P.by0;
+    b[3] = F.overflow ? 0 : P.by1;
   };
   const bool all = voronoi_walk(R, pi, G, run, box);
-  if (all && !overflow) {
+  if (all && !F.overflow) {
     // tiny boxes: other periodic images than the minimum one can still shape
     // the cell when the relevance box reaches half a period
     poly_refresh_box(P);
     const int64_t b[4] = {P.bx0, P.bx1, P.by0, P.by1};
+    auto visit = [&](int32_t qx, int32_t qy, int32_t jid, int32_t slot) { cell_visit_one(P, F, qx, qy, jid, slot); };
     if (!within_half(b, Lx, Ly)) far_images(R, self, pi, pos, ids, visit);
   }
-  if (bad) set_status(status, kStRange);
+  if (F.bad) set_status(status, kStRange);
   if (seen_out) *seen_out = seen;
-  return !overflow;
+  return !F.overflow;
 }
 
 // Effect of site m on the current cell: 1 if it cuts a vertex, 2 if some

@@ -183,3 +183,26 @@ def test_fov_after_many_steps_with_hints():
     with vk.from_workload(w, fov=1, fov_cos=0.2) as sim:
         sim.step(30)
         check_step(sim, w, "knn", lists=fov_lists(w.box_q, 7, 0.2))
+
+
+# ------------------------------------------------------------ batched replicas
+
+def test_metric_and_view_in_a_replica_batch():
+    """Replicas with their own box and fixed-point resolution: r0q is
+    rint(r0 * 2^F) per replica; each replica's lists and one teacher-forced
+    step match the oracle, for the metric rule and for a field of view."""
+    ws = [W.uniform_system(n, L, F, 2, input_seed=70 + i, rule="metric", k=5, v0=0.5, eta=0.3)
+          for i, (n, L, F) in enumerate([(700, 26.0, 16), (1500, 30.0, 12), (300, 15.0, 20)])]
+    pos = np.ascontiguousarray(np.concatenate([w.pos_q for w in ws]))
+    d = np.ascontiguousarray(np.concatenate([w.dir for w in ws]))
+    for params, lists in [(dict(rule="metric", r0=1.3), lambda w: metric_lists(w.box_q, r0q_of(1.3, w.frac_bits))),
+                          (dict(rule="knn", k=5, fov=1, fov_cos=0.3), lambda w: fov_lists(w.box_q, 5, 0.3))]:
+        with vk.Sim.create_batch([w.n for w in ws], pos, d, [w.box_q for w in ws], [w.frac_bits for w in ws],
+                                 eta_r=[w.eta for w in ws], v0=0.5, eta=0.3, **params) as sim:
+            for _ in range(2):
+                for r, w in enumerate(ws):
+                    pos0, d0, _, t0 = sim.state(r)
+                    off, ids = sim.neighbors(r)
+                    woff, wids = lists(w)(pos0, d0)
+                    assert np.array_equal(off, woff) and np.array_equal(ids, wids), (params, r)
+                sim.step(1)

@@ -489,6 +489,10 @@ def secondary_block(stream) -> dict:
             out[name] = dict(_rate(stream, sim, wv.n, 20, 50),
                              config={"workload": wv.name, "rule": "voronoi", "eta": 0.1,
                                      "voronoi_rebuild": rebuild})
+    wp = W.precision_study("voronoi")
+    with vk.from_workload(wp, stream=stream) as sim:
+        out["voronoi_uniform1M_rho2"] = dict(_rate(stream, sim, wp.n, 5, 10),
+                                             config={"workload": wp.name, "rule": "voronoi", "eta": wp.eta})
     wc = W.clustered_large()
     with vk.from_workload(wc, stream=stream, rule="metric", r0=1.0, cell_occupancy=256.0) as sim:
         out["metric_clustered4M_r1"] = dict(_rate(stream, sim, wc.n, 5, 20),

@@ -675,6 +675,58 @@ __device__ __forceinline__ int site_effect(const Poly<CAP>& P, int32_t mx, int32
   return r;
 }
 
+// every lane: could the candidate at (qx, qy) cut or touch the current cell?
+template <int CAP>
+__device__ __forceinline__ bool site_matters(const Poly<CAP>& P, int32_t qx, int32_t qy) {
+  const uint64_t D = (uint64_t)((int64_t)qx * qx) + (uint64_t)((int64_t)qy * qy);
+  if (D == 0) return true;
+  const float Df = (float)D * (1.0f - 2.384185791015625e-07f);
+  if (Df > 4.0f * P.max_r2) return false;
+  if (qx < P.bx0 || qx > P.bx1 || qy < P.by0 || qy > P.by1) return false;
+  return site_effect(P, qx, qy, Df) != 0;
+}
+
+// the lanes whose candidate matters hand it to lane 0, which applies them in
+// lane order; every lane leaves with lane 0's overflow flag
+template <int CAP>
+__device__ __forceinline__ void warp_apply(Poly<CAP>& P, CellFlags& F, bool flag, int32_t qx, int32_t qy,
+                                           int32_t jid, int32_t slot) {
+  const int lane = threadIdx.x & 31;
+  unsigned mask = __ballot_sync(0xffffffffu, flag);
+  while (mask) {
+    const int src = __ffs(mask) - 1;
+    mask &= mask - 1;
+    const int32_t sx = __shfl_sync(0xffffffffu, qx, src), sy = __shfl_sync(0xffffffffu, qy, src);
+    const int32_t sid = __shfl_sync(0xffffffffu, jid, src), ss = __shfl_sync(0xffffffffu, slot, src);
+    if (lane == 0) cell_visit(P, F, sx, sy, sid, ss);
+    __syncwarp();
+  }
+  F.overflow = __shfl_sync(0xffffffffu, F.overflow, 0);
+}
+
+// The warp's pass over slots [qb, qe): the lanes test 32 candidates at a
+// time against the current cell (in shared memory), lane 0 applies the few
+// that matter.  All lanes call it; out of line like cell_visit_slots.
+template <int CAP>
+__device__ __noinline__ void warp_visit_slots(Poly<CAP>& P, CellFlags& F, const int2* __restrict__ pos,
+                                              const int32_t* __restrict__ ids, int64_t self, int32_t px,
+                                              int32_t py, int64_t Lx, int64_t Ly, uint32_t qb, uint32_t qe) {
+  const int lane = threadIdx.x & 31;
+  for (uint32_t q0 = qb; q0 < qe && !F.overflow; q0 += 32) {
+    const uint32_t q = q0 + (uint32_t)lane;
+    bool flag = false;
+    int32_t qx = 0, qy = 0, jid = 0;
+    if (q < qe && (int64_t)q != self) {
+      const int2 pj = pos[q];
+      qx = (int32_t)min_image((int64_t)pj.x - px, Lx);
+      qy = (int32_t)min_image((int64_t)pj.y - py, Ly);
+      jid = ids[q];
+      flag = site_matters(P, qx, qy);
+    }
+    warp_apply(P, F, flag, qx, qy, jid, (int32_t)q);
+  }
+}
+
 // The same cell as voronoi_cell, built by a whole warp (all 32 lanes call
 // it; P is the warp's polygon in shared memory).  The walk is the same; the
 // lanes test 32 candidates at a time against the current cell, and lane 0
@@ -685,105 +737,32 @@ __device__ bool voronoi_cell_warp(const Rep& R, int64_t self, const int32_t* pi,
                                   const int2* __restrict__ pos, const int32_t* __restrict__ ids, const GridView& G,
                                   Poly<CAP>& P, int32_t* status, const Seeds& sd, uint32_t* seen_out) {
   const int lane = threadIdx.x & 31;
-  bool bad = false, overflow = false;  // kept by lane 0, broadcast after every serial part
-  if (lane == 0) poly_init(P, self_id, R.L[0], R.L[1], &bad);
-  __syncwarp();
+  CellFlags F{false, false};  // lane 0's is authoritative, broadcast after every serial part
+  if (lane == 0) poly_init(P, self_id, R.L[0], R.L[1], &F.bad);
   const int64_t Lx = R.L[0], Ly = R.L[1];
-  auto add_twin = [&](int32_t slot, int32_t jid, int32_t of) {
-    for (int t = 0; t < P.nt; ++t)
-      if (P.tw_slot[t] == slot) return;  // met again (a seed is visited twice)
-    if (P.nt == Poly<CAP>::TW) {
-      overflow = true;
-      return;
-    }
-    P.tw_slot[P.nt] = slot;
-    P.tw_id[P.nt] = jid;
-    P.tw_of[P.nt] = of;
-    ++P.nt;
-  };
-  // lane 0: the serial visit of voronoi_cell
-  auto visit0 = [&](int32_t qx, int32_t qy, int32_t jid, int32_t slot) {
-    if (overflow) return;
-    const uint64_t D = (uint64_t)((int64_t)qx * qx) + (uint64_t)((int64_t)qy * qy);
-    if (D == 0) {
-      add_twin(slot, jid, -2);
-      return;
-    }
-    const float Df = (float)D * (1.0f - 2.384185791015625e-07f);
-    if (Df > 4.0f * P.max_r2) return;
-    if (qx < P.bx0 || qx > P.bx1 || qy < P.by0 || qy > P.by1) return;
-    bool touch = false;
-    if (!poly_clip(P, qx, qy, jid, slot, Df, &bad, &touch)) {
-      overflow = true;
-      return;
-    }
-    if (touch) {
-      for (int a = 0; a < P.m; ++a)
-        if (P.qx[a] == qx && P.qy[a] == qy && P.slot[a] >= 0) {
-          if (P.slot[a] != slot) add_twin(slot, jid, P.slot[a]);  // not the edge site itself, met again
-          break;
-        }
-    }
-  };
-  // every lane: does its candidate matter for the current cell?
-  auto matters = [&](int32_t qx, int32_t qy) -> bool {
-    const uint64_t D = (uint64_t)((int64_t)qx * qx) + (uint64_t)((int64_t)qy * qy);
-    if (D == 0) return true;
-    const float Df = (float)D * (1.0f - 2.384185791015625e-07f);
-    if (Df > 4.0f * P.max_r2) return false;
-    if (qx < P.bx0 || qx > P.bx1 || qy < P.by0 || qy > P.by1) return false;
-    return site_effect(P, qx, qy, Df) != 0;
-  };
-  auto process = [&](bool flag, int32_t qx, int32_t qy, int32_t jid, int32_t slot) {
-    unsigned mask = __ballot_sync(0xffffffffu, flag);
-    while (mask) {
-      const int src = __ffs(mask) - 1;
-      mask &= mask - 1;
-      const int32_t sx = __shfl_sync(0xffffffffu, qx, src), sy = __shfl_sync(0xffffffffu, qy, src);
-      const int32_t sid = __shfl_sync(0xffffffffu, jid, src), ss = __shfl_sync(0xffffffffu, slot, src);
-      if (lane == 0) visit0(sx, sy, sid, ss);
-      __syncwarp();
-    }
-    overflow = __shfl_sync(0xffffffffu, overflow, 0);
-  };
+  if (lane == 0 && sd.n > 0) {
+    int32_t ss[kVorSeed];
+    const int n = min(sd.n, kVorSeed);
+    for (int j = 0; j < n; ++j) ss[j] = sd.slot_of[R.p0 + sd.ids[j]];
+    cell_visit_slots(P, F, pos, ids, self, pi[0], pi[1], Lx, Ly, ss, 0u, (uint32_t)n);
+  }
+  __syncwarp();
+  F.overflow = __shfl_sync(0xffffffffu, F.overflow, 0);
   uint32_t seen = 0;
   auto run = [&](uint32_t qb, uint32_t qe) {
     seen += qe - qb;
-    for (uint32_t q0 = qb; q0 < qe; q0 += 32) {
-      const uint32_t q = q0 + (uint32_t)lane;
-      bool flag = false;
-      int32_t qx = 0, qy = 0, jid = 0;
-      if (q < qe && (int64_t)q != self && !overflow) {
-        const int2 pj = pos[q];
-        qx = (int32_t)min_image((int64_t)pj.x - pi[0], Lx);
-        qy = (int32_t)min_image((int64_t)pj.y - pi[1], Ly);
-        jid = ids[q];
-        flag = matters(qx, qy);
-      }
-      process(flag, qx, qy, jid, (int32_t)q);
-    }
+    warp_visit_slots(P, F, pos, ids, self, pi[0], pi[1], Lx, Ly, qb, qe);
   };
-  if (lane == 0) {
-    for (int j = 0; j < sd.n && !overflow; ++j) {
-      const int32_t jid = sd.ids[j];
-      const int32_t q = sd.slot_of[R.p0 + jid];
-      if ((int64_t)q == self) continue;
-      const int2 pj = pos[q];
-      visit0((int32_t)min_image((int64_t)pj.x - pi[0], Lx), (int32_t)min_image((int64_t)pj.y - pi[1], Ly), jid, q);
-    }
-  }
-  __syncwarp();
-  overflow = __shfl_sync(0xffffffffu, overflow, 0);
   auto box = [&](int64_t* b) {
     if (lane == 0) poly_refresh_box(P);
     __syncwarp();
-    b[0] = overflow ? 0 : P.bx0;
-    b[1] = overflow ? 0 : P.bx1;
-    b[2] = overflow ? 0 : P.by0;
-    b[3] = overflow ? 0 : P.by1;
+    b[0] = F.overflow ? 0 : P.bx0;
+    b[1] = F.overflow ? 0 : P.bx1;
+    b[2] = F.overflow ? 0 : P.by0;
+    b[3] = F.overflow ? 0 : P.by1;
   };
   const bool all = voronoi_walk(R, pi, G, run, box);
-  if (all && !overflow) {
+  if (all && !F.overflow) {
     if (lane == 0) poly_refresh_box(P);
     __syncwarp();
     const int64_t b[4] = {P.bx0, P.bx1, P.by0, P.by1};
@@ -803,15 +782,15 @@ __device__ bool voronoi_cell_warp(const Rep& R, int64_t self, const int32_t* pi,
           for (int sx = -1; sx <= 1; ++sx) {
             if (sx == 0 && sy == 0) continue;
             const int32_t X = (int32_t)((int64_t)qx0 + sx * Lx), Y = (int32_t)((int64_t)qy0 + sy * Ly);
-            process(ok && !overflow && matters(X, Y), X, Y, jid, (int32_t)q);
+            warp_apply(P, F, ok && !F.overflow && site_matters(P, X, Y), X, Y, jid, (int32_t)q);
           }
       }
     }
   }
-  bad = __shfl_sync(0xffffffffu, bad, 0);
-  if (bad && lane == 0) set_status(status, kStRange);
+  F.bad = __shfl_sync(0xffffffffu, F.bad, 0);
+  if (F.bad && lane == 0) set_status(status, kStRange);
   if (seen_out) *seen_out = seen;
-  return !overflow;
+  return !F.overflow;
 }
 
 // neighbors: sites of edges with positive length (never the particle's own

@@ -140,6 +140,15 @@ def test_fov_lists_and_steps(fov_cos, search):
             check_step(sim, w, "knn", lists=fov_lists(w.box_q, 7, fov_cos))
 
 
+@pytest.mark.parametrize("noise,include_self", [("vectorial", False), ("vectorial", True), ("angular", True)])
+def test_fov_update_modes(noise, include_self):
+    """A short in-view list changes m, the count Eq. (2) averages over."""
+    w = W.uniform_system(2000, 44.0, 16, 2, input_seed=58, rule="knn", k=6, v0=0.5, eta=0.5, noise=noise)
+    with vk.from_workload(w, fov=1, fov_cos=0.6, include_self=int(include_self)) as sim:
+        for _ in range(3):
+            check_step(sim, w, "knn", lists=fov_lists(w.box_q, 6, 0.6), include_self=include_self)
+
+
 def test_fov_full_circle_is_the_plain_rule():
     w = W.uniform_system(2000, 44.0, 16, 2, input_seed=55, rule="knn", k=7)
     with vk.from_workload(w, fov=1, fov_cos=-1.0) as a, vk.from_workload(w) as b:

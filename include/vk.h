@@ -295,9 +295,16 @@ vk_status vk_get_info(vk_sim* sim, vk_info* out);
 /* Re-pick the search grid (particles per cell) by timing `trial_steps` steps
  * for each candidate occupancy on a scratch copy of the state; the state and
  * the step counter are restored afterwards.  Results never depend on the
- * grid; only the speed does.  On return *best holds the chosen occupancy. */
+ * grid; only the speed does.  On return *best holds the chosen occupancy.
+ * The choice is remembered for the process, keyed by (dimension, rule, k,
+ * floor(log2(mean particles per replica))): later sims of the same kind
+ * whose params leave cell_occupancy at 0 start from it. */
 vk_status vk_autotune(vk_sim* sim, const float* candidates, int32_t n_candidates,
                       int32_t trial_steps, float* best);
+
+/* Forget every occupancy vk_autotune has chosen in this process (see
+ * vk_autotune: later sims then start from the built-in defaults again). */
+void vk_autotune_forget(void);
 
 /* ------------------------------------------------------------------------
  * Allocation-free kNN lists.  (The paper has no counterpart: this is a

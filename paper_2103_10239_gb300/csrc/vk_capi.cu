@@ -10,7 +10,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/vk.h"
@@ -120,8 +123,28 @@ StepParams step_params(const vk_sim* s) {
   return P;
 }
 
-float default_occupancy(const vk_params& p, int dim) {
+// Occupancies chosen by vk_autotune, keyed by (dimension, rule, k, size
+// bucket = floor(log2(mean particles per replica))): a later sim of the same
+// kind whose caller leaves cell_occupancy at 0 starts from the tuned value.
+// Process-wide; speed only.
+using TuneKey = std::tuple<int, int, int, int>;
+std::map<TuneKey, float> g_tuned;
+std::mutex g_tuned_mu;
+
+TuneKey tune_key(const vk_params& p, int dim, int64_t n_total, int n_rep) {
+  const int64_t mean = std::max<int64_t>(1, n_total / std::max(1, n_rep));
+  int bucket = 0;
+  while ((int64_t)1 << (bucket + 1) <= mean) ++bucket;
+  return TuneKey(dim, p.rule, p.rule == VK_RULE_KNN ? p.k : 0, bucket);
+}
+
+float default_occupancy(const vk_params& p, int dim, int64_t n_total, int n_rep) {
   if (p.cell_occupancy > 0.f) return p.cell_occupancy;
+  {
+    std::lock_guard<std::mutex> lock(g_tuned_mu);
+    auto it = g_tuned.find(tune_key(p, dim, n_total, n_rep));
+    if (it != g_tuned.end()) return it->second;
+  }
   if (p.rule == VK_RULE_VORONOI) return 2.0f;
   // 2D kNN and metric: coarse cells of a few hundred particles split into
   // sub-grids (the radius-first search measured fastest at 256 on uniform
@@ -416,7 +439,7 @@ vk_status build_sim(int32_t n_rep, const int64_t* n_r, const int32_t* pos_q, con
     for (int first = 0; first < R.n; first += kBlock) s->tasks_h.push_back({r, first});
     p0 += n_r[r];
   }
-  s->occupancy = default_occupancy(*params, dim);
+  s->occupancy = default_occupancy(*params, dim, total, n_rep);
   plan_cells(s, s->occupancy);
 
   if (cuda_stream) {
@@ -1001,7 +1024,16 @@ vk_status vk_autotune(vk_sim* s, const float* candidates, int32_t n_candidates, 
   if (st2) return st2;
   s->occupancy = best_occ;
   if (best) *best = best_occ;
+  {
+    std::lock_guard<std::mutex> lock(g_tuned_mu);
+    g_tuned[tune_key(s->prm, s->dim, s->n_total, s->n_rep)] = best_occ;
+  }
   return read_status(s);
+}
+
+void vk_autotune_forget(void) {
+  std::lock_guard<std::mutex> lock(g_tuned_mu);
+  g_tuned.clear();
 }
 
 }  // extern "C"

@@ -95,6 +95,7 @@ _SIGS = {
     "vk_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(vk_info)]),
     "vk_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.POINTER(ctypes.c_float)]),
+    "vk_autotune_forget": (None, []),
     "vk_knn_lists_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(vk_box),
                                             ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
@@ -349,6 +350,11 @@ class Sim:
 
     def __exit__(self, *a):
         self.close()
+
+
+def autotune_forget() -> None:
+    """vk_autotune_forget: drop the occupancies vk_autotune chose in this process."""
+    load().vk_autotune_forget()
 
 
 def knn_lists_noalloc(pos_q, box_q, frac_bits: int, k: int, out_ids, dev_status=None, stream=None) -> None:

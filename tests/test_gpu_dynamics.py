@@ -128,16 +128,30 @@ def test_profiling_counts_phases():
 
 def test_autotune_keeps_results():
     w = W.uniform_system(20000, 141.0, 16, 2, input_seed=17, rule="knn", k=7)
-    with vk.from_workload(w) as sim:
-        sim.step(3)
-        before = sim.state()
-        best = sim.autotune([0.5, 1.0, 2.0, 3.0], trial_steps=2)
-        after = sim.state()
-        assert best in (0.5, 1.0, 2.0, 3.0)
-        assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
-        assert before[3] == after[3]
-        sim.step(1)
-        check_step(sim, w, "knn")
+    try:
+        with vk.from_workload(w) as sim:
+            sim.step(3)
+            before = sim.state()
+            best = sim.autotune([0.5, 1.0, 2.0, 3.0], trial_steps=2)
+            after = sim.state()
+            assert best in (0.5, 1.0, 2.0, 3.0)
+            assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+            assert before[3] == after[3]
+            sim.step(1)
+            check_step(sim, w, "knn")
+            tuned_cells = sim.info().n_cells
+        # a later sim of the same kind (2D, kNN, k = 7, 2^14..2^15 particles)
+        # starts from the tuned grid; another k does not
+        w2 = W.uniform_system(30000, 173.0, 16, 2, input_seed=18, rule="knn", k=7)
+
+        def cells(**kw):
+            with vk.from_workload(w2, **kw) as x:
+                return x.info().n_cells
+        assert tuned_cells > 0
+        assert cells() == cells(cell_occupancy=best)
+        assert cells(k=8) == cells(k=8, cell_occupancy=256.0)
+    finally:
+        vk.autotune_forget()
 
 
 def test_free_running_order_parameter_statistics():

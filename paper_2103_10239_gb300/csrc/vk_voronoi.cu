@@ -82,8 +82,16 @@ constexpr uint32_t kHeavyKeep = VK_VOR_HEAVY_HINT > 0 ? VK_VOR_HEAVY_HINT / 2 : 
 #ifndef VK_VOR_MIN_BLOCKS
 #define VK_VOR_MIN_BLOCKS 2
 #endif
+// threads per block of the main kernel: each 256-particle block task is
+// split into kBlock / VK_VOR_BLOCK blocks, so that the few slow cells (void
+// rims) hold back smaller blocks and the SMs stay evenly loaded
+#ifndef VK_VOR_BLOCK
+#define VK_VOR_BLOCK 256
+#endif
+constexpr int kVorBlock = VK_VOR_BLOCK;
+constexpr int kVorSplit = kBlock / kVorBlock;
 
-__global__ void __launch_bounds__(kBlock, VK_VOR_MIN_BLOCKS) voronoi_step_kernel(
+__global__ void __launch_bounds__(kVorBlock, VK_VOR_MIN_BLOCKS * kVorSplit) voronoi_step_kernel(
     const Rep* __restrict__ reps, const BlockTask* __restrict__ tasks, const int2* __restrict__ S_pos,
     const float2* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G,
     int2* __restrict__ U_pos, float2* __restrict__ U_dir, int32_t* __restrict__ U_id,
@@ -92,9 +100,9 @@ __global__ void __launch_bounds__(kBlock, VK_VOR_MIN_BLOCKS) voronoi_step_kernel
     int32_t* __restrict__ vor_seed_n, const int32_t* __restrict__ slot_of) {
   __shared__ PhiShared phs;
   phi_block_begin(phs);
-  const BlockTask t = tasks[blockIdx.x];
+  const BlockTask t = tasks[blockIdx.x / kVorSplit];
   const Rep R = reps[t.rep];
-  const int li = t.first + (int)threadIdx.x;
+  const int li = t.first + (int)(blockIdx.x % kVorSplit) * kVorBlock + (int)threadIdx.x;
   const int64_t step = *d_step;
   float nnew[3] = {0.f, 0.f, 0.f};
   uint32_t n_cand = 0, n_runs = 0;
@@ -225,7 +233,7 @@ static GridView grid_view(const Buffers& b) {
 
 cudaError_t launch_voronoi_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st) {
   const GridView G = grid_view(b);
-  voronoi_step_kernel<<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, (const int2*)b.S_pos, (const float2*)b.S_dir,
+  voronoi_step_kernel<<<g.n_tasks * kVorSplit, kVorBlock, 0, st>>>(g.reps, g.tasks, (const int2*)b.S_pos, (const float2*)b.S_dir,
                                                     b.S_id, G, (int2*)b.U_pos, (float2*)b.U_dir, b.U_id,
                                                     b.counts, b.phi_acc, b.d_step, P, b.ovf_list,
                                                     b.ovf_count, b.d_status, b.vor_seed, b.vor_seed_n,

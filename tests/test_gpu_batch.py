@@ -57,3 +57,25 @@ def test_full_replica_batch_runs():
         phi = sim.order_parameter(511)
         assert phi.shape[0] == 20 and np.all((phi >= 0) & (phi <= 1))
         check_step(sim, ws[300], "knn", replica=300)
+
+
+def test_voronoi_batch_equals_single_runs():
+    """The Voronoi rule in a batch (seeds, heavy-cell flags and the cost-
+    grouped visiting order are all per replica): every replica equals the
+    same system alone, and the lists of each match the oracle."""
+    import oracle
+    ws = W.replica_batch(n_rep=5, sizes=[1024, 3000, 1500, 700, 2500])
+    for w in ws:
+        w.rule = "voronoi"
+    with vk.batch_from_workloads(ws, rule="voronoi", v0=0.3) as sim:
+        sim.step(30)
+        batch = [sim.state(r) for r in range(len(ws))]
+        for r, w in enumerate(ws):
+            off, ids = sim.neighbors(r)
+            woff, wids = oracle.voronoi(batch[r][0], w.box_q)
+            assert np.array_equal(off, woff) and np.array_equal(ids, wids)
+    for r in (1, 3, 4):
+        with vk.from_workload(ws[r], replica_offset=r, rule="voronoi", v0=0.3) as sim:
+            sim.step(30)
+            pos, d, _, _ = sim.state()
+        assert np.array_equal(pos, batch[r][0]) and np.array_equal(d, batch[r][1])

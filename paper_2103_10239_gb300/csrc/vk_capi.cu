@@ -298,7 +298,7 @@ vk_status clear_phi(vk_sim* s) {
 int search_launches(const vk_sim* s) {
   if (s->prm.rule == VK_RULE_KNN) return (s->dim == 2 && s->prm.knn_search == 0) ? 3 : 1;
   if (s->prm.rule == VK_RULE_METRIC) return 1;
-  return voronoi_step_launches(s->b);
+  return 2;
 }
 
 vk_status enqueue_step(vk_sim* s) {
@@ -479,14 +479,8 @@ vk_status build_sim(int32_t n_rep, const int64_t* n_r, const int32_t* pos_q, con
       return bail(cuda_fail(s, e, "kNN search buffers"));
   }
   if (params->rule == VK_RULE_VORONOI && !params->voronoi_rebuild) {
-    // first block task of every replica (tasks are listed replica by replica)
-    std::vector<int32_t> task0(n_rep + 1, 0);
-    for (size_t t = 0; t < s->tasks_h.size(); ++t) task0[s->tasks_h[t].rep + 1] = (int32_t)t + 1;
-    for (int r = 0; r < n_rep; ++r) task0[r + 1] = std::max(task0[r + 1], task0[r]);
     if ((e = dalloc(&s->b.vor_seed, N * kVorSeed)) || (e = dalloc(&s->b.vor_seed_n, N)) ||
-        (e = dalloc(&s->b.slot_of, N)) || (e = dalloc(&s->b.vor_order, N)) ||
-        (e = dalloc(&s->b.vor_bucket, s->tasks_h.size() * kVorBuckets)) || (e = dalloc(&s->b.rep_task0, n_rep + 1)) ||
-        (e = cudaMemcpy(s->b.rep_task0, task0.data(), sizeof(int32_t) * (n_rep + 1), cudaMemcpyHostToDevice)))
+        (e = dalloc(&s->b.slot_of, N)))
       return bail(cuda_fail(s, e, "Voronoi seed buffers"));
   }
   if (ensure_cells_capacity(s)) return bail(VK_ERR_OOM);
@@ -850,7 +844,7 @@ void vk_destroy(vk_sim* s) {
                   s->b.ovf_list, s->b.ovf_count, s->reps_d, s->tasks_d, s->b.sub_s, s->b.sub_base,
                   s->b.sub_count, s->b.sub_off, s->b.bsum2, s->d_stats, s->b.bounds,
                   s->st_pos, s->st_dir, s->st_theta, s->b.S_hint, s->b.U_hint, s->b.vor_seed,
-                  s->b.vor_seed_n, s->b.slot_of, s->b.vor_order, s->b.vor_bucket, s->b.rep_task0};
+                  s->b.vor_seed_n, s->b.slot_of};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);

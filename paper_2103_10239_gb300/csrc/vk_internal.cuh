@@ -657,17 +657,9 @@ struct Buffers {
   int32_t* vor_seed;
   int32_t* vor_seed_n;
   int32_t* slot_of;
-  // Voronoi rule, with the seeds: the order the main kernel visits each
-  // replica's particles in (slots grouped by last step's cost, so that the
-  // lanes of a warp build cells of similar cost), a per-block-task table of
-  // bucket counts / offsets, and the first block task of every replica
-  int32_t* vor_order;
-  uint32_t* vor_bucket;
-  int32_t* rep_task0;
 };
 
 constexpr int kVorSeed = 12;
-constexpr int kVorBuckets = 16;  // cost buckets of the visiting order
 
 struct Geometry {
   int dim;
@@ -735,8 +727,6 @@ cudaError_t launch_tissue(const Geometry& g, const Buffers& b, int rep, int n, d
 
 // vk_voronoi.cu
 cudaError_t launch_voronoi_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st);
-// kernels launch_voronoi_step issues per step
-int voronoi_step_launches(const Buffers& b);
 cudaError_t launch_voronoi_export(const Geometry& g, const Buffers& b, int rep, int n, int pass, int32_t* deg,
                                   const int64_t* out_off, int32_t* out_ids, cudaStream_t st);
 // largest Voronoi cell (edges) handled; larger cells latch VK_ERR_CAPACITY

@@ -41,15 +41,14 @@ __device__ __forceinline__ void voronoi_update(const Rep& R, const StepParams& P
                                                int2* __restrict__ U_pos, float2* __restrict__ U_dir,
                                                int32_t* __restrict__ U_id, uint32_t* __restrict__ counts,
                                                float* nnew, int32_t* __restrict__ seed_out,
-                                               int32_t* __restrict__ seed_n_out, bool heavy_next,
-                                               uint32_t seen) {
+                                               int32_t* __restrict__ seed_n_out, bool heavy_next) {
   int32_t nid[CAP + Poly<CAP>::TW], nslot[CAP + Poly<CAP>::TW];
   const int cnt = voronoi_neighbors(P, id, nid, nslot);
   if (seed_out) {
     // the next step's seeds (any subset of sites would do)
     const int ns = min(cnt, kVorSeed);
     for (int j = 0; j < ns; ++j) seed_out[j] = nid[j];
-    *seed_n_out = ns | (heavy_next ? kSeedHeavy : 0) | (cost_bucket(seen) << kSeedCostShift);
+    *seed_n_out = ns | (heavy_next ? kSeedHeavy : 0);
   }
   HeadSum<2> H;
   H.init();
@@ -66,96 +65,6 @@ __device__ __forceinline__ void voronoi_update(const Rep& R, const StepParams& P
   U_id[s] = id;
   atomicAdd(counts + linear_cell<2>(R, pout), 1u);
 }
-
-// The visiting order of the main kernel.  Each particle carries the cost
-// bucket of its last build in its seed word; the particles of every replica
-// are grouped by bucket (stably: sorted order inside a bucket), so that a
-// warp's lanes build cells of similar cost and the few expensive cells
-// share warps instead of holding back 31 cheap ones each.  Three passes:
-// bucket counts per block task, offsets per replica (one warp per replica,
-// one lane per bucket), and the stable scatter.
-__device__ __forceinline__ int order_bucket(const Rep& R, int li, const int32_t* __restrict__ S_id,
-                                            const int32_t* __restrict__ vor_seed_n) {
-  if (li >= R.n) return kVorBuckets;  // no particle: a bucket of its own, never counted
-  const int32_t w = vor_seed_n[R.p0 + S_id[R.p0 + li]];
-  return (w >> kSeedCostShift) & (kVorBuckets - 1);
-}
-
-__global__ void __launch_bounds__(kBlock) order_count_kernel(const Rep* __restrict__ reps,
-                                                             const BlockTask* __restrict__ tasks,
-                                                             const int32_t* __restrict__ S_id,
-                                                             const int32_t* __restrict__ vor_seed_n,
-                                                             uint32_t* __restrict__ table) {
-  __shared__ uint32_t cnt[kVorBuckets];
-  if (threadIdx.x < kVorBuckets) cnt[threadIdx.x] = 0;
-  __syncthreads();
-  const BlockTask t = tasks[blockIdx.x];
-  const Rep R = reps[t.rep];
-  const int b = order_bucket(R, t.first + (int)threadIdx.x, S_id, vor_seed_n);
-  if (b < kVorBuckets) atomicAdd(&cnt[b], 1u);
-  __syncthreads();
-  if (threadIdx.x < kVorBuckets) table[(size_t)blockIdx.x * kVorBuckets + threadIdx.x] = cnt[threadIdx.x];
-}
-
-// one warp per replica: lane b < kVorBuckets turns the counts of bucket b in
-// the replica's block tasks into write offsets (slot indices)
-__global__ void __launch_bounds__(32) order_offset_kernel(const Rep* __restrict__ reps,
-                                                          const int32_t* __restrict__ rep_task0,
-                                                          uint32_t* __restrict__ table) {
-  const int r = blockIdx.x;
-  const int lane = (int)threadIdx.x;
-  const int t0 = rep_task0[r], t1 = rep_task0[r + 1];
-  uint32_t total = 0;
-  if (lane < kVorBuckets)
-    for (int t = t0; t < t1; ++t) total += table[(size_t)t * kVorBuckets + lane];
-  // exclusive scan of the bucket totals across the lanes
-  uint32_t base = total;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t v = __shfl_up_sync(0xffffffffu, base, o);
-    if (lane >= o) base += v;
-  }
-  base -= total;
-  if (lane < kVorBuckets) {
-    uint32_t run = (uint32_t)reps[r].p0 + base;
-    for (int t = t0; t < t1; ++t) {
-      const uint32_t c = table[(size_t)t * kVorBuckets + lane];
-      table[(size_t)t * kVorBuckets + lane] = run;
-      run += c;
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kBlock) order_scatter_kernel(const Rep* __restrict__ reps,
-                                                               const BlockTask* __restrict__ tasks,
-                                                               const int32_t* __restrict__ S_id,
-                                                               const int32_t* __restrict__ vor_seed_n,
-                                                               const uint32_t* __restrict__ table,
-                                                               int32_t* __restrict__ order) {
-  __shared__ uint32_t wcnt[kBlock / 32][kVorBuckets + 1];  // per warp and bucket
-  for (int i = (int)threadIdx.x; i < (kBlock / 32) * (kVorBuckets + 1); i += kBlock) (&wcnt[0][0])[i] = 0u;
-  __syncthreads();
-  const BlockTask t = tasks[blockIdx.x];
-  const Rep R = reps[t.rep];
-  const int li = t.first + (int)threadIdx.x;
-  const int b = order_bucket(R, li, S_id, vor_seed_n);
-  const int lane = (int)(threadIdx.x & 31), wid = (int)(threadIdx.x >> 5);
-  // rank among the warp's lanes of the same bucket (lane order)
-  const unsigned same = __match_any_sync(0xffffffffu, b);
-  const uint32_t rank_w = (uint32_t)__popc(same & ((1u << lane) - 1u));
-  if (lane == __ffs(same) - 1) wcnt[wid][b] = (uint32_t)__popc(same);
-  __syncthreads();
-  if (b < kVorBuckets) {
-    uint32_t before = 0;  // earlier warps of the block, same bucket
-    for (int w2 = 0; w2 < wid; ++w2) before += wcnt[w2][b];
-    order[table[(size_t)blockIdx.x * kVorBuckets + b] + before + rank_w] = (int32_t)(R.p0 + li);
-  }
-}
-
-// 1: visit each replica's particles grouped by last step's cost (needs the seeds)
-#ifndef VK_VOR_ORDER
-#define VK_VOR_ORDER 1
-#endif
 
 // Heavy-cell hint: a cell that needed more than kHeavyHint candidates in the
 // main kernel, or more than kHeavyKeep in the warp kernel, is flagged in its
@@ -188,7 +97,7 @@ __global__ void __launch_bounds__(kVorBlock, VK_VOR_MIN_BLOCKS * kVorSplit) voro
     int2* __restrict__ U_pos, float2* __restrict__ U_dir, int32_t* __restrict__ U_id,
     uint32_t* __restrict__ counts, PhiAcc* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams Pm,
     int2* __restrict__ ovf_list, int32_t* __restrict__ ovf_count, int32_t* status, int32_t* __restrict__ vor_seed,
-    int32_t* __restrict__ vor_seed_n, const int32_t* __restrict__ slot_of, const int32_t* __restrict__ order) {
+    int32_t* __restrict__ vor_seed_n, const int32_t* __restrict__ slot_of) {
   __shared__ PhiShared phs;
   phi_block_begin(phs);
   const BlockTask t = tasks[blockIdx.x / kVorSplit];
@@ -198,8 +107,7 @@ __global__ void __launch_bounds__(kVorBlock, VK_VOR_MIN_BLOCKS * kVorSplit) voro
   float nnew[3] = {0.f, 0.f, 0.f};
   uint32_t n_cand = 0, n_runs = 0;
   if (li < R.n) {
-    // the replica's particles in the cost-grouped order (sorted order without seeds)
-    const int64_t s = order ? (int64_t)order[R.p0 + li] : R.p0 + li;
+    const int64_t s = R.p0 + li;
     const int2 p = S_pos[s];
     const float2 nv = S_dir[s];
     const int32_t pi[3] = {p.x, p.y, 0};
@@ -217,7 +125,7 @@ __global__ void __launch_bounds__(kVorBlock, VK_VOR_MIN_BLOCKS * kVorSplit) voro
                               : voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status, kHeavy, sd, &seen));
     if (ok) {
       voronoi_update(R, Pm, step, s, P, pi, ni, id, S_dir, U_pos, U_dir, U_id, counts, nnew,
-                     vor_seed ? vor_seed + gi * kVorSeed : nullptr, vor_seed_n + gi, seen > kHeavyHint, seen);
+                     vor_seed ? vor_seed + gi * kVorSeed : nullptr, vor_seed_n + gi, seen > kHeavyHint);
     } else {
       const int q = atomicAdd(ovf_count, 1);
       ovf_list[q] = make_int2((int)s, t.rep);
@@ -264,7 +172,7 @@ __global__ void __launch_bounds__(32 * kOvfWarps) voronoi_overflow_kernel(
         const float ni[3] = {nv.x, nv.y, 0.f};
         float nnew[3] = {0.f, 0.f, 0.f};
         voronoi_update(R, Pm, step, s, P, pi, ni, id, S_dir, U_pos, U_dir, U_id, counts, nnew,
-                       vor_seed ? vor_seed + gi * kVorSeed : nullptr, vor_seed_n + gi, seen > kHeavyKeep, seen);
+                       vor_seed ? vor_seed + gi * kVorSeed : nullptr, vor_seed_n + gi, seen > kHeavyKeep);
         PhiAcc* acc = phi_acc + ((size_t)(step % Pm.phi_cap) * (size_t)Pm.n_rep + (size_t)e.y) * 3;
         atomicAdd(acc + 0, (PhiAcc)phi_fixed(nnew[0]));
         atomicAdd(acc + 1, (PhiAcc)phi_fixed(nnew[1]));
@@ -325,24 +233,17 @@ static GridView grid_view(const Buffers& b) {
 
 cudaError_t launch_voronoi_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st) {
   const GridView G = grid_view(b);
-  const bool ordered = VK_VOR_ORDER && b.vor_order != nullptr;
-  if (ordered) {
-    order_count_kernel<<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, b.S_id, b.vor_seed_n, b.vor_bucket);
-    order_offset_kernel<<<g.n_rep, 32, 0, st>>>(g.reps, b.rep_task0, b.vor_bucket);
-    order_scatter_kernel<<<g.n_tasks, kBlock, 0, st>>>(g.reps, g.tasks, b.S_id, b.vor_seed_n, b.vor_bucket,
-                                                       b.vor_order);
-  }
-  voronoi_step_kernel<<<g.n_tasks * kVorSplit, kVorBlock, 0, st>>>(
-      g.reps, g.tasks, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id, G, (int2*)b.U_pos, (float2*)b.U_dir,
-      b.U_id, b.counts, b.phi_acc, b.d_step, P, b.ovf_list, b.ovf_count, b.d_status, b.vor_seed, b.vor_seed_n,
-      b.slot_of, ordered ? b.vor_order : nullptr);
-  voronoi_overflow_kernel<<<device_sm_count(), 32 * kOvfWarps, 0, st>>>(
-      g.reps, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id, G, (int2*)b.U_pos, (float2*)b.U_dir, b.U_id,
-      b.counts, b.phi_acc, b.d_step, P, b.ovf_list, b.ovf_count, b.d_status, b.vor_seed, b.vor_seed_n, b.slot_of);
+  voronoi_step_kernel<<<g.n_tasks * kVorSplit, kVorBlock, 0, st>>>(g.reps, g.tasks, (const int2*)b.S_pos, (const float2*)b.S_dir,
+                                                    b.S_id, G, (int2*)b.U_pos, (float2*)b.U_dir, b.U_id,
+                                                    b.counts, b.phi_acc, b.d_step, P, b.ovf_list,
+                                                    b.ovf_count, b.d_status, b.vor_seed, b.vor_seed_n,
+                                                    b.slot_of);
+  voronoi_overflow_kernel<<<device_sm_count(), 32 * kOvfWarps, 0, st>>>(g.reps, (const int2*)b.S_pos, (const float2*)b.S_dir, b.S_id,
+                                              G, (int2*)b.U_pos, (float2*)b.U_dir, b.U_id,
+                                              b.counts, b.phi_acc, b.d_step, P, b.ovf_list, b.ovf_count,
+                                              b.d_status, b.vor_seed, b.vor_seed_n, b.slot_of);
   return cudaGetLastError();
 }
-
-int voronoi_step_launches(const Buffers& b) { return (VK_VOR_ORDER && b.vor_order != nullptr) ? 5 : 2; }
 
 cudaError_t launch_voronoi_export(const Geometry& g, const Buffers& b, int rep, int n, int pass, int32_t* deg,
                                   const int64_t* out_off, int32_t* out_ids, cudaStream_t st) {

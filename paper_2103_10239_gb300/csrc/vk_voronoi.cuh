@@ -533,13 +533,6 @@ struct Seeds {
 // rim of a void), which goes straight to the warp-cooperative kernel
 constexpr int32_t kSeedCount = 0xFF;
 constexpr int32_t kSeedHeavy = 0x100;
-// ... and, in bits 9-12, the cost bucket of the last build: the bit length
-// of the number of candidates it examined (capped at 15)
-constexpr int kSeedCostShift = 9;
-
-__device__ __forceinline__ int32_t cost_bucket(uint32_t seen) {
-  return min(32 - __clz((int)seen), kVorBuckets - 1);
-}
 
 // flags of one cell build
 struct CellFlags {

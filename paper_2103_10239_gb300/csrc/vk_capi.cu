@@ -41,6 +41,10 @@ struct vk_sim {
   int32_t* st_pos = nullptr;
   float* st_dir = nullptr;
   float* st_theta = nullptr;
+  // tissue model scratch, allocated at the first vk_get_tissue call: per-slot
+  // cells and the outputs by id (area n, perimeter n, force 2n, energy 1)
+  TissueScratch tis{};
+  double* tis_out = nullptr;
   int64_t cells_cap = 0;
   std::vector<Rep> reps_h;
   std::vector<BlockTask> tasks_h;
@@ -679,21 +683,31 @@ vk_status vk_get_tissue(vk_sim* s, int32_t replica, double KA, double KP, double
   cudaEvent_t e0 = nullptr;
   vk_status st = record_begin(s, 4, &e0);
   if (st) return st;
-  // per-slot scratch over the whole state (slots of this replica are p0..p0+n-1)
+  // per-slot scratch over the whole state (slots of this replica are p0..p0+n-1),
+  // kept for later calls
   const size_t N = (size_t)s->n_total;
-  TissueScratch w{};
-  double *area_d = nullptr, *perim_d = nullptr, *force_d = nullptr, *energy_d = nullptr;
+  TissueScratch& w = s->tis;
   cudaError_t e = cudaSuccess;
-  const bool allocated =
-      !((e = dalloc(&w.nb_n, N)) || (e = dalloc(&w.nb_slot, N * kTissueCap)) ||
-        (e = dalloc(&w.nb_off, N * kTissueCap)) || (e = dalloc(&w.area, N)) || (e = dalloc(&w.perim, N)) ||
-        (area && (e = dalloc(&area_d, n))) || (perimeter && (e = dalloc(&perim_d, n))) ||
-        (force && (e = dalloc(&force_d, 2 * n))) || (energy && (e = dalloc(&energy_d, 1))));
-  if (allocated) {
-    const double unit = std::ldexp(1.0, -s->boxes[replica].frac_bits);
-    e = launch_tissue(s->g, s->b, replica, (int)n, KA, KP, A0, P0, unit, w, area_d, perim_d, force_d, energy_d,
-                      s->stream);
+  if (!s->tis_out) {
+    const bool ok = !((e = dalloc(&w.nb_n, N)) || (e = dalloc(&w.nb_slot, N * kTissueCap)) ||
+                      (e = dalloc(&w.nb_off, N * kTissueCap)) || (e = dalloc(&w.area, N)) ||
+                      (e = dalloc(&w.perim, N)) || (e = dalloc(&s->tis_out, 4 * N + 1)));
+    if (!ok) {
+      void* part[] = {w.nb_n, w.nb_slot, w.nb_off, w.area, w.perim, s->tis_out};
+      for (void* p : part)
+        if (p) cudaFree(p);
+      w = TissueScratch{};
+      s->tis_out = nullptr;
+      return cuda_fail(s, e, "tissue scratch");
+    }
   }
+  double* area_d = area ? s->tis_out : nullptr;
+  double* perim_d = perimeter ? s->tis_out + N : nullptr;
+  double* force_d = force ? s->tis_out + 2 * N : nullptr;
+  double* energy_d = energy ? s->tis_out + 4 * N : nullptr;
+  const double unit = std::ldexp(1.0, -s->boxes[replica].frac_bits);
+  e = launch_tissue(s->g, s->b, replica, (int)n, KA, KP, A0, P0, unit, w, area_d, perim_d, force_d, energy_d,
+                    s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e == cudaSuccess) st = record_end(s, 4, e0, energy ? 3 : 2);
   if (e == cudaSuccess && st == VK_OK) st = read_status(s);
@@ -703,9 +717,6 @@ vk_status vk_get_tissue(vk_sim* s, int32_t replica, double KA, double KP, double
     if (e == cudaSuccess && force) e = cudaMemcpy(force, force_d, sizeof(double) * 2 * n, cudaMemcpyDefault);
     if (e == cudaSuccess && energy) e = cudaMemcpy(energy, energy_d, sizeof(double), cudaMemcpyDefault);
   }
-  void* bufs[] = {w.nb_n, w.nb_slot, w.nb_off, w.area, w.perim, area_d, perim_d, force_d, energy_d};
-  for (void* p : bufs)
-    if (p) cudaFree(p);
   if (e != cudaSuccess) return cuda_fail(s, e, "tissue model");
   return st;
 }
@@ -844,7 +855,8 @@ void vk_destroy(vk_sim* s) {
                   s->b.ovf_list, s->b.ovf_count, s->reps_d, s->tasks_d, s->b.sub_s, s->b.sub_base,
                   s->b.sub_count, s->b.sub_off, s->b.bsum2, s->d_stats, s->b.bounds,
                   s->st_pos, s->st_dir, s->st_theta, s->b.S_hint, s->b.U_hint, s->b.vor_seed,
-                  s->b.vor_seed_n, s->b.slot_of};
+                  s->b.vor_seed_n, s->b.slot_of, s->tis.nb_n, s->tis.nb_slot, s->tis.nb_off, s->tis.area,
+                  s->tis.perim, s->tis_out};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);

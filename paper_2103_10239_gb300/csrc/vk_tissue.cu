@@ -45,19 +45,24 @@ __global__ void __launch_bounds__(64) tissue_cells_kernel(const Rep* __restrict_
                                                           TissueParams T, int32_t* __restrict__ nb_n,
                                                           int32_t* __restrict__ nb_slot, int2* __restrict__ nb_off,
                                                           double* __restrict__ area, double* __restrict__ perim,
-                                                          int32_t* status) {
+                                                          int32_t* status, const int32_t* __restrict__ vor_seed,
+                                                          const int32_t* __restrict__ vor_seed_n,
+                                                          const int32_t* __restrict__ slot_of) {
   const Rep R = reps[rep];
   for (int li = blockIdx.x * blockDim.x + threadIdx.x; li < R.n; li += gridDim.x * blockDim.x) {
     const int64_t s = R.p0 + li;
     const int2 p = S_pos[s];
     const int32_t pi[3] = {p.x, p.y, 0};
     const int32_t id = S_id[s];
-    const Seeds none{nullptr, 0, nullptr};
+    // a Voronoi-rule sim's last neighbors seed the cell (any seeds give the same cell)
+    const int64_t gi = R.p0 + id;
+    const Seeds sd{vor_seed ? vor_seed + gi * kVorSeed : nullptr, vor_seed ? vor_seed_n[gi] & kSeedCount : 0,
+                   slot_of};
     Poly<kFastCap> P;
     int m = 0;
     area[s] = 0.0;
     perim[s] = 0.0;
-    if (!voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status, 0u, none, nullptr) || P.m > kTissueCap) {
+    if (!voronoi_cell(R, s, pi, id, S_pos, S_id, G, P, status, 0u, sd, nullptr) || P.m > kTissueCap) {
       set_status(status, kStCapacity);
     } else if (P.nt > 0) {
       set_status(status, kStDegenerate);  // coincident particles: one site, no cell each
@@ -258,7 +263,8 @@ cudaError_t launch_tissue(const Geometry& g, const Buffers& b, int rep, int n, d
   const TissueParams T{KA, KP, A0, P0, unit};
   const int nb = std::min((n + 63) / 64, device_sm_count() * 16);
   tissue_cells_kernel<<<nb, 64, 0, st>>>(g.reps, rep, (const int2*)b.S_pos, b.S_id, tissue_view(b), T, w.nb_n,
-                                         w.nb_slot, w.nb_off, w.area, w.perim, b.d_status);
+                                         w.nb_slot, w.nb_off, w.area, w.perim, b.d_status, b.vor_seed, b.vor_seed_n,
+                                         b.slot_of);
   const int nf = std::min((n + 127) / 128, device_sm_count() * 16);
   tissue_force_kernel<<<nf, 128, 0, st>>>(g.reps, rep, b.S_id, T, w.nb_n, w.nb_slot, w.nb_off, w.area, w.perim,
                                           force_out, area_out, perim_out, b.d_status);

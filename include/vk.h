@@ -110,9 +110,9 @@ typedef struct {
                            Dense coarse cells get sub-grids of about 2 particles per sub-cell.
                            Results never depend on it; only the speed does. */
   int32_t phi_capacity; /* order-parameter history kept per replica; 0 = 4096 steps */
-  int32_t knn_search;   /* 2D kNN search: 0 = radius first (default), 1 = per-particle walk only.
-                           Results never depend on it; only the speed does. */
-  float search_halo;    /* radius first: half-width of a particle's search square, as a multiple
+  int32_t knn_search;   /* kNN search: 0 = radius first (default; a square in 2D, a cube in 3D),
+                           1 = the ring walk only.  Results never depend on it; only the speed does. */
+  float search_halo;    /* radius first: half-width of a particle's search square (cube), as a multiple
                            of its k-th neighbor distance at the previous step; 0 = default (1.15).
                            Results never depend on it; only the speed does. */
   float search_halo_step; /* radius first: plus this multiple of the distance a particle moves

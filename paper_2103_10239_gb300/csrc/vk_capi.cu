@@ -478,8 +478,8 @@ vk_status build_sim(int32_t n_rep, const int64_t* n_r, const int32_t* pos_q, con
       (e = dalloc(&s->d_stats, kCounters)) ||
       (e = dalloc(&s->tasks_d, s->tasks_h.size())))
     return bail(cuda_fail(s, e, "cudaMalloc"));
-  if (params->rule == VK_RULE_KNN && dim == 2) {
-    if ((e = dalloc(&s->b.S_hint, N)) || (e = dalloc(&s->b.U_hint, N)) || (e = prepare_knn2()))
+  if (params->rule == VK_RULE_KNN) {
+    if ((e = dalloc(&s->b.S_hint, N)) || (e = dalloc(&s->b.U_hint, N)) || (dim == 2 && (e = prepare_knn2())))
       return bail(cuda_fail(s, e, "kNN search buffers"));
   }
   if (params->rule == VK_RULE_VORONOI && !params->voronoi_rebuild) {

@@ -450,7 +450,7 @@ cudaError_t launch_scatter(const Geometry& g, const Buffers& b, const StepParams
   else
     scatter_kernel<3><<<g.n_tasks, kBlock, 0, st>>>(
         g.reps, g.tasks, (const int4*)b.U_pos, (const float4*)b.U_dir, b.U_id, b.U_rank, b.bounds, G,
-        (int4*)b.S_pos, (float4*)b.S_dir, b.S_id, nullptr, nullptr, nullptr, advance_step, b.d_step, b.phi_acc,
+        (int4*)b.S_pos, (float4*)b.S_dir, b.S_id, b.U_hint, b.S_hint, nullptr, advance_step, b.d_step, b.phi_acc,
         P.n_rep, P.phi_cap, b.ovf_count);
   return cudaGetLastError();
 }

@@ -97,13 +97,108 @@ __device__ __forceinline__ void knn_search(const Rep& R, int64_t self, const int
   grid_walk3(R, pi, G, run, stop);
 }
 
+// ---------------------------------------------------------------------------
+// Radius first (3D): each particle scans the cube [p - a, p + a]^3, a a
+// little above its k-th neighbor distance at the previous step, as the
+// x-row segments of the cells it meets (each a contiguous run of the sorted
+// arrays, with the periodic image it lies in).  Every candidate with exact
+// squared distance D <= tau = (a+1)^2 - 1 goes into the register top-k by
+// (D, id); nothing outside the cube is that close, so once the k-th best is
+// <= tau the list is exact, ties included.  Otherwise one larger cube, then
+// the ring walk.
+// ---------------------------------------------------------------------------
+
+// unwrapped cell index of an unwrapped coordinate, -L <= x < 2L
+__device__ __forceinline__ int ucell3(int64_t x, int n, const uint32_t* __restrict__ bnd, float inv_w, int64_t L) {
+  if (x < 0) return cell_of_tab((uint32_t)(x + L), n, bnd, inv_w) - n;
+  if (x >= L) return cell_of_tab((uint32_t)(x - L), n, bnd, inv_w) + n;
+  return cell_of_tab((uint32_t)x, n, bnd, inv_w);
+}
+
+// the coordinate of the particle shifted into the image an unwrapped cell
+// index u lies in: offsets x_j - that are exact in wrapping 32-bit arithmetic
+__device__ __forceinline__ uint32_t image_ref(uint32_t p, int u, int n, uint32_t L) {
+  return u < 0 ? p + L : (u >= n ? p - L : p);
+}
+
+// the k nearest from the cube of half-width a; true when they are exact
+template <int KC>
+__device__ __forceinline__ bool cube_search(const Rep& R, const uint32_t* __restrict__ bounds, const GridView& G,
+                                            const int4* __restrict__ pos, const int32_t* __restrict__ ids,
+                                            int64_t self, const int32_t* pi, int64_t a, TopK<KC>& T,
+                                            uint32_t* n_cand, uint32_t* n_runs) {
+  int lo[3], hi[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const int64_t L = R.L[ax];
+    if (2 * (2 * a + 1) >= L) return false;
+    const uint32_t* bnd = bounds + R.bnd[ax];
+    lo[ax] = ucell3((int64_t)pi[ax] - a, R.nc[ax], bnd, R.inv_w[ax], L);
+    hi[ax] = ucell3((int64_t)pi[ax] + a, R.nc[ax], bnd, R.inv_w[ax], L);
+    if (hi[ax] - lo[ax] + 1 > R.nc[ax]) return false;
+  }
+  const uint64_t tau = (uint64_t)(a + 1) * (uint64_t)(a + 1) - 1;
+  const int nx = R.nc[0], ny = R.nc[1], nz = R.nc[2];
+  for (int uz = lo[2]; uz <= hi[2]; ++uz) {
+    const int cz = uz < 0 ? uz + nz : (uz >= nz ? uz - nz : uz);
+    const uint32_t oz = image_ref((uint32_t)pi[2], uz, nz, R.L[2]);
+    for (int uy = lo[1]; uy <= hi[1]; ++uy) {
+      const int cy = uy < 0 ? uy + ny : (uy >= ny ? uy - ny : uy);
+      const uint32_t oy = image_ref((uint32_t)pi[1], uy, ny, R.L[1]);
+      const int64_t row = R.c0 + ((int64_t)cz * ny + cy) * nx;
+      // the x range splits at the period into up to three segments
+      for (int seg = 0; seg < 3; ++seg) {
+        int xs = seg == 0 ? lo[0] : (seg == 1 ? max(lo[0], 0) : max(lo[0], nx));
+        int xe = seg == 0 ? min(hi[0], -1) : (seg == 1 ? min(hi[0], nx - 1) : hi[0]);
+        if (xs > xe) continue;
+        const uint32_t ox = image_ref((uint32_t)pi[0], xs, nx, R.L[0]);
+        const int wxs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+        const uint32_t qb = __ldg(G.off + row + wxs), qe = __ldg(G.off + row + wxs + (xe - xs) + 1);
+        if (n_cand) {
+          *n_cand += qe - qb;
+          *n_runs += 1;
+        }
+        for (uint32_t q = qb; q < qe; ++q) {
+          const int4 pj = __ldg(pos + q);
+          const int32_t dx = (int32_t)((uint32_t)pj.x - ox), dy = (int32_t)((uint32_t)pj.y - oy),
+                        dz = (int32_t)((uint32_t)pj.z - oz);
+          const uint64_t D = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy) +
+                             (uint64_t)((int64_t)dz * dz);
+          if (D <= tau && D <= T.d[KC - 1] && (int64_t)q != self) {
+            const int32_t idj = __ldg(ids + q);
+            if (D < T.d[KC - 1] || idj < T.id[KC - 1]) topk_insert<KC>(T, D, idj, (int32_t)q);
+          }
+        }
+      }
+    }
+  }
+  return T.d[KC - 1] <= tau;
+}
+
+// search radius without a hint: from the density of the particle's own cell
+__device__ __forceinline__ float cube_radius_estimate(const Rep& R, const uint32_t* __restrict__ bounds,
+                                                      const GridView& G, const int32_t* pi, int k) {
+  int c[3];
+  float vol = 1.f;
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const uint32_t* bnd = bounds + R.bnd[ax];
+    c[ax] = cell_of_tab((uint32_t)pi[ax], R.nc[ax], bnd, R.inv_w[ax]);
+    vol *= (float)(__ldg(bnd + c[ax] + 1) - __ldg(bnd + c[ax]));
+  }
+  const int64_t gc = R.c0 + ((int64_t)c[2] * R.nc[1] + c[1]) * R.nc[0] + c[0];
+  const float m = (float)max(__ldg(G.off + gc + 1) - __ldg(G.off + gc), 1u);
+  return 1.3f * cbrtf(3.f * (float)k * vol / (4.f * 3.14159265f * m));
+}
+
 template <int DIM, int KC>
 __global__ void __launch_bounds__(kBlock) knn_step_kernel(
     const Rep* __restrict__ reps, const BlockTask* __restrict__ tasks,
     const typename Vec<DIM>::P* __restrict__ S_pos, const typename Vec<DIM>::F* __restrict__ S_dir,
     const int32_t* __restrict__ S_id, GridView G, typename Vec<DIM>::P* __restrict__ U_pos,
     typename Vec<DIM>::F* __restrict__ U_dir, int32_t* __restrict__ U_id,
-    uint32_t* __restrict__ counts, PhiAcc* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P) {
+    uint32_t* __restrict__ counts, PhiAcc* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams P,
+    const uint32_t* __restrict__ bounds, const float* __restrict__ S_hint, float* __restrict__ U_hint) {
   using PV = typename Vec<DIM>::P;
   using FV = typename Vec<DIM>::F;
   const BlockTask t = tasks[blockIdx.x];
@@ -120,9 +215,24 @@ __global__ void __launch_bounds__(kBlock) knn_step_kernel(
     unpack(S_dir[s], ni);
     const int32_t id = S_id[s];
     TopK<KC> T;
-    topk_init<KC>(T, P.k);
-    if (P.stats) knn_search<DIM, KC>(R, s, pi, S_pos, S_id, G, T, &n_cand, &n_runs);
-    else knn_search<DIM, KC>(R, s, pi, S_pos, S_id, G, T);
+    bool done = false;
+    if (S_hint && P.knn_search == 0) {
+      // radius first: the hinted cube, then one larger
+      const float hint = S_hint[s];
+      float r = hint > 0.f ? P.halo_alpha * hint : cube_radius_estimate(R, bounds, G, pi, P.k);
+      for (int tr = 0; tr < 2 && !done; ++tr) {
+        topk_init<KC>(T, P.k);
+        done = cube_search<KC>(R, bounds, G, S_pos, S_id, s, pi, (int64_t)ceilf(fminf(r, 1.0e9f)), T,
+                               P.stats ? &n_cand : nullptr, &n_runs);
+        r *= 1.6f;
+      }
+    }
+    if (!done) {
+      topk_init<KC>(T, P.k);
+      if (P.stats) knn_search<DIM, KC>(R, s, pi, S_pos, S_id, G, T, &n_cand, &n_runs);
+      else knn_search<DIM, KC>(R, s, pi, S_pos, S_id, G, T);
+    }
+    if (U_hint) U_hint[s] = sqrtf((float)T.d[KC - 1]) * 1.0001f + 1.f;
     HeadSum<DIM> H;
     H.init();
     if (P.include_self) H.add(ni, P.sum_mode);
@@ -181,7 +291,7 @@ cudaError_t step_dispatch(const Geometry& g, const Buffers& b, const StepParams&
   using FV = typename Vec<DIM>::F;
   knn_step_kernel<DIM, KC><<<g.n_tasks, kBlock, 0, st>>>(
       g.reps, g.tasks, (const PV*)b.S_pos, (const FV*)b.S_dir, b.S_id, grid_view(b), (PV*)b.U_pos,
-      (FV*)b.U_dir, b.U_id, b.counts, b.phi_acc, b.d_step, P);
+      (FV*)b.U_dir, b.U_id, b.counts, b.phi_acc, b.d_step, P, b.bounds, b.S_hint, b.U_hint);
   return cudaGetLastError();
 }
 

@@ -106,3 +106,14 @@ def test_cells_over_32_edges_report_capacity():
         with pytest.raises(vk.VKError) as e:
             sim.tissue(1.0, 1.0, 1.0, 3.8)
         assert e.value.status == vk.VK_ERR_CAPACITY
+
+
+def test_repeated_calls_and_steps_between_them():
+    """The scratch is kept between calls, and a Voronoi sim seeds the cells
+    with its last neighbors: every call still matches the oracle."""
+    w = W.uniform_system(2500, 50.0, 16, 2, input_seed=69, rule="voronoi", k=0, v0=0.3, eta=0.4)
+    with vk.from_workload(w) as sim:
+        for KA, KP, A0, P0 in PARAMS:
+            pos, _, _, _ = sim.state()
+            _compare(sim, pos, w.box_q, 16, KA, KP, A0, P0)
+            sim.step(3)

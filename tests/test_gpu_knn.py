@@ -127,6 +127,32 @@ def test_3d_knn_vectorial():
             check_step(sim, w, "knn")
 
 
+@pytest.mark.parametrize("n,L,k", [(40, 3.4, 7), (200, 5.8, 7), (700, 8.9, 16), (1500, 11.4, 32), (3000, 14.4, 1)])
+def test_3d_radius_first_steps(n, L, k):
+    """The 3D step searches the hinted cube first (the ring walk serves what
+    the cube cannot: tiny boxes, missed squares); several teacher-forced steps
+    so that the hints are in use."""
+    w = W.uniform_system(n, L, 16, 3, input_seed=n + k, rule="knn", k=k, noise="vectorial", eta=0.3)
+    with vk.from_workload(w) as sim:
+        for _ in range(4):
+            check_step(sim, w, "knn")
+
+
+def test_3d_cubic_lattice_ties():
+    """Equal distances everywhere: the cube keeps the (D, id) order exactly."""
+    m, a = 6, 1 << 16
+    i, j, l = np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij")
+    pos = np.stack([i.ravel() * a, j.ravel() * a, l.ravel() * a], axis=1).astype(np.int32)
+    box = (m * a,) * 3
+    d = W.random_dirs(pos.shape[0], dim=3)
+    for k in (6, 7, 18, 19):
+        w = W.Workload(name="lattice3", dim=3, pos_q=pos, dir=d, theta=None, box_q=box, frac_bits=16,
+                       rule="knn", k=k, v0=0.0, dt=1.0, eta=0.2, noise="vectorial")
+        with vk.from_workload(w) as sim:
+            for _ in range(3):
+                check_step(sim, w, "knn")
+
+
 def test_3d_full_size_sampled():
     w = W.knn_3d()
     rng = np.random.default_rng(1)

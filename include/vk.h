@@ -106,14 +106,14 @@ typedef struct {
   int32_t advect_new;   /* 1: advect with n_i(t+dt) instead of n_i(t) (default 0) */
   int32_t sum_mode;     /* vk_sum_mode for the heading sums (default compensated) */
   float cell_occupancy; /* target particles per coarse cell of the search grid at the mean
-                           density; 0 = default (256 in 2D, 2 for Voronoi, 3 in 3D).
+                           density; 0 = default (256 in 2D, 2 for Voronoi, 1.5 in 3D).
                            Dense coarse cells get sub-grids of about 2 particles per sub-cell.
                            Results never depend on it; only the speed does. */
   int32_t phi_capacity; /* order-parameter history kept per replica; 0 = 4096 steps */
   int32_t knn_search;   /* kNN search: 0 = radius first (default; a square in 2D, a cube in 3D),
                            1 = the ring walk only.  Results never depend on it; only the speed does. */
   float search_halo;    /* radius first: half-width of a particle's search square (cube), as a multiple
-                           of its k-th neighbor distance at the previous step; 0 = default (1.15).
+                           of its k-th neighbor distance at the previous step; 0 = default (1.15 in 2D, 1.3 in 3D).
                            Results never depend on it; only the speed does. */
   float search_halo_step; /* radius first: plus this multiple of the distance a particle moves
                            in one step (v0 dt); < 0 = default (0).  Speed only. */

@@ -120,7 +120,8 @@ StepParams step_params(const vk_sim* s) {
   P.n_rep = s->n_rep;
   P.phi_cap = s->phi_cap;
   P.knn_search = s->prm.knn_search;
-  P.halo_alpha = s->prm.search_halo > 0.f ? s->prm.search_halo : 1.15f;
+  // measured defaults: squares 1.15 x the last k-th distance (2D), cubes 1.3 x (3D)
+  P.halo_alpha = s->prm.search_halo > 0.f ? s->prm.search_halo : (s->dim == 3 ? 1.3f : 1.15f);
   P.halo_beta = s->prm.search_halo_step >= 0.f ? s->prm.search_halo_step : 0.f;
   P.fov_cq = fov_cq(s->prm);
   P.stats = (s->prof && s->prof_counters) ? s->d_stats : nullptr;
@@ -152,8 +153,8 @@ float default_occupancy(const vk_params& p, int dim, int64_t n_total, int n_rep)
   if (p.rule == VK_RULE_VORONOI) return 2.0f;
   // 2D kNN and metric: coarse cells of a few hundred particles split into
   // sub-grids (the radius-first search measured fastest at 256 on uniform
-  // and clustered flocks)
-  return dim == 2 ? 256.0f : 3.0f;
+  // and clustered flocks); 3D: cells of about 1.5 particles (the cube search)
+  return dim == 2 ? 256.0f : 1.5f;
 }
 
 // per-replica search grid for a target occupancy; fills nc, c0 and the cell

@@ -20,6 +20,9 @@ Functions and the passages of arxiv 2103.10239 they follow:
 * :func:`voronoi` -- Voronoi neighbors via the Delaunay triangulation's
   empty-circumcircle definition and the Delaunay/Voronoi duality (Sec.
   "Computational tools: Voronoi neighbor lists").
+* :func:`voronoi3` -- 3D Voronoi neighbors (same section): each cell by
+  exact half-space clipping with the bisectors of the periodic images,
+  neighbors sharing a face of positive area, and the cell volumes.
 * :func:`vicsek_step` -- Eq. (1) advection and Eq. (2) alignment with noise.
 * :func:`order_parameter` -- the polar order |sum n_i|/N.
 * :func:`philox4x32_10` -- the counter-based generator the noise is drawn from.
@@ -108,6 +111,11 @@ def _load():
         lib.orc_tissue.argtypes = [ctypes.c_int64, i32p, i64p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, f64p, f64p, f64p, f64p]
         lib.orc_tissue.restype = ctypes.c_int
+        lib.orc_voronoi3.argtypes = [ctypes.c_int64, i32p, i64p, i64p, ctypes.c_int64, ctypes.c_int32, i32p,
+                                     i32p, f64p]
+        lib.orc_voronoi3.restype = ctypes.c_int
+        lib.orc_voronoi3_side.argtypes = [i64p, i64p, i64p, i64p]
+        lib.orc_voronoi3_side.restype = ctypes.c_int
         lib.orc_num_threads.argtypes = []
         lib.orc_num_threads.restype = ctypes.c_int
         _lib = lib
@@ -232,6 +240,49 @@ def voronoi(pos_q: np.ndarray, box_q):
     return off, ids[: int(nnz[0])]
 
 
+def voronoi3(pos_q: np.ndarray, box_q, query: Optional[np.ndarray] = None, volumes: bool = False):
+    """Voronoi neighbors in a periodic 3D box: the particles whose cell shares
+    a face of positive area with the cell of each (query) particle.  Returns
+    (offsets int64[nq+1], ids int32[nnz]) with rows sorted by id, plus the
+    cell volumes in grid units^3 (float64[nq]) when ``volumes``."""
+    lib = _load()
+    pos = np.ascontiguousarray(pos_q, dtype=np.int32)
+    n = pos.shape[0]
+    box = _box(box_q, 3)
+    q = None if query is None else np.ascontiguousarray(query, dtype=np.int64)
+    nq = n if q is None else q.shape[0]
+    vol = np.zeros(max(1, nq), dtype=np.float64)
+    maxdeg = 64
+    while True:
+        deg = np.zeros(max(1, nq), dtype=np.int32)
+        ids = np.zeros(max(1, nq) * maxdeg, dtype=np.int32)
+        rc = lib.orc_voronoi3(n, _ptr(pos, ctypes.c_int32), _ptr(box, ctypes.c_int64),
+                              None if q is None else _ptr(q, ctypes.c_int64), nq, maxdeg,
+                              _ptr(deg, ctypes.c_int32), _ptr(ids, ctypes.c_int32), _ptr(vol, ctypes.c_double))
+        if rc == 1 and nq and int(deg[:nq].max()) > maxdeg:
+            maxdeg = int(deg[:nq].max())
+            continue
+        _check(rc, "voronoi3")
+        break
+    deg = deg[:nq].astype(np.int64)
+    off = np.zeros(nq + 1, dtype=np.int64)
+    np.cumsum(deg, out=off[1:])
+    rows = ids.reshape(max(1, nq), maxdeg)
+    out = np.concatenate([rows[r, : deg[r]] for r in range(nq)]) if nq else np.zeros(0, np.int32)
+    out = out.astype(np.int32)
+    if volumes:
+        return off, out, vol[:nq].copy()
+    return off, out
+
+
+def voronoi3_side(da, db, dc, de) -> int:
+    """Sign of d_e.y - |d_e|^2 at the point y where d_x.y = |d_x|^2 for
+    x = a, b, c (the exact vertex test of :func:`voronoi3`)."""
+    lib = _load()
+    arrs = [np.asarray(p, dtype=np.int64).copy() for p in (da, db, dc, de)]
+    return int(lib.orc_voronoi3_side(*[_ptr(p, ctypes.c_int64) for p in arrs]))
+
+
 def delaunay_star_triangles(pos_q: np.ndarray, box_q):
     """Triangles of the periodic Delaunay triangulation touching an original
     point: (coords int64 (T,3,2) in tiled coordinates, ids int32 (T,3))."""
@@ -344,5 +395,5 @@ def neighbors(pos_q: np.ndarray, box_q, rule: str, k: int = 7):
     if rule == "knn":
         return csr_from_dense(knn(pos_q, box_q, k))
     if rule == "voronoi":
-        return voronoi(pos_q, box_q)
+        return voronoi3(pos_q, box_q) if np.asarray(pos_q).shape[1] == 3 else voronoi(pos_q, box_q)
     raise ValueError(rule)

@@ -25,6 +25,11 @@
  *   - the polar order parameter |sum_i n_i| / N;
  *   - the k nearest neighbors inside a field of view and the metric (r0)
  *     neighbors (Sec. "Metric and topological flocking models");
+ *   - the 3D Voronoi neighbors (same section): every cell built by exact
+ *     clipping with the bisector half-spaces of the periodic images of the
+ *     other particles, neighbors being the sites whose plane carries a face
+ *     of positive area (insphere-type integer determinants decide every
+ *     vertex); coincident particles are reported as degenerate;
  *   - the Voronoi tissue model (Sec. "Geometric models of dense tissue"):
  *     cell areas and perimeters, the energy of Eq. (vmEnergy) and the forces
  *     of Sec. "Voronoi model forces" by the chain rule through the vertices.
@@ -1042,6 +1047,549 @@ int orc_tissue(int64_t n, const int32_t* pos, const int64_t* box, double unit, d
   free(beg); free(sa); free(sb); free(ord); free(hx); free(hy); free(fill);
   vtess_free(&V);
   return rc;
+}
+
+/* ======================================================================== */
+/* 3D Voronoi neighbors (Sec. "Computational tools: Voronoi neighbor lists": */
+/* the Voronoi cell of a particle holds the points closer to it than to any  */
+/* other particle; two particles are neighbors when their cells share a      */
+/* face).                                                                    */
+/*                                                                          */
+/* The cell is the intersection of the half-spaces {x : d.x <= |d|^2 / 2},   */
+/* one for every periodic image d (offset from the particle) of every other  */
+/* particle, and of the particle's own images.  It is built by clipping a    */
+/* polytope held as faces (one per plane) with vertex loops.  A vertex is    */
+/* the meeting point y/2 of three planes (d_a.y = w_a, d_b.y = w_b,          */
+/* d_c.y = w_c with w = |d|^2); whether it lies beyond the plane of a site e */
+/* is decided exactly: with M the 3x3 matrix of rows d_a, d_b, d_c,          */
+/*   det [d_a w_a; d_b w_b; d_c w_c; d_e w_e] = det(M) (w_e - d_e.y),        */
+/* so sign(d_e.y - w_e) = -sign(det4) sign(det M), both integer determinants */
+/* (the 4x4 one is the insphere test of the particle, a, b, c and e).        */
+/* Neighbors are the sites whose plane carries a face of positive area; a    */
+/* plane that meets the cell in an edge or a vertex only (the diagonal       */
+/* neighbors of a cubic lattice) does not count.  Coincident particles are   */
+/* reported as degenerate.                                                   */
+/* ======================================================================== */
+
+typedef struct {
+  int64_t d[3]; /* offset of the site image from the particle (grid units) */
+  i128 w;       /* |d|^2 */
+  int32_t id;   /* particle id of the site; -1 for an image of the particle itself */
+} c3plane;
+
+typedef struct {
+  int32_t p[3]; /* the three planes defining the vertex */
+  int32_t alive;
+  double x[3];  /* approximate position (grid units): search radius and volume only */
+} c3vert;
+
+typedef struct {
+  int32_t plane, alive, n, cap;
+  int32_t* v;   /* vertex loop, counter-clockwise seen from outside the cell */
+} c3face;
+
+typedef struct {
+  c3plane* pl; int32_t npl, cappl;
+  c3vert* vt; int32_t nvt, capvt;
+  c3face* fc; int32_t nfc, capfc;
+  int8_t* sg; int32_t capsg;            /* side of every vertex for the current clip */
+  int32_t* memo; int32_t nmemo, capmemo; /* crossing vertices of the current clip: (a, b, x) */
+  int32_t* eg; int32_t neg, capeg;      /* boundary edges of the new face: (tail, head) */
+  int32_t* tmp; int32_t captmp;
+} c3cell;
+
+static int c3_grow(void** p, int32_t* cap, int64_t need, size_t elem) {
+  if (need <= *cap) return 0;
+  int64_t nc = *cap ? *cap : 16;
+  while (nc < need) nc *= 2;
+  if (nc > INT32_MAX) return 1;
+  void* q = realloc(*p, (size_t)nc * elem);
+  if (!q) return 1;
+  *p = q;
+  *cap = (int32_t)nc;
+  return 0;
+}
+
+static void c3_free(c3cell* C) {
+  for (int32_t f = 0; f < C->capfc; ++f) free(C->fc[f].v);
+  free(C->pl); free(C->vt); free(C->fc); free(C->sg); free(C->memo); free(C->eg); free(C->tmp);
+  memset(C, 0, sizeof(*C));
+}
+
+static i128 det3_i(const int64_t* a, const int64_t* b, const int64_t* c) {
+  return (i128)a[0] * ((i128)b[1] * c[2] - (i128)b[2] * c[1]) -
+         (i128)a[1] * ((i128)b[0] * c[2] - (i128)b[2] * c[0]) +
+         (i128)a[2] * ((i128)b[0] * c[1] - (i128)b[1] * c[0]);
+}
+
+static double i256_to_double(i256 a) {
+  const int neg = (a.w[3] >> 63) != 0;
+  if (neg) a = i256_neg(a);
+  double r = 0.0;
+  for (int t = 3; t >= 0; --t) r = r * 18446744073709551616.0 + (double)a.w[t];
+  return neg ? -r : r;
+}
+
+/* Side of vertex v of the cell with respect to the plane of site e:
+ * +1 strictly beyond it, 0 on it, -1 strictly inside. */
+static int c3_side(const c3cell* C, int32_t v, int32_t e) {
+  const c3plane* A = &C->pl[C->vt[v].p[0]];
+  const c3plane* B = &C->pl[C->vt[v].p[1]];
+  const c3plane* D = &C->pl[C->vt[v].p[2]];
+  const c3plane* E = &C->pl[e];
+  const i128 m = det3_i(A->d, B->d, D->d);
+  /* det4 expanded along its last column (w) */
+  i256 t = i256_mul(-A->w, det3_i(B->d, D->d, E->d));
+  t = i256_add(t, i256_mul(B->w, det3_i(A->d, D->d, E->d)));
+  t = i256_add(t, i256_mul(-D->w, det3_i(A->d, B->d, E->d)));
+  t = i256_add(t, i256_mul(E->w, m));
+  const int s4 = i256_sign(t), sm = (m > 0) - (m < 0);
+  return -s4 * sm;
+}
+
+/* new vertex of planes (a, b, c); its approximate position by Cramer's rule
+ * on the exact integer determinants */
+static int32_t c3_new_vertex(c3cell* C, int32_t a, int32_t b, int32_t c) {
+  if (c3_grow((void**)&C->vt, &C->capvt, (int64_t)C->nvt + 1, sizeof(c3vert))) return -1;
+  c3vert* V = &C->vt[C->nvt];
+  V->p[0] = a; V->p[1] = b; V->p[2] = c;
+  V->alive = 1;
+  const int64_t* M[3] = {C->pl[a].d, C->pl[b].d, C->pl[c].d};
+  const i128 w[3] = {C->pl[a].w, C->pl[b].w, C->pl[c].w};
+  /* cofactors of M: cyclic index form */
+  i128 cf[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int k = 0; k < 3; ++k) {
+      const int r0 = (r + 1) % 3, r1 = (r + 2) % 3, k0 = (k + 1) % 3, k1 = (k + 2) % 3;
+      cf[r][k] = (i128)M[r0][k0] * M[r1][k1] - (i128)M[r0][k1] * M[r1][k0];
+    }
+  const i128 det = (i128)M[0][0] * cf[0][0] + (i128)M[0][1] * cf[0][1] + (i128)M[0][2] * cf[0][2];
+  const double dd = (double)det;
+  for (int k = 0; k < 3; ++k) {
+    i256 num = i256_add(i256_add(i256_mul(w[0], cf[0][k]), i256_mul(w[1], cf[1][k])), i256_mul(w[2], cf[2][k]));
+    V->x[k] = 0.5 * i256_to_double(num) / dd; /* x = y / 2 */
+  }
+  return C->nvt++;
+}
+
+static int32_t c3_add_plane(c3cell* C, const int64_t* d, int32_t id) {
+  if (c3_grow((void**)&C->pl, &C->cappl, (int64_t)C->npl + 1, sizeof(c3plane))) return -1;
+  c3plane* P = &C->pl[C->npl];
+  for (int a = 0; a < 3; ++a) P->d[a] = d[a];
+  P->w = (i128)d[0] * d[0] + (i128)d[1] * d[1] + (i128)d[2] * d[2];
+  P->id = id;
+  return C->npl++;
+}
+
+static int c3_face_push(c3face* F, int32_t v) {
+  if (c3_grow((void**)&F->v, &F->cap, (int64_t)F->n + 1, sizeof(int32_t))) return 1;
+  F->v[F->n++] = v;
+  return 0;
+}
+
+static int32_t c3_new_face(c3cell* C, int32_t plane) {
+  if (C->nfc == C->capfc) {
+    const int32_t old = C->capfc;
+    if (c3_grow((void**)&C->fc, &C->capfc, (int64_t)C->nfc + 1, sizeof(c3face))) return -1;
+    for (int32_t f = old; f < C->capfc; ++f) {
+      C->fc[f].v = NULL;
+      C->fc[f].cap = 0;
+    }
+  }
+  c3face* F = &C->fc[C->nfc];
+  F->plane = plane;
+  F->alive = 1;
+  F->n = 0;
+  return C->nfc++;
+}
+
+/* The cell bounded by the particle's own images at +-L along each axis: the
+ * box-shaped cube (planes 0..5 = +x, -x, +y, -y, +z, -z). */
+static int c3_init(c3cell* C, const int64_t* box) {
+  C->npl = C->nvt = C->nfc = 0;
+  for (int a = 0; a < 3; ++a)
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      int64_t d[3] = {0, 0, 0};
+      d[a] = sgn ? -box[a] : box[a];
+      if (c3_add_plane(C, d, -1) < 0) return ORC_ERR_OOM;
+    }
+  /* vertex (sx, sy, sz) = bit 0, 1, 2 set for the + side */
+  for (int v = 0; v < 8; ++v)
+    if (c3_new_vertex(C, (v & 1) ? 0 : 1, (v & 2) ? 2 : 3, (v & 4) ? 4 : 5) < 0) return ORC_ERR_OOM;
+  static const int loops[6][4] = {{1, 3, 7, 5}, {0, 4, 6, 2}, {2, 6, 7, 3},
+                                  {0, 1, 5, 4}, {4, 5, 7, 6}, {0, 2, 3, 1}};
+  for (int f = 0; f < 6; ++f) {
+    const int32_t h = c3_new_face(C, f);
+    if (h < 0) return ORC_ERR_OOM;
+    for (int k = 0; k < 4; ++k)
+      if (c3_face_push(&C->fc[h], loops[f][k])) return ORC_ERR_OOM;
+  }
+  return ORC_OK;
+}
+
+/* the vertex where the plane of site e crosses the edge a->b of face f
+ * (one end strictly inside, the other strictly beyond); shared with the
+ * edge's other face, which runs it as b->a */
+static int32_t c3_cross(c3cell* C, int32_t f, int32_t a, int32_t b, int32_t e) {
+  for (int32_t t = 0; t < C->nmemo; ++t) {
+    const int32_t* m = C->memo + 3 * t;
+    if ((m[0] == a && m[1] == b) || (m[0] == b && m[1] == a)) return m[2];
+  }
+  int32_t g = -1;
+  for (int32_t h = 0; h < C->nfc && g < 0; ++h) {
+    if (h == f || !C->fc[h].alive) continue;
+    const c3face* F = &C->fc[h];
+    for (int32_t k = 0; k < F->n; ++k)
+      if (F->v[k] == b && F->v[(k + 1) % F->n] == a) {
+        g = h;
+        break;
+      }
+  }
+  if (g < 0) return -2;
+  const int32_t x = c3_new_vertex(C, C->fc[f].plane, C->fc[g].plane, e);
+  if (x < 0) return -1;
+  if (c3_grow((void**)&C->memo, &C->capmemo, 3 * ((int64_t)C->nmemo + 1), sizeof(int32_t))) return -1;
+  C->memo[3 * C->nmemo] = a;
+  C->memo[3 * C->nmemo + 1] = b;
+  C->memo[3 * C->nmemo + 2] = x;
+  ++C->nmemo;
+  return x;
+}
+
+static int c3_edge(c3cell* C, int32_t tail, int32_t head) {
+  if (c3_grow((void**)&C->eg, &C->capeg, 2 * ((int64_t)C->neg + 1), sizeof(int32_t))) return 1;
+  C->eg[2 * C->neg] = tail;
+  C->eg[2 * C->neg + 1] = head;
+  ++C->neg;
+  return 0;
+}
+
+/* Clip the cell by the half-space of plane e.  *cut = 1 when some vertex lay
+ * strictly beyond it (the plane then carries a new face of positive area). */
+static int c3_clip(c3cell* C, int32_t e, int* cut) {
+  *cut = 0;
+  const int32_t nv0 = C->nvt;
+  if (c3_grow((void**)&C->sg, &C->capsg, nv0, sizeof(int8_t))) return ORC_ERR_OOM;
+  int any_out = 0;
+  for (int32_t v = 0; v < nv0; ++v) {
+    C->sg[v] = C->vt[v].alive ? (int8_t)c3_side(C, v, e) : 0;
+    any_out |= C->vt[v].alive && C->sg[v] > 0;
+  }
+  if (!any_out) return ORC_OK;
+  *cut = 1;
+  C->nmemo = 0;
+  C->neg = 0;
+  const int32_t nf0 = C->nfc;
+  for (int32_t f = 0; f < nf0; ++f) {
+    c3face* F = &C->fc[f];
+    if (!F->alive) continue;
+    int nin = 0, nout = 0;
+    for (int32_t k = 0; k < F->n; ++k) {
+      nin += C->sg[F->v[k]] < 0;
+      nout += C->sg[F->v[k]] > 0;
+    }
+    if (!nout) {
+      /* untouched; an edge lying in the plane bounds the new face */
+      for (int32_t k = 0; k < F->n; ++k) {
+        const int32_t u = F->v[k], v = F->v[(k + 1) % F->n];
+        if (C->sg[u] == 0 && C->sg[v] == 0 && c3_edge(C, v, u)) return ORC_ERR_OOM;
+      }
+      continue;
+    }
+    if (!nin) {
+      F->alive = 0; /* nothing of it is strictly inside: gone (or reduced to an edge or a vertex) */
+      continue;
+    }
+    int32_t k0 = 0;
+    while (C->sg[F->v[k0]] >= 0) ++k0;
+    if (c3_grow((void**)&C->tmp, &C->captmp, (int64_t)F->n + 2, sizeof(int32_t))) return ORC_ERR_OOM;
+    int32_t m = 0, A = -1, B = -1;
+    for (int32_t t = 0; t < F->n; ++t) {
+      const int32_t u = F->v[(k0 + t) % F->n], v = F->v[(k0 + t + 1) % F->n];
+      const int su = C->sg[u], sv = C->sg[v];
+      if (su <= 0) C->tmp[m++] = u;
+      if (su < 0 && sv > 0) {
+        const int32_t x = c3_cross(C, f, u, v, e);
+        if (x < 0) return x == -1 ? ORC_ERR_OOM : ORC_ERR_INTERNAL;
+        C->tmp[m++] = x;
+        A = x;
+      } else if (su == 0 && sv > 0) {
+        A = u;
+      } else if (su > 0 && sv < 0) {
+        const int32_t x = c3_cross(C, f, u, v, e);
+        if (x < 0) return x == -1 ? ORC_ERR_OOM : ORC_ERR_INTERNAL;
+        C->tmp[m++] = x;
+        B = x;
+      } else if (su > 0 && sv == 0) {
+        B = v;
+      }
+      if (c3_grow((void**)&C->tmp, &C->captmp, (int64_t)m + 2, sizeof(int32_t))) return ORC_ERR_OOM;
+    }
+    if (A < 0 || B < 0) return ORC_ERR_INTERNAL;
+    F = &C->fc[f]; /* (no reallocation of fc happens above; kept for clarity) */
+    F->n = 0;
+    for (int32_t t = 0; t < m; ++t)
+      if (c3_face_push(F, C->tmp[t])) return ORC_ERR_OOM;
+    if (c3_edge(C, B, A)) return ORC_ERR_OOM;
+  }
+  for (int32_t v = 0; v < nv0; ++v)
+    if (C->sg[v] > 0) C->vt[v].alive = 0;
+  /* chain the boundary edges into the loop of the new face */
+  const int32_t h = c3_new_face(C, e);
+  if (h < 0) return ORC_ERR_OOM;
+  if (C->neg < 3) return ORC_ERR_INTERNAL;
+  const int32_t start = C->eg[0];
+  int32_t cur = start, steps = 0;
+  do {
+    if (c3_face_push(&C->fc[h], cur)) return ORC_ERR_OOM;
+    int32_t nxt = -1;
+    for (int32_t t = 0; t < C->neg; ++t)
+      if (C->eg[2 * t] == cur) {
+        if (nxt >= 0) return ORC_ERR_INTERNAL; /* two edges leave one vertex */
+        nxt = C->eg[2 * t + 1];
+      }
+    if (nxt < 0) return ORC_ERR_INTERNAL;
+    cur = nxt;
+    ++steps;
+  } while (cur != start && steps <= C->neg);
+  if (cur != start || steps != C->neg) return ORC_ERR_INTERNAL;
+  return ORC_OK;
+}
+
+/* squared distance of the farthest vertex, rounded up generously */
+static double c3_radius2(const c3cell* C) {
+  double r2 = 0.0;
+  for (int32_t v = 0; v < C->nvt; ++v) {
+    if (!C->vt[v].alive) continue;
+    const double* x = C->vt[v].x;
+    const double q = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    if (q > r2) r2 = q;
+  }
+  return r2 * (1.0 + 1e-9) + 1.0;
+}
+
+/* Euler's relation V - E + F = 2 of the finished cell: a self-check */
+static int c3_check(const c3cell* C) {
+  int64_t V = 0, E2 = 0, F = 0;
+  for (int32_t v = 0; v < C->nvt; ++v) V += C->vt[v].alive;
+  for (int32_t f = 0; f < C->nfc; ++f)
+    if (C->fc[f].alive) {
+      if (C->fc[f].n < 3) return ORC_ERR_INTERNAL;
+      ++F;
+      E2 += C->fc[f].n;
+    }
+  return (E2 % 2 == 0 && V - E2 / 2 + F == 2) ? ORC_OK : ORC_ERR_INTERNAL;
+}
+
+static double c3_volume(const c3cell* C) {
+  double vol = 0.0;
+  for (int32_t f = 0; f < C->nfc; ++f) {
+    const c3face* F = &C->fc[f];
+    if (!F->alive) continue;
+    const double* a = C->vt[F->v[0]].x;
+    for (int32_t k = 1; k + 1 < F->n; ++k) {
+      const double* b = C->vt[F->v[k]].x;
+      const double* c = C->vt[F->v[k + 1]].x;
+      vol += a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) +
+             a[2] * (b[0] * c[1] - b[1] * c[0]);
+    }
+  }
+  return vol / 6.0;
+}
+
+typedef struct {
+  uint64_t w;
+  int32_t id;
+  int64_t d[3];
+} c3cand;
+
+static int cmp_c3cand(const void* x, const void* y) {
+  const c3cand* a = (const c3cand*)x;
+  const c3cand* b = (const c3cand*)y;
+  if (a->w != b->w) return a->w < b->w ? -1 : 1;
+  if (a->id != b->id) return a->id < b->id ? -1 : 1;
+  for (int t = 0; t < 3; ++t)
+    if (a->d[t] != b->d[t]) return a->d[t] < b->d[t] ? -1 : 1;
+  return 0;
+}
+
+/* clip the cube by every candidate in (w, id) order, skipping those that
+ * lie too far to reach the cell */
+static int c3_build(c3cell* C, const int64_t* box, const c3cand* cand, int64_t nc) {
+  int rc = c3_init(C, box);
+  if (rc) return rc;
+  double r2 = c3_radius2(C);
+  for (int64_t t = 0; t < nc; ++t) {
+    if ((double)cand[t].w >= 4.0 * r2) break; /* |d|/2 >= every vertex's distance */
+    const int32_t e = c3_add_plane(C, cand[t].d, cand[t].id);
+    if (e < 0) return ORC_ERR_OOM;
+    int cut = 0;
+    if ((rc = c3_clip(C, e, &cut))) return rc;
+    if (cut) r2 = c3_radius2(C);
+    else --C->npl; /* the plane carries no face and no vertex: drop it */
+  }
+  return c3_check(C);
+}
+
+/* Cell of particle i.  Candidates are the minimum images of the other
+ * particles within a growing radius T, until the cell is certified to lie
+ * within sqrt(T)/2 of the particle; when the cell reaches a quarter of the
+ * box, every periodic image within twice its radius is used instead. */
+static int c3_particle(c3cell* C, int64_t n, const int32_t* pos, const int64_t* box, int64_t i, double T,
+                       c3cand** buf, int64_t* cap) {
+  int rc;
+  const int64_t Lmin = box[0] < box[1] ? (box[0] < box[2] ? box[0] : box[2]) : (box[1] < box[2] ? box[1] : box[2]);
+  for (;;) {
+    int64_t nc = 0;
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      int64_t d[3];
+      uint64_t w = 0;
+      for (int a = 0; a < 3; ++a) {
+        d[a] = min_image((int64_t)pos[3 * j + a] - (int64_t)pos[3 * i + a], box[a]);
+        w += (uint64_t)(d[a] * d[a]);
+      }
+      if (w == 0) return ORC_ERR_DEGENERATE;
+      if ((double)w > T) continue;
+      if (nc == *cap) {
+        const int64_t nc2 = *cap ? 2 * *cap : 1024;
+        c3cand* q = (c3cand*)realloc(*buf, (size_t)nc2 * sizeof(c3cand));
+        if (!q) return ORC_ERR_OOM;
+        *buf = q;
+        *cap = nc2;
+      }
+      c3cand* c = &(*buf)[nc++];
+      c->w = w;
+      c->id = (int32_t)j;
+      for (int a = 0; a < 3; ++a) c->d[a] = d[a];
+    }
+    qsort(*buf, (size_t)nc, sizeof(c3cand), cmp_c3cand);
+    if ((rc = c3_build(C, box, *buf, nc))) return rc;
+    const double r2 = c3_radius2(C);
+    const int all = (nc == n - 1);
+    if (4.0 * r2 > T && !all) {
+      T *= 4.0;
+      continue;
+    }
+    /* a non-minimum image is at least Lmin/2 away: it cannot reach the cell
+     * when 4 r2 <= (Lmin/2)^2 */
+    if (16.0 * r2 <= (double)Lmin * (double)Lmin) return ORC_OK;
+    /* small box: every image of every particle within 2 sqrt(r2) */
+    const double R = sqrt(r2);
+    int64_t K[3];
+    for (int a = 0; a < 3; ++a) K[a] = (int64_t)floor((2.0 * R + 0.5 * (double)box[a]) / (double)box[a]) + 1;
+    nc = 0;
+    for (int64_t j = 0; j < n; ++j) {
+      int64_t d0[3];
+      for (int a = 0; a < 3; ++a) d0[a] = min_image((int64_t)pos[3 * j + a] - (int64_t)pos[3 * i + a], box[a]);
+      for (int64_t kx = -K[0]; kx <= K[0]; ++kx)
+        for (int64_t ky = -K[1]; ky <= K[1]; ++ky)
+          for (int64_t kz = -K[2]; kz <= K[2]; ++kz) {
+            if (j == i && kx == 0 && ky == 0 && kz == 0) continue;
+            const int64_t d[3] = {d0[0] + kx * box[0], d0[1] + ky * box[1], d0[2] + kz * box[2]};
+            const double wd = (double)d[0] * d[0] + (double)d[1] * d[1] + (double)d[2] * d[2];
+            if (wd >= 4.0 * r2) continue;
+            if (nc == *cap) {
+              const int64_t nc2 = *cap ? 2 * *cap : 1024;
+              c3cand* q = (c3cand*)realloc(*buf, (size_t)nc2 * sizeof(c3cand));
+              if (!q) return ORC_ERR_OOM;
+              *buf = q;
+              *cap = nc2;
+            }
+            c3cand* c = &(*buf)[nc++];
+            c->w = (uint64_t)(d[0] * d[0]) + (uint64_t)(d[1] * d[1]) + (uint64_t)(d[2] * d[2]);
+            c->id = j == i ? -1 : (int32_t)j;
+            for (int a = 0; a < 3; ++a) c->d[a] = d[a];
+          }
+    }
+    qsort(*buf, (size_t)nc, sizeof(c3cand), cmp_c3cand);
+    return c3_build(C, box, *buf, nc);
+  }
+}
+
+static int cmp_i32(const void* x, const void* y) {
+  const int32_t a = *(const int32_t*)x, b = *(const int32_t*)y;
+  return (a > b) - (a < b);
+}
+
+/* Voronoi neighbors (sorted by id) and cell volumes (grid units^3) of the
+ * query particles (all when query is NULL).  Rows hold up to maxdeg ids;
+ * deg[q] is the true count, and a larger one returns ORC_ERR_ARG.  Box edges
+ * up to 2^28. */
+int orc_voronoi3(int64_t n, const int32_t* pos, const int64_t* box, const int64_t* query, int64_t nq,
+                 int32_t maxdeg, int32_t* deg, int32_t* ids, double* volume) {
+  if (n < 1 || nq < 0 || maxdeg < 0) return ORC_ERR_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (box[a] < 1 || box[a] > (1ll << 28)) return ORC_ERR_ARG;
+  for (int64_t j = 0; j < 3 * n; ++j)
+    if (pos[j] < 0 || (int64_t)pos[j] >= box[j % 3]) return ORC_ERR_ARG;
+  /* first radius: about 4.5 mean spacings */
+  const double spacing = cbrt((double)box[0] * (double)box[1] * (double)box[2] / (double)n);
+  const double T0 = 20.0 * spacing * spacing;
+  int rc_all = ORC_OK;
+#pragma omp parallel
+  {
+    c3cell C;
+    memset(&C, 0, sizeof(C));
+    c3cand* buf = NULL;
+    int64_t cap = 0;
+    int32_t* row = NULL;
+    int32_t rowcap = 0;
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t q = 0; q < nq; ++q) {
+      const int64_t i = query ? query[q] : q;
+      int rc = (i < 0 || i >= n) ? ORC_ERR_ARG : c3_particle(&C, n, pos, box, i, T0, &buf, &cap);
+      int32_t cnt = 0;
+      if (!rc) {
+        for (int32_t f = 0; f < C.nfc && !rc; ++f) {
+          if (!C.fc[f].alive || C.pl[C.fc[f].plane].id < 0) continue;
+          if (c3_grow((void**)&row, &rowcap, (int64_t)cnt + 1, sizeof(int32_t))) rc = ORC_ERR_OOM;
+          else row[cnt++] = C.pl[C.fc[f].plane].id;
+        }
+      }
+      if (!rc) {
+        qsort(row, (size_t)cnt, sizeof(int32_t), cmp_i32);
+        int32_t u = 0;
+        for (int32_t t = 0; t < cnt; ++t)
+          if (u == 0 || row[t] != row[u - 1]) row[u++] = row[t];
+        cnt = u;
+        deg[q] = cnt;
+        if (cnt > maxdeg) rc = ORC_ERR_ARG;
+        else
+          for (int32_t t = 0; t < cnt; ++t) ids[q * (int64_t)maxdeg + t] = row[t];
+        if (volume) volume[q] = c3_volume(&C);
+      }
+      if (rc) {
+#pragma omp critical
+        if (rc_all == ORC_OK || rc == ORC_ERR_DEGENERATE) rc_all = rc;
+      }
+    }
+    c3_free(&C);
+    free(buf);
+    free(row);
+  }
+  return rc_all;
+}
+
+/* The exact side test on explicit site offsets (for the tests): the sign of
+ * d_e.y - |d_e|^2 at the point y where d_a.y = |d_a|^2, d_b.y = |d_b|^2 and
+ * d_c.y = |d_c|^2 (0 when a, b, c do not meet in one point). */
+int orc_voronoi3_side(const int64_t* da, const int64_t* db, const int64_t* dc, const int64_t* de) {
+  c3cell C;
+  memset(&C, 0, sizeof(C));
+  int s = 0;
+  if (c3_add_plane(&C, da, 0) >= 0 && c3_add_plane(&C, db, 1) >= 0 && c3_add_plane(&C, dc, 2) >= 0 &&
+      c3_add_plane(&C, de, 3) >= 0 && det3_i(da, db, dc) != 0) {
+    c3vert V;
+    V.p[0] = 0; V.p[1] = 1; V.p[2] = 2; V.alive = 1;
+    if (c3_grow((void**)&C.vt, &C.capvt, 1, sizeof(c3vert)) == 0) {
+      C.vt[0] = V;
+      C.nvt = 1;
+      s = c3_side(&C, 0, 3);
+    }
+  }
+  c3_free(&C);
+  return s;
 }
 
 /* ======================================================================== */

@@ -205,6 +205,19 @@ def knn_3d(n: int = 1 << 20, k: int = 7, seed: int = 1023) -> Workload:
                           check_every=50)
 
 
+def voronoi_3d(n: int = 1 << 18, seed: int = 1024, eta: float = 0.2) -> Workload:
+    """3D Voronoi flock: cubic periodic box at density 1 (L = N^(1/3), 64 for
+    N = 2^18), vectorial noise.  F = 15 keeps the box within 2^21 grid units
+    (L_q = 2^21 at N = 2^18), the range of the exact 3D Voronoi predicates."""
+    L = float(n) ** (1.0 / 3.0)
+    F = 15
+    while F > 0 and L * float(1 << F) > float(1 << 21):
+        F -= 1
+    return uniform_system(n, L, F, 3, seed, name=f"voronoi3d_N{n}_F{F}", rule="voronoi", k=0,
+                          v0=0.5, dt=1.0, eta=eta, seed=1, noise="vectorial", steps=200,
+                          check_every=50)
+
+
 def replica_sizes(n_rep: int = 512, lo: int = 1024, hi: int = 65536, seed: int = 1004) -> np.ndarray:
     rng = _rng(seed)
     u = rng.uniform(math.log(lo), math.log(hi), size=n_rep)
@@ -266,6 +279,30 @@ def stretched_hex_lattice(cols: int, rows: int, dx_q: int, dy_q: int) -> tuple:
     y = r.ravel() * dy_q
     box = (cols * dx_q, rows * dy_q)
     pos = np.stack([np.mod(x, box[0]), np.mod(y, box[1])], axis=1).astype(np.int32)
+    return pos, box
+
+
+def cubic_lattice(kind: str, m, spacing_q, offset_q=(0, 0, 0)) -> tuple:
+    """Simple cubic ("sc"), body-centred ("bcc") or face-centred ("fcc")
+    lattice of m = (mx, my, mz) conventional cells of edges spacing_q =
+    (ax, ay, az) (even, so that the centring offsets a/2 stay on the grid),
+    shifted by offset_q and wrapped into the periodic box (mx ax, my ay, mz az)."""
+    m = (m,) * 3 if np.isscalar(m) else tuple(m)
+    a = (spacing_q,) * 3 if np.isscalar(spacing_q) else tuple(spacing_q)
+    if kind != "sc" and any(x % 2 for x in a):
+        raise ValueError("centred lattices need even spacings")
+    basis = {"sc": [(0, 0, 0)],
+             "bcc": [(0, 0, 0), (1, 1, 1)],
+             "fcc": [(0, 0, 0), (1, 1, 0), (1, 0, 1), (0, 1, 1)]}[kind]
+    k, j, i = np.meshgrid(np.arange(m[2]), np.arange(m[1]), np.arange(m[0]), indexing="ij")
+    cells = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1).astype(np.int64)
+    box = tuple(int(m[t] * a[t]) for t in range(3))
+    pts = []
+    for b in basis:
+        off = np.array([b[t] * (a[t] // 2) + offset_q[t] for t in range(3)], dtype=np.int64)
+        pts.append(cells * np.array(a, dtype=np.int64) + off)
+    pos = np.concatenate(pts, axis=0)
+    pos = np.mod(pos, np.array(box, dtype=np.int64)).astype(np.int32)
     return pos, box
 
 

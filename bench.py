@@ -64,7 +64,7 @@ def parse():
                     help="timed (and warm-up) steps of each arm of the replica-batch block")
     ap.add_argument("--autotune", action="store_true",
                     help="let the library's autotuner pick the occupancy on the warmed-up state instead")
-    ap.add_argument("--scenario", choices=["headline", "replicas", "voronoi", "knn3d"], default="headline",
+    ap.add_argument("--scenario", choices=["headline", "replicas", "voronoi", "voronoi3d", "knn3d"], default="headline",
                     help="headline: the benchmark line; the others are secondary measurements")
     return ap.parse_args()
 
@@ -226,15 +226,17 @@ def scenario_cpu_baseline(w, budget_s: float) -> dict:
     oracle.build()
     if w.rule == "voronoi":
         t0 = time.perf_counter()
-        off, ids = oracle.voronoi(w.pos_q, w.box_q)
+        off, ids = (oracle.voronoi3 if w.dim == 3 else oracle.voronoi)(w.pos_q, w.box_q)
         t_nb = time.perf_counter() - t0
         t0 = time.perf_counter()
         oracle.vicsek_step(w.pos_q, w.dir, w.box_q, off, ids, frac_bits=w.frac_bits, v0=w.v0, dt=w.dt,
                            eta=w.eta, seed=w.seed, step=0)
         t_upd = time.perf_counter() - t0
         return {"value": w.n / (t_nb + t_upd), "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-                "sample": f"one whole step of all {w.n} particles ({t_nb + t_upd:.1f} s): serial Bowyer-Watson "
-                          f"triangulation ({t_nb:.1f} s) + FP64 update on {oracle.num_threads()} threads"}
+                "sample": f"one whole step of all {w.n} particles ({t_nb + t_upd:.1f} s): "
+                          + ("exact cell clipping on %d threads" % oracle.num_threads() if w.dim == 3
+                             else "serial Bowyer-Watson triangulation")
+                          + f" ({t_nb:.1f} s) + FP64 update on {oracle.num_threads()} threads"}
     rate, m, cores, secs = oracle_sample_rate(w, budget_s)
     return {"value": rate, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
             "sample": f"{m} random particles of the {w.n}-particle workload: brute-force kNN over all N "
@@ -505,6 +507,10 @@ def secondary_block(stream) -> dict:
     with vk.from_workload(w3, stream=stream) as sim:
         out["knn3d_1M"] = dict(_rate(stream, sim, w3.n, 5, 20), config={"workload": w3.name, "rule": "knn",
                                                                         "k": 7, "dim": 3})
+    wv3 = W.voronoi_3d()
+    with vk.from_workload(wv3, stream=stream) as sim:
+        out["voronoi3d_256k"] = dict(_rate(stream, sim, wv3.n, 3, 10),
+                                     config={"workload": wv3.name, "rule": "voronoi", "dim": 3, "eta": wv3.eta})
     # the tissue model's energy and forces of a uniform state: wall time of the
     # whole synchronous call (scratch allocation, three kernels, copies to host)
     wt = W.uniform_system(1 << 20, 1024.0, 16, 2, input_seed=1011, rule="voronoi", k=0)
@@ -580,6 +586,8 @@ def run_scenario(args):
     else:
         if args.scenario == "voronoi":
             w = W.voronoi_mixed(eta=0.1)
+        elif args.scenario == "voronoi3d":
+            w = W.voronoi_3d()
         else:
             w = W.knn_3d()
         sim = vk.from_workload(w, stream=stream)

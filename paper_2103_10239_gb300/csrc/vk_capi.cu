@@ -314,7 +314,8 @@ vk_status enqueue_step(vk_sim* s) {
   if (s->prm.rule == VK_RULE_KNN && s->dim == 2) VK_CUDA(s, launch_knn2_step(s->g, s->b, P, s->stream));
   else if (s->prm.rule == VK_RULE_KNN) VK_CUDA(s, launch_knn_step(s->g, s->b, P, s->stream));
   else if (s->prm.rule == VK_RULE_METRIC) VK_CUDA(s, launch_metric_step(s->g, s->b, P, s->stream));
-  else VK_CUDA(s, launch_voronoi_step(s->g, s->b, P, s->stream));
+  else if (s->dim == 2) VK_CUDA(s, launch_voronoi_step(s->g, s->b, P, s->stream));
+  else VK_CUDA(s, launch_voronoi3_step(s->g, s->b, P, s->stream));
   const int deferred_launches = (s->prm.rule == VK_RULE_KNN && s->dim == 2 && s->prm.knn_search == 0) ? 2 : 0;
   if ((st = record_end(s, 0, e0, search_launches(s) - deferred_launches))) return st;
   if (deferred_launches) {
@@ -361,7 +362,6 @@ bool valid_params(const vk_params* p, int dim, std::string* why) {
   if (p->rule == VK_RULE_KNN && (p->k < 1 || p->k > kMaxK)) return *why = "k must be in [1, 32]", false;
   if (p->noise != VK_NOISE_ANGULAR && p->noise != VK_NOISE_VECTORIAL) return *why = "unknown noise", false;
   if (dim == 3 && p->noise != VK_NOISE_VECTORIAL) return *why = "3D needs vectorial noise", false;
-  if (dim == 3 && p->rule == VK_RULE_VORONOI) return *why = "the Voronoi rule is 2D only", false;
   if (p->sum_mode < 0 || p->sum_mode > 2) return *why = "unknown sum mode", false;
   if (!std::isfinite(p->v0) || !std::isfinite(p->dt) || !std::isfinite(p->eta))
     return *why = "v0, dt and eta must be finite", false;
@@ -399,9 +399,10 @@ vk_status build_sim(int32_t n_rep, const int64_t* n_r, const int32_t* pos_q, con
     if (B.dim != dim) return fail(nullptr, VK_ERR_ARG, "all replicas must share the dimension");
     if (B.frac_bits < 0 || B.frac_bits > 30) return fail(nullptr, VK_ERR_RANGE, "frac_bits must be in [0, 30]");
     for (int a = 0; a < dim; ++a) {
-      const uint64_t lim = params->rule == VK_RULE_VORONOI ? (1ull << 30) : (1ull << 31);
+      const uint64_t lim = params->rule != VK_RULE_VORONOI ? (1ull << 31) : (dim == 2 ? (1ull << 30) : (1ull << 23));
       if (B.box_q[a] < 1 || B.box_q[a] > lim)
-        return fail(nullptr, VK_ERR_RANGE, "box edge outside [1, 2^31] (2^30 for the Voronoi rule)");
+        return fail(nullptr, VK_ERR_RANGE,
+                    "box edge outside [1, 2^31] (2^30 for the 2D Voronoi rule, 2^23 for the 3D one)");
     }
     const float vdt = params->v0 * params->dt;
     const double sgrid = std::ldexp((double)vdt, B.frac_bits);
@@ -483,7 +484,7 @@ vk_status build_sim(int32_t n_rep, const int64_t* n_r, const int32_t* pos_q, con
     if ((e = dalloc(&s->b.S_hint, N)) || (e = dalloc(&s->b.U_hint, N)) || (dim == 2 && (e = prepare_knn2())))
       return bail(cuda_fail(s, e, "kNN search buffers"));
   }
-  if (params->rule == VK_RULE_VORONOI && !params->voronoi_rebuild) {
+  if (params->rule == VK_RULE_VORONOI && dim == 2 && !params->voronoi_rebuild) {
     if ((e = dalloc(&s->b.vor_seed, N * kVorSeed)) || (e = dalloc(&s->b.vor_seed_n, N)) ||
         (e = dalloc(&s->b.slot_of, N)))
       return bail(cuda_fail(s, e, "Voronoi seed buffers"));
@@ -629,7 +630,8 @@ vk_status vk_get_neighbors(vk_sim* s, int32_t replica, int64_t* offsets, int32_t
     const bool metric = s->prm.rule == VK_RULE_METRIC;
     auto exporter = [&](int pass, int32_t* deg, const int64_t* off, int32_t* ids_out) {
       return metric ? launch_metric_export(s->g, s->b, replica, (int)n, pass, deg, off, ids_out, s->stream)
-                    : launch_voronoi_export(s->g, s->b, replica, (int)n, pass, deg, off, ids_out, s->stream);
+          : s->dim == 2 ? launch_voronoi_export(s->g, s->b, replica, (int)n, pass, deg, off, ids_out, s->stream)
+                        : launch_voronoi3_export(s->g, s->b, replica, (int)n, pass, deg, off, ids_out, s->stream);
     };
     int32_t* deg_d = nullptr;
     int64_t* off_d = nullptr;

@@ -729,6 +729,11 @@ cudaError_t launch_tissue(const Geometry& g, const Buffers& b, int rep, int n, d
 cudaError_t launch_voronoi_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st);
 cudaError_t launch_voronoi_export(const Geometry& g, const Buffers& b, int rep, int n, int pass, int32_t* deg,
                                   const int64_t* out_off, int32_t* out_ids, cudaStream_t st);
+// vk_voronoi3.cu (3D Voronoi rule)
+cudaError_t launch_voronoi3_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st);
+cudaError_t launch_voronoi3_export(const Geometry& g, const Buffers& b, int rep, int n, int pass, int32_t* deg,
+                                   const int64_t* out_off, int32_t* out_ids, cudaStream_t st);
+
 // largest Voronoi cell (edges) handled; larger cells latch VK_ERR_CAPACITY
 constexpr int kVoronoiMaxDeg = 256;
 

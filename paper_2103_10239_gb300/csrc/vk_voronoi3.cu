@@ -1,0 +1,297 @@
+// vk_voronoi3.cu -- Voronoi-neighbor rule in 3D (Sec. "Computational tools:
+// Voronoi neighbor lists": neighbors are the particles whose Voronoi cells
+// share a face; the relation is reciprocal) fused with the Vicsek update of
+// Eq. (1) and Eq. (2) (vectorial noise, as every 3D rule here).
+//
+// One thread per particle, in cell-sorted order.  The cell starts as the box
+// bounded by the particle's own periodic images and is clipped by the bisector
+// planes of the candidates that the ring walk of the uniform 3D grid delivers
+// (vk_voronoi3.cuh: exact predicates, dual triangulation).  A site at offset
+// d can cut the cell only if |d| < 2R, R the distance of the farthest vertex,
+// so the walk stops once the scanned block holds that ball.  When 2R reaches a
+// quarter of the box, non-minimum images of other particles can cut too: the
+// cell is then finished against every image of every particle within 2R.
+// Neighbors are the sites of faces of positive area, in id order.
+// Coincident particles latch VK_ERR_DEGENERATE (no cell separates them).
+#include <algorithm>
+
+#include "vk_internal.cuh"
+#include "vk_voronoi3.cuh"
+
+namespace vk {
+
+namespace {
+
+// the main kernel's cells (about 15.5 faces and 27 vertices on average for
+// uniform points) and the overflow kernel's, for the rare cell whose
+// intermediate polytope outgrows the first
+using CellS = v3::Cell<64, 128>;
+using CellL = v3::Cell<128, 256>;
+
+// the cell of the particle at sorted slot `self` (replica R); false when
+// the build failed (C.status says why)
+template <class Cell>
+__device__ bool voronoi3_cell(const Rep& R, int64_t self, const int32_t* pi, const int4* __restrict__ S_pos,
+                              const GridView& G, Cell& C, int8_t* sg, uint32_t* n_cand) {
+  v3::cell_init(C, R.L);
+  auto clip = [&](int64_t q, const int32_t* d) {
+    if (d[0] == 0 && d[1] == 0 && d[2] == 0) {
+      C.status = v3::kCoincident;
+      return;
+    }
+    v3::cell_clip(C, d, (int32_t)q, sg);
+  };
+  auto run = [&](uint32_t qb, uint32_t qe) {
+    if (C.status != v3::kOk) return;
+    *n_cand += qe - qb;
+    for (uint32_t q = qb; q < qe && C.status == v3::kOk; ++q) {
+      if ((int64_t)q == self) continue;
+      const int4 pj = __ldg(S_pos + q);
+      const int32_t d[3] = {(int32_t)min_image((int64_t)pj.x - pi[0], (int64_t)R.L[0]),
+                            (int32_t)min_image((int64_t)pj.y - pi[1], (int64_t)R.L[1]),
+                            (int32_t)min_image((int64_t)pj.z - pi[2], (int64_t)R.L[2])};
+      clip(q, d);
+    }
+  };
+  // every unscanned site is at squared distance >= B2; none can cut once
+  // B2 >= 4 R^2 (the FP32 B2 is lowered by 2^-22 to stay below the exact value)
+  auto stop = [&](uint64_t B2) { return C.status != v3::kOk || (float)B2 * 0.99999976f >= 4.f * C.r2; };
+  grid_walk3(R, pi, G, run, stop);
+  if (C.status != v3::kOk) return false;
+  // other images lie at >= L_min / 2: they matter only when 2R > L_min / 2
+  const float Lmin = (float)min(R.L[0], min(R.L[1], R.L[2]));
+  if (16.f * C.r2 > Lmin * Lmin) {
+    for (int32_t lj = 0; lj < R.n && C.status == v3::kOk; ++lj) {
+      const int64_t q = R.p0 + lj;
+      if (q == self) continue;
+      const int4 pj = __ldg(S_pos + q);
+      const int64_t d0[3] = {min_image((int64_t)pj.x - pi[0], (int64_t)R.L[0]),
+                             min_image((int64_t)pj.y - pi[1], (int64_t)R.L[1]),
+                             min_image((int64_t)pj.z - pi[2], (int64_t)R.L[2])};
+      const float Rr = sqrtf(C.r2);
+      int K[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) K[a] = (int)floorf((2.f * Rr + 0.5f * (float)R.L[a]) / (float)R.L[a]) + 1;
+      for (int kx = -K[0]; kx <= K[0]; ++kx)
+        for (int ky = -K[1]; ky <= K[1]; ++ky)
+          for (int kz = -K[2]; kz <= K[2] && C.status == v3::kOk; ++kz) {
+            const int32_t d[3] = {(int32_t)(d0[0] + (int64_t)kx * R.L[0]), (int32_t)(d0[1] + (int64_t)ky * R.L[1]),
+                                  (int32_t)(d0[2] + (int64_t)kz * R.L[2])};
+            clip(q, d);
+          }
+    }
+  }
+  return C.status == v3::kOk;
+}
+
+__device__ __forceinline__ int32_t status_of(int st) {
+  return st == v3::kCoincident ? kStDegenerate : kStCapacity;
+}
+
+// neighbor ids (sorted, each once) and their slots; returns the count
+template <class Cell>
+__device__ int voronoi3_neighbors(const Cell& C, const int32_t* __restrict__ S_id, int32_t* nid, int32_t* nslot) {
+  int cnt = 0;
+  for (int p = 0; p < C.np; ++p) {
+    if (C.pref[p] == 0 || C.pslot[p] < 0 || !v3::face_positive(C, p)) continue;
+    const int32_t id = __ldg(S_id + C.pslot[p]);
+    int j = cnt;
+    while (j > 0 && nid[j - 1] > id) {
+      nid[j] = nid[j - 1];
+      nslot[j] = nslot[j - 1];
+      --j;
+    }
+    if (j > 0 && nid[j - 1] == id) {  // another image of a site already listed
+      for (int t = j; t < cnt; ++t) {
+        nid[t] = nid[t + 1];
+        nslot[t] = nslot[t + 1];
+      }
+      continue;
+    }
+    nid[j] = id;
+    nslot[j] = C.pslot[p];
+    ++cnt;
+  }
+  return cnt;
+}
+
+constexpr int kV3Block = 128;
+constexpr int kV3Split = kBlock / kV3Block;
+
+// Eq. (2) + Eq. (1) for one particle from its finished cell; writes the next
+// state and counts its new grid cell
+template <class Cell>
+__device__ __forceinline__ void voronoi3_update(const Rep& R, const StepParams& Pm, int64_t step, int64_t s,
+                                                const Cell& C, const int32_t* pi, const float* ni, int32_t id,
+                                                const int32_t* __restrict__ S_id, const float4* __restrict__ S_dir,
+                                                int4* __restrict__ U_pos, float4* __restrict__ U_dir,
+                                                int32_t* __restrict__ U_id, uint32_t* __restrict__ counts,
+                                                float* nnew) {
+  int32_t nid[Cell::P], nslot[Cell::P];
+  const int cnt = voronoi3_neighbors(C, S_id, nid, nslot);
+  HeadSum<3> H;
+  H.init();
+  if (Pm.include_self) H.add(ni, Pm.sum_mode);
+  for (int j = 0; j < cnt; ++j) {
+    const float4 d = __ldg(S_dir + nslot[j]);
+    const float v[3] = {d.x, d.y, d.z};
+    H.add(v, Pm.sum_mode);
+  }
+  int32_t pout[3];
+  align_advect<3>(R, Pm, (uint32_t)step, id, ni, H, cnt + (Pm.include_self ? 1 : 0), pi, pout, nnew);
+  U_pos[s] = make_int4(pout[0], pout[1], pout[2], 0);
+  U_dir[s] = make_float4(nnew[0], nnew[1], nnew[2], 0.f);
+  U_id[s] = id;
+  atomicAdd(counts + linear_cell<3>(R, pout), 1u);
+}
+
+// a particle whose cell could not be built: the state is carried over
+// unchanged and the status latched (the host reports it)
+__device__ __forceinline__ void voronoi3_keep(const Rep& R, int64_t s, const int32_t* pi, const float* ni,
+                                              int32_t id, int st, int32_t* status, int4* __restrict__ U_pos,
+                                              float4* __restrict__ U_dir, int32_t* __restrict__ U_id,
+                                              uint32_t* __restrict__ counts, float* nnew) {
+  set_status(status, status_of(st));
+  nnew[0] = ni[0];
+  nnew[1] = ni[1];
+  nnew[2] = ni[2];
+  U_pos[s] = make_int4(pi[0], pi[1], pi[2], 0);
+  U_dir[s] = make_float4(ni[0], ni[1], ni[2], 0.f);
+  U_id[s] = id;
+  atomicAdd(counts + linear_cell<3>(R, pi), 1u);
+}
+
+__global__ void __launch_bounds__(kV3Block) voronoi3_step_kernel(
+    const Rep* __restrict__ reps, const BlockTask* __restrict__ tasks, const int4* __restrict__ S_pos,
+    const float4* __restrict__ S_dir, const int32_t* __restrict__ S_id, GridView G, int4* __restrict__ U_pos,
+    float4* __restrict__ U_dir, int32_t* __restrict__ U_id, uint32_t* __restrict__ counts,
+    PhiAcc* __restrict__ phi_acc, const int64_t* __restrict__ d_step, StepParams Pm, int32_t* status,
+    int2* __restrict__ ovf_list, int32_t* __restrict__ ovf_count) {
+  __shared__ PhiShared phs;
+  phi_block_begin(phs);
+  const BlockTask t = tasks[blockIdx.x / kV3Split];
+  const Rep R = reps[t.rep];
+  const int li = t.first + (int)(blockIdx.x % kV3Split) * kV3Block + (int)threadIdx.x;
+  const int64_t step = *d_step;
+  float nnew[3] = {0.f, 0.f, 0.f};
+  uint32_t n_cand = 0;
+  if (li < R.n) {
+    const int64_t s = R.p0 + li;
+    const int4 p = S_pos[s];
+    const float4 nv = S_dir[s];
+    const int32_t pi[3] = {p.x, p.y, p.z};
+    const float ni[3] = {nv.x, nv.y, nv.z};
+    const int32_t id = S_id[s];
+    CellS C;
+    int8_t sg[CellS::T];
+    if (voronoi3_cell(R, s, pi, S_pos, G, C, sg, &n_cand)) {
+      voronoi3_update(R, Pm, step, s, C, pi, ni, id, S_id, S_dir, U_pos, U_dir, U_id, counts, nnew);
+    } else if (C.status == v3::kCapacity) {
+      // finished by the overflow kernel (its heading enters phi there)
+      const int q = atomicAdd(ovf_count, 1);
+      ovf_list[q] = make_int2((int)s, t.rep);
+    } else {
+      voronoi3_keep(R, s, pi, ni, id, C.status, status, U_pos, U_dir, U_id, counts, nnew);
+    }
+  }
+  record_search_stats(Pm.stats, li < R.n, n_cand, 0);
+  phi_block_end<3>(phs, nnew, phi_acc + ((size_t)(step % Pm.phi_cap) * (size_t)Pm.n_rep + (size_t)t.rep) * 3);
+}
+
+// Overflow kernel: the particles whose intermediate cell outgrew CellS, one
+// thread each with the larger cell.
+constexpr int kV3OvfBlock = 64;
+
+__global__ void __launch_bounds__(kV3OvfBlock) voronoi3_overflow_kernel(
+    const Rep* __restrict__ reps, const int4* __restrict__ S_pos, const float4* __restrict__ S_dir,
+    const int32_t* __restrict__ S_id, GridView G, int4* __restrict__ U_pos, float4* __restrict__ U_dir,
+    int32_t* __restrict__ U_id, uint32_t* __restrict__ counts, PhiAcc* __restrict__ phi_acc,
+    const int64_t* __restrict__ d_step, StepParams Pm, int32_t* status, const int2* __restrict__ ovf_list,
+    const int32_t* __restrict__ ovf_count) {
+  const int total = *ovf_count;
+  const int64_t step = *d_step;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+    const int2 e = ovf_list[q];
+    const Rep R = reps[e.y];
+    const int64_t s = e.x;
+    const int4 p = S_pos[s];
+    const float4 nv = S_dir[s];
+    const int32_t pi[3] = {p.x, p.y, p.z};
+    const float ni[3] = {nv.x, nv.y, nv.z};
+    const int32_t id = S_id[s];
+    CellL C;
+    int8_t sg[CellL::T];
+    uint32_t n_cand = 0;
+    float nnew[3];
+    if (voronoi3_cell(R, s, pi, S_pos, G, C, sg, &n_cand))
+      voronoi3_update(R, Pm, step, s, C, pi, ni, id, S_id, S_dir, U_pos, U_dir, U_id, counts, nnew);
+    else
+      voronoi3_keep(R, s, pi, ni, id, C.status, status, U_pos, U_dir, U_id, counts, nnew);
+    PhiAcc* acc = phi_acc + ((size_t)(step % Pm.phi_cap) * (size_t)Pm.n_rep + (size_t)e.y) * 3;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) atomicAdd(acc + a, (PhiAcc)phi_fixed(nnew[a]));
+  }
+}
+
+// Export (not on the hot path): pass 0 writes the degree of every particle
+// (by id), pass 1 the sorted ids at out_off[id].
+__global__ void __launch_bounds__(kV3Block) voronoi3_export_kernel(
+    const Rep* __restrict__ reps, int rep, const int4* __restrict__ S_pos, const int32_t* __restrict__ S_id,
+    GridView G, int pass, int32_t* __restrict__ deg, const int64_t* __restrict__ out_off,
+    int32_t* __restrict__ out_ids, int32_t* status) {
+  const Rep R = reps[rep];
+  for (int li = blockIdx.x * blockDim.x + threadIdx.x; li < R.n; li += gridDim.x * blockDim.x) {
+    const int64_t s = R.p0 + li;
+    const int4 p = S_pos[s];
+    const int32_t pi[3] = {p.x, p.y, p.z};
+    const int32_t id = S_id[s];
+    CellL C;
+    int8_t sg[CellL::T];
+    uint32_t n_cand = 0;
+    if (!voronoi3_cell(R, s, pi, S_pos, G, C, sg, &n_cand)) {
+      set_status(status, status_of(C.status));
+      if (pass == 0) deg[id] = 0;
+      continue;
+    }
+    int32_t nid[CellL::P], nslot[CellL::P];
+    const int cnt = voronoi3_neighbors(C, S_id, nid, nslot);
+    if (pass == 0) {
+      deg[id] = cnt;
+    } else {
+      const int64_t o = out_off[id];
+      for (int j = 0; j < cnt; ++j) out_ids[o + j] = nid[j];
+    }
+  }
+}
+
+GridView grid_view3(const Buffers& b) {
+  GridView G;
+  G.off = b.offsets;
+  G.sub_s = b.sub_s;
+  G.sub_base = b.sub_base;
+  G.sub_off = b.sub_off;
+  return G;
+}
+
+}  // namespace
+
+cudaError_t launch_voronoi3_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st) {
+  voronoi3_step_kernel<<<g.n_tasks * kV3Split, kV3Block, 0, st>>>(
+      g.reps, g.tasks, (const int4*)b.S_pos, (const float4*)b.S_dir, b.S_id, grid_view3(b), (int4*)b.U_pos,
+      (float4*)b.U_dir, b.U_id, b.counts, b.phi_acc, b.d_step, P, b.d_status, b.ovf_list, b.ovf_count);
+  voronoi3_overflow_kernel<<<device_sm_count(), kV3OvfBlock, 0, st>>>(
+      g.reps, (const int4*)b.S_pos, (const float4*)b.S_dir, b.S_id, grid_view3(b), (int4*)b.U_pos,
+      (float4*)b.U_dir, b.U_id, b.counts, b.phi_acc, b.d_step, P, b.d_status, b.ovf_list, b.ovf_count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_voronoi3_export(const Geometry& g, const Buffers& b, int rep, int n, int pass, int32_t* deg,
+                                   const int64_t* out_off, int32_t* out_ids, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int nb = std::min((n + kV3Block - 1) / kV3Block, device_sm_count() * 8);
+  voronoi3_export_kernel<<<nb, kV3Block, 0, st>>>(g.reps, rep, (const int4*)b.S_pos, b.S_id, grid_view3(b), pass,
+                                                  deg, out_off, out_ids, b.d_status);
+  return cudaGetLastError();
+}
+
+}  // namespace vk

@@ -28,6 +28,8 @@ def angle_between(a, b) -> np.ndarray:
 def oracle_neighbors(pos, box, rule, k):
     if rule == "knn":
         return oracle.csr_from_dense(oracle.knn(pos, box, k))
+    if np.asarray(pos).shape[1] == 3:
+        return oracle.voronoi3(pos, box)
     return oracle.voronoi(pos, box)
 
 

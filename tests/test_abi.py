@@ -52,6 +52,15 @@ def test_argument_errors_are_reported_without_gpu():
     with pytest.raises(vk.VKError) as e:
         vk.Sim.create(pos, d, (1000, 1000), 30, k=2, v0=1.0)  # step of 2^30 grid units
     assert e.value.status == vk.VK_ERR_RANGE
+    # 3D Voronoi: exact predicates in int128 need box edges <= 2^23
+    p3 = np.zeros((4, 3), dtype=np.int32)
+    d3 = np.ones((4, 3), dtype=np.float32)
+    with pytest.raises(vk.VKError) as e:
+        vk.Sim.create(p3, d3, (1 << 23, (1 << 23) + 1, 1 << 23), 16, rule="voronoi", noise="vectorial")
+    assert e.value.status == vk.VK_ERR_RANGE
+    with pytest.raises(vk.VKError) as e:
+        vk.Sim.create(p3, d3, (1000, 1000, 1000), 8, rule="voronoi")  # 3D needs vectorial noise
+    assert e.value.status == vk.VK_ERR_ARG
 
 
 def test_product_path_does_not_import_the_oracle():

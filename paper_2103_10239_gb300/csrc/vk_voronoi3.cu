@@ -28,6 +28,8 @@ namespace {
 using CellS = v3::Cell<64, 128>;
 using CellL = v3::Cell<128, 256>;
 
+constexpr int kMaxImages = 64;
+
 // the cell of the particle at sorted slot `self` (replica R); false when
 // the build failed (C.status says why)
 template <class Cell>
@@ -71,7 +73,16 @@ __device__ bool voronoi3_cell(const Rep& R, int64_t self, const int32_t* pi, con
       const float Rr = sqrtf(C.r2);
       int K[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) K[a] = (int)floorf((2.f * Rr + 0.5f * (float)R.L[a]) / (float)R.L[a]) + 1;
+      for (int a = 0; a < 3; ++a) {
+        const float k = floorf((2.f * Rr + 0.5f * (float)R.L[a]) / (float)R.L[a]) + 1.f;
+        // more than kMaxImages images per axis (a box far longer than wide
+        // holding a handful of particles) is outside the supported range
+        if (!(k <= (float)kMaxImages)) {
+          C.status = v3::kCapacity;
+          return false;
+        }
+        K[a] = (int)k;
+      }
       for (int kx = -K[0]; kx <= K[0]; ++kx)
         for (int ky = -K[1]; ky <= K[1]; ++ky)
           for (int kz = -K[2]; kz <= K[2] && C.status == v3::kOk; ++kz) {

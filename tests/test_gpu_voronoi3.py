@@ -93,6 +93,7 @@ def test_coincident_particles_are_degenerate():
     with _create(pos, (100, 100, 100), 4) as sim:
         with pytest.raises(vk.VKError) as e:
             sim.step(1)
+            sim.sync()  # the step is asynchronous; the latched status is read here
         assert e.value.status == vk.VK_ERR_DEGENERATE
 
 

@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scenario-n", type=int, default=0,
+                    help="particles of the voronoi3d / knn3d scenario (0: the workload's default)")
     ap.add_argument("--occupancy", type=float, default=256.0,
                     help="coarse-grid occupancy (particles per cell) of the headline run; 256 was the "
                          "fastest of a sweep on the clustered 4M workload (steps 5-25 / 100-130, halo "
@@ -584,12 +586,13 @@ def run_scenario(args):
                     "config": {"workload": "512 replicas, N_r log-uniform [1024, 65536], k=7, F=16",
                                "n_total": total}})
     else:
+        kw = {"n": args.scenario_n} if args.scenario_n > 0 else {}
         if args.scenario == "voronoi":
             w = W.voronoi_mixed(eta=0.1)
         elif args.scenario == "voronoi3d":
-            w = W.voronoi_3d()
+            w = W.voronoi_3d(**kw)
         else:
-            w = W.knn_3d()
+            w = W.knn_3d(**kw)
         sim = vk.from_workload(w, stream=stream)
         sim.step(args.warmup)
         ms = _timed(stream, lambda: sim.step(args.steps)) / args.steps

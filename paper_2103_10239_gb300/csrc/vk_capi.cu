@@ -150,7 +150,9 @@ float default_occupancy(const vk_params& p, int dim, int64_t n_total, int n_rep)
     auto it = g_tuned.find(tune_key(p, dim, n_total, n_rep));
     if (it != g_tuned.end()) return it->second;
   }
-  if (p.rule == VK_RULE_VORONOI) return 2.0f;
+  // Voronoi: 2 particles per cell in 2D; 1 in 3D (a sweep of 1, 1.5, 2 and 3
+  // at N = 2^18 uniform: 83, 89, 96, 109 ms per step)
+  if (p.rule == VK_RULE_VORONOI) return dim == 2 ? 2.0f : 1.0f;
   // 2D kNN and metric: coarse cells of a few hundred particles split into
   // sub-grids (the radius-first search measured fastest at 256 on uniform
   // and clustered flocks); 3D: cells of about 1.5 particles (the cube search)

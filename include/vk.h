@@ -14,13 +14,15 @@
  * Conventions shared by every call
  *   - Positions are fixed-point grid coordinates: int32 pos_q in [0, L_q) per
  *     axis, real coordinate = pos_q * 2^-F.  The box is periodic with edge
- *     L_q <= 2^31 grid units (<= 2^30 for the Voronoi rule).  Distances use the
+ *     L_q <= 2^31 grid units (<= 2^30 for the 2D Voronoi rule, <= 2^23 for the
+ *     3D one, whose exact int128 predicates need it).  Distances use the
  *     minimum image, differences mapped into (-L_q/2, L_q/2], and are compared
  *     as exact integer squared distances D.
  *   - kNN lists are ordered by (D, id) ascending (ties broken by the smaller
  *     particle id); self is excluded.  Voronoi lists hold the ids whose
- *     Voronoi cell shares an edge of positive length with the particle's cell
- *     (Delaunay edges between cocircular points are dropped), sorted by id.
+ *     Voronoi cell shares an edge of positive length (2D) or a face of positive
+ *     area (3D) with the particle's cell (Delaunay edges between cocircular or
+ *     cospherical points are dropped), sorted by id.
  *   - Headings are FP32 unit vectors (the authoritative state).  In 2D the
  *     angle theta = atan2(n_y, n_x) in [0, 2pi) is also exported.
  *   - Noise: Philox4x32-10 keyed by the 64-bit seed, counter (particle id,
@@ -44,12 +46,15 @@
  *     (capacity overflow, values out of range) latch a sticky status word on
  *     the device; it is returned by the next vk_sync or vk_get_* call.
  *     vk_last_error gives a message for the last failure.
- *   - Coincident particles are valid input under both rules.  The paper
+ *   - Coincident particles are valid input under both rules in 2D.  The paper
  *     leaves the Voronoi cell of coincident points undefined; this library
  *     reads them as one Voronoi site: they are each other's neighbors and
  *     share the site's other neighbors.  (An earlier reading returned
  *     VK_ERR_DEGENERATE; coincident points do occur on the fixed-point grid
- *     in long runs, so an error would end the simulation.)
+ *     in long runs, so an error would end the simulation.)  The 3D Voronoi
+ *     rule reports coincident particles as VK_ERR_DEGENERATE (latched by the
+ *     step, returned by the next synchronising call); there a collision on the
+ *     2^-F grid needs ~2^(3F) / N^2 steps.
  */
 #ifndef VK_NM_H
 #define VK_NM_H
@@ -70,15 +75,16 @@ typedef enum {
   VK_ERR_CAPACITY = 4,   /* an output buffer or an internal bound was too small */
   VK_ERR_RANGE = 5,      /* box / fixed-point range outside the supported limits */
   VK_ERR_DEGENERATE = 6, /* the tissue model met coincident particles or a zero-length Voronoi edge
-                            (the Voronoi rule itself treats coincident points as one site) */
+                            (the 2D Voronoi rule itself treats coincident points as one site),
+                            or the 3D Voronoi rule met coincident particles */
   VK_ERR_TIMEOUT = 7,    /* a bounded device wait gave up */
   VK_ERR_STATE = 8       /* call not valid in the current state */
 } vk_status;
 
 /* Neighbor rules (Sec. "Metric and topological flocking models"): the k
  * nearest particles at any distance (optionally only those inside a field of
- * view, 2D), the Voronoi neighbors (2D), or every particle within the metric
- * radius r0 (the original Vicsek rule, 2D and 3D). */
+ * view, 2D), the Voronoi neighbors (2D and 3D), or every particle within the
+ * metric radius r0 (the original Vicsek rule, 2D and 3D). */
 typedef enum { VK_RULE_KNN = 0, VK_RULE_VORONOI = 1, VK_RULE_METRIC = 2 } vk_rule;
 typedef enum { VK_NOISE_ANGULAR = 0, VK_NOISE_VECTORIAL = 1 } vk_noise;
 typedef enum { VK_SUM_PLAIN = 0, VK_SUM_COMPENSATED = 1, VK_SUM_FP64 = 2 } vk_sum_mode;
@@ -135,7 +141,7 @@ typedef struct {
                            in view aligns with those it has (its list is shorter). */
   float fov_cos;        /* cosine of the half-angle of the field of view, in [-1, 1]; -1 is the
                            full circle (the plain rule), 0 the half-plane ahead */
-  int32_t voronoi_rebuild; /* VK_RULE_VORONOI: 0 (default) = start every cell from last step's
+  int32_t voronoi_rebuild; /* VK_RULE_VORONOI, 2D: 0 (default) = start every cell from last step's
                            neighbors and re-check it (Sec. "Computational tools: Voronoi neighbor
                            lists": the old triangulation is kept where every circumcircle is still
                            empty and repaired where it is not); 1 = build every cell from scratch.
@@ -176,9 +182,10 @@ vk_status vk_step(vk_sim* sim, int64_t nsteps);
  * nearest in view, so a row may be shorter than k.  Metric rule: every other
  * particle at exact squared distance <= r0q^2 (reciprocal), row i sorted by
  * id.  Voronoi rule: the particles
- * whose Voronoi cell shares an edge of positive length with i's, i.e. the
- * Delaunay neighbors by the empty-circumcircle property (Sec. "Computational
- * tools: Voronoi neighbor lists"), row i sorted by id.  These are the lists
+ * whose Voronoi cell shares an edge of positive length (2D) or a face of
+ * positive area (3D) with i's, i.e. the Delaunay neighbors by the
+ * empty-circumcircle (circumsphere) property (Sec. "Computational tools:
+ * Voronoi neighbor lists"), row i sorted by id.  These are the lists
  * the next vk_step uses.  If ids_capacity is too small (or ids is NULL),
  * *nnz_needed receives the count and VK_ERR_CAPACITY is returned (VK_OK when
  * ids is NULL).  Synchronous. */

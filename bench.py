@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--voronoi3-kernel", type=int, choices=[0, 1], default=None,
+                    help="voronoi3d scenario: 0 one thread per cell, 1 one warp per cell (default: the library's)")
     ap.add_argument("--scenario-n", type=int, default=0,
                     help="particles of the voronoi3d / knn3d scenario (0: the workload's default)")
     ap.add_argument("--occupancy", type=float, default=256.0,
@@ -593,7 +595,8 @@ def run_scenario(args):
             w = W.voronoi_3d(**kw)
         else:
             w = W.knn_3d(**kw)
-        sim = vk.from_workload(w, stream=stream)
+        over = {} if args.voronoi3_kernel is None else {"voronoi3_kernel": args.voronoi3_kernel}
+        sim = vk.from_workload(w, stream=stream, **over)
         sim.step(args.warmup)
         ms = _timed(stream, lambda: sim.step(args.steps)) / args.steps
         sim.set_profiling(True)
@@ -602,7 +605,7 @@ def run_scenario(args):
         sim.close()
         out.update({"metric": f"particle-steps/s ({w.rule}, {w.dim}D)", "value": w.n / (ms * 1e-3),
                     "unit": "particle-steps/s", "ms_per_step": ms,
-                    "config": {"workload": w.name, "n": w.n, "rule": w.rule, "k": w.k, "dim": w.dim},
+                    "config": dict({"workload": w.name, "n": w.n, "rule": w.rule, "k": w.k, "dim": w.dim}, **over),
                     "phases_ms_per_step": {k: v[0] / 3 for k, v in prof.items() if v[1]}})
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = scenario_cpu_baseline(w, args.cpu_seconds)

@@ -146,6 +146,11 @@ typedef struct {
                            lists": the old triangulation is kept where every circumcircle is still
                            empty and repaired where it is not); 1 = build every cell from scratch.
                            Results never depend on it; only the speed does. */
+  int32_t voronoi3_kernel; /* VK_RULE_VORONOI, 3D: 0 (default) = one thread builds each cell (in
+                           thread-local memory); 1 = one warp builds each cell (in shared memory:
+                           the lanes test the vertices and solve new vertices in parallel).  Both
+                           use the same exact predicates and give the same results; only the speed
+                           differs. */
 } vk_params;
 
 /* Fills p with the defaults: kNN, k = 7, v0 = 0.5, dt = 1, eta = 0.3, seed = 1,

@@ -124,6 +124,7 @@ StepParams step_params(const vk_sim* s) {
   P.halo_alpha = s->prm.search_halo > 0.f ? s->prm.search_halo : (s->dim == 3 ? 1.3f : 1.15f);
   P.halo_beta = s->prm.search_halo_step >= 0.f ? s->prm.search_halo_step : 0.f;
   P.fov_cq = fov_cq(s->prm);
+  P.v3_warp = s->prm.voronoi3_kernel;
   P.stats = (s->prof && s->prof_counters) ? s->d_stats : nullptr;
   return P;
 }
@@ -376,6 +377,7 @@ bool valid_params(const vk_params* p, int dim, std::string* why) {
     return *why = "r0 must be finite and >= 0", false;
   if (p->fov != 0 && p->fov != 1) return *why = "fov must be 0 or 1", false;
   if (p->voronoi_rebuild != 0 && p->voronoi_rebuild != 1) return *why = "voronoi_rebuild must be 0 or 1", false;
+  if (p->voronoi3_kernel != 0 && p->voronoi3_kernel != 1) return *why = "voronoi3_kernel must be 0 or 1", false;
   if (p->fov && (p->rule != VK_RULE_KNN || dim != 2)) return *why = "a field of view needs the 2D kNN rule", false;
   if (p->fov && !(p->fov_cos >= -1.f && p->fov_cos <= 1.f)) return *why = "fov_cos must be in [-1, 1]", false;
   return true;
@@ -550,6 +552,7 @@ void vk_default_params(vk_params* p) {
   p->r0 = 1.0f;
   p->fov = 0;
   p->fov_cos = -1.0f;
+  p->voronoi3_kernel = 0;
 }
 
 vk_status vk_init(const int32_t* pos_q, const float* heading, int32_t heading_kind, int64_t n,

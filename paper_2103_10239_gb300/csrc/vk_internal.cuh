@@ -68,6 +68,8 @@ struct StepParams {
   // 2D kNN field of view: the cosine of the half-angle in 2^-24 units, or
   // INT_MIN for the full circle (the plain rule)
   int32_t fov_cq;
+  // 3D Voronoi: 0 one thread per cell, 1 one warp per cell
+  int32_t v3_warp;
   // tracing only (NULL = off): [candidates, runs or squares, max candidates,
   // particles, particles whose own coarse cell is split (walk) or that fell
   // back to the walk (radius first), then radius first only: squares, runs,

@@ -209,12 +209,14 @@ V3_HD void set_triangle(Cell& C, int t, int a, int b, int c) {
   ++C.pref[c];
 }
 
-// the box bounded by the particle's own images at +-L per axis
+// the box bounded by the particle's own images at +-L per axis; clears the
+// scratch sg (Cell::T entries) that cell_clip and clip_topology take
 template <class Cell>
-V3_HD void cell_init(Cell& C, const uint32_t* L) {
+V3_HD void cell_init(Cell& C, const uint32_t* L, int8_t* sg) {
   C.np = 6;
   C.nt = 8;
   C.status = kOk;
+  for (int t = 0; t < Cell::T; ++t) sg[t] = 0;
   for (int a = 0; a < 3; ++a)
     for (int s = 0; s < 2; ++s) {
       const int p = 2 * a + s;
@@ -241,24 +243,16 @@ V3_HD void cell_init(Cell& C, const uint32_t* L) {
   refresh_radius(C);
 }
 
-// Clip by the plane of the site at offset d (slot: its sorted slot).
-// Returns 1 when some vertex lay strictly beyond it, 0 when not, -1 on a
-// failure (C.status set).  sg is scratch of Cell::T entries.
+// The topology of a clip by the plane at offset d (slot: the site's sorted
+// slot), given sg[t] = 1 for the triangles whose point lies strictly beyond
+// it (0 for every other slot below C.nt; at least one is 1): a new plane,
+// the boundary edges of the removed region, the removed triangles freed and
+// the new ones (p, q, e) linked in their place.  The new triangles' slots go
+// to bt[0..*nb); their points are NOT computed (vertex_of does that).
+// Returns the new plane, or -1 on a failure (C.status set).  sg is left
+// cleared.
 template <class Cell>
-V3_HD int cell_clip(Cell& C, const int32_t* d, int32_t slot, int8_t* sg) {
-  const int64_t w = norm2(d);
-  const float wf = (float)w;
-  if (wf >= 4.f * C.r2) return 0;  // |d| / 2 beyond every vertex: cannot cut
-  const float band = side_band(C, wf);
-  int nout = 0;
-  for (int t = 0; t < C.nt; ++t) {
-    sg[t] = 0;
-    if (C.ty[t][3] == 0.f) continue;
-    const int side = side_of(C, t, d, wf, band);
-    sg[t] = (int8_t)(side > 0);
-    nout += side > 0;
-  }
-  if (nout == 0) return 0;
+V3_HD int clip_topology(Cell& C, const int32_t* d, int32_t slot, int8_t* sg, uint8_t* bt, int* nb_out) {
   const int e = new_plane(C, d, slot);
   if (e < 0) {
     C.status = kCapacity;
@@ -266,7 +260,7 @@ V3_HD int cell_clip(Cell& C, const int32_t* d, int32_t slot, int8_t* sg) {
   }
   // boundary edges (p -> q) of the removed region, with the kept triangle
   // across them
-  uint8_t bp[Cell::B], bq[Cell::B], bo[Cell::B], bt[Cell::B];
+  uint8_t bp[Cell::B], bq[Cell::B], bo[Cell::B];
   int nb = 0;
   for (int t = 0; t < C.nt; ++t) {
     if (!sg[t]) continue;
@@ -290,6 +284,7 @@ V3_HD int cell_clip(Cell& C, const int32_t* d, int32_t slot, int8_t* sg) {
   // free the removed triangles; their slots are reused first
   for (int t = 0; t < C.nt; ++t) {
     if (!sg[t]) continue;
+    sg[t] = 0;
     C.ty[t][3] = 0.f;
     --C.pref[C.tp[t][0]];
     --C.pref[C.tp[t][1]];
@@ -306,12 +301,17 @@ V3_HD int cell_clip(Cell& C, const int32_t* d, int32_t slot, int8_t* sg) {
       ++C.nt;
     }
     bt[j] = (uint8_t)scan;
-    C.ty[scan][3] = 1.f;  // reserve
+    C.ty[scan][3] = 1.f;  // alive (its point follows)
     ++scan;
   }
   for (int j = 0; j < nb; ++j) {
     const int t = bt[j];
-    set_triangle(C, t, bp[j], bq[j], e);
+    C.tp[t][0] = bp[j];
+    C.tp[t][1] = bq[j];
+    C.tp[t][2] = (uint8_t)e;
+    ++C.pref[bp[j]];
+    ++C.pref[bq[j]];
+    ++C.pref[e];
     // edge 0 (p, q): the kept triangle, which points back across (q, p)
     const int o = bo[j];
     C.tn[t][0] = (uint8_t)o;
@@ -332,6 +332,38 @@ V3_HD int cell_clip(Cell& C, const int32_t* d, int32_t slot, int8_t* sg) {
     C.tn[t][2] = bt[pv];
   }
   while (C.nt > 0 && C.ty[C.nt - 1][3] == 0.f) --C.nt;
+  *nb_out = nb;
+  return e;
+}
+
+// the point of triangle t from its planes
+template <class Cell>
+V3_HD void vertex_of(Cell& C, int t) {
+  vertex_y(C.pd[C.tp[t][0]], C.pd[C.tp[t][1]], C.pd[C.tp[t][2]], C.ty[t]);
+}
+
+// Clip by the plane of the site at offset d (slot: its sorted slot).
+// Returns 1 when some vertex lay strictly beyond it, 0 when not, -1 on a
+// failure (C.status set).  sg is scratch of Cell::T entries, all zero on
+// entry and on return.
+template <class Cell>
+V3_HD int cell_clip(Cell& C, const int32_t* d, int32_t slot, int8_t* sg) {
+  const int64_t w = norm2(d);
+  const float wf = (float)w;
+  if (wf >= 4.f * C.r2) return 0;  // |d| / 2 beyond every vertex: cannot cut
+  const float band = side_band(C, wf);
+  int nout = 0;
+  for (int t = 0; t < C.nt; ++t) {
+    if (C.ty[t][3] == 0.f) continue;
+    const int side = side_of(C, t, d, wf, band);
+    sg[t] = (int8_t)(side > 0);
+    nout += side > 0;
+  }
+  if (nout == 0) return 0;
+  uint8_t bt[Cell::B];
+  int nb = 0;
+  if (clip_topology(C, d, slot, sg, bt, &nb) < 0) return -1;
+  for (int j = 0; j < nb; ++j) vertex_of(C, bt[j]);
   refresh_radius(C);
   return 1;
 }

@@ -45,7 +45,7 @@ class vk_params(ctypes.Structure):
                 ("knn_search", ctypes.c_int32), ("search_halo", ctypes.c_float),
                 ("search_halo_step", ctypes.c_float), ("replica_offset", ctypes.c_int32),
                 ("r0", ctypes.c_float), ("fov", ctypes.c_int32), ("fov_cos", ctypes.c_float),
-                ("voronoi_rebuild", ctypes.c_int32)]
+                ("voronoi_rebuild", ctypes.c_int32), ("voronoi3_kernel", ctypes.c_int32)]
 
 
 class vk_info(ctypes.Structure):

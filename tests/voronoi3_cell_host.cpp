@@ -41,7 +41,7 @@ int build(Cell& C, int8_t* sg, int64_t n, const int32_t* pos, const int64_t* box
       std::swap(ord[j], ord[s % (uint64_t)(j + 1)]);
     }
   }
-  cell_init(C, L);
+  cell_init(C, L, sg);
   for (int64_t j : ord) {
     if (j == i) continue;
     const int32_t d[3] = {(int32_t)off(j, 0), (int32_t)off(j, 1), (int32_t)off(j, 2)};

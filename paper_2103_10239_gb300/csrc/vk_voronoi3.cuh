@@ -37,10 +37,16 @@
 #include <cmath>
 #include <cstdint>
 
+// V3_HD: small helpers, inlined.  V3_OUT: the large ones (int128 solves, the
+// rewiring of a clip, the face test), kept out of line on the device so that
+// one copy of each serves every call site: inlined copies made the kernels
+// stall on instruction fetch.
 #ifdef __CUDACC__
 #define V3_HD __host__ __device__ __forceinline__
+#define V3_OUT __host__ __device__ __noinline__
 #else
 #define V3_HD inline
+#define V3_OUT inline
 #endif
 
 namespace vk {
@@ -118,7 +124,7 @@ V3_HD int sgn128(i128 v) { return (v > 0) - (v < 0); }
 
 // exact side of the point of planes (a, b, c) with respect to plane e:
 // +1 beyond (d_e.y > w_e), 0 on it, -1 inside
-V3_HD int side_exact(const int32_t* da, const int32_t* db, const int32_t* dc, const int32_t* de) {
+V3_OUT int side_exact(const int32_t* da, const int32_t* db, const int32_t* dc, const int32_t* de) {
   const i128 m = det3(da, db, dc);
   const i128 t = -(i128)norm2(da) * det3(db, dc, de) + (i128)norm2(db) * det3(da, dc, de) -
                  (i128)norm2(dc) * det3(da, db, de) + (i128)norm2(de) * m;
@@ -126,7 +132,7 @@ V3_HD int side_exact(const int32_t* da, const int32_t* db, const int32_t* dc, co
 }
 
 // y = 2x of the point of planes (a, b, c) by Cramer's rule on exact integers
-V3_HD void vertex_y(const int32_t* da, const int32_t* db, const int32_t* dc, float* y) {
+V3_OUT void vertex_y(const int32_t* da, const int32_t* db, const int32_t* dc, float* y) {
   const int32_t* M[3] = {da, db, dc};
   const int64_t w[3] = {norm2(da), norm2(db), norm2(dc)};
   int64_t cf[3][3];
@@ -252,7 +258,7 @@ V3_HD void cell_init(Cell& C, const uint32_t* L, int8_t* sg) {
 // Returns the new plane, or -1 on a failure (C.status set).  sg is left
 // cleared.
 template <class Cell>
-V3_HD int clip_topology(Cell& C, const int32_t* d, int32_t slot, int8_t* sg, uint8_t* bt, int* nb_out) {
+V3_OUT int clip_topology(Cell& C, const int32_t* d, int32_t slot, int8_t* sg, uint8_t* bt, int* nb_out) {
   const int e = new_plane(C, d, slot);
   if (e < 0) {
     C.status = kCapacity;
@@ -347,7 +353,7 @@ V3_HD void vertex_of(Cell& C, int t) {
 // failure (C.status set).  sg is scratch of Cell::T entries, all zero on
 // entry and on return.
 template <class Cell>
-V3_HD int cell_clip(Cell& C, const int32_t* d, int32_t slot, int8_t* sg) {
+V3_OUT int cell_clip(Cell& C, const int32_t* d, int32_t slot, int8_t* sg) {
   const int64_t w = norm2(d);
   const float wf = (float)w;
   if (wf >= 4.f * C.r2) return 0;  // |d| / 2 beyond every vertex: cannot cut
@@ -370,7 +376,7 @@ V3_HD int cell_clip(Cell& C, const int32_t* d, int32_t slot, int8_t* sg) {
 
 // Does the face of plane p (live, C.pref[p] > 0) have positive area?
 template <class Cell>
-V3_HD bool face_positive(const Cell& C, int p) {
+V3_OUT bool face_positive(const Cell& C, int p) {
   int t0 = -1, k0 = 0;
   for (int t = 0; t < C.nt && t0 < 0; ++t) {
     if (C.ty[t][3] == 0.f) continue;

@@ -19,7 +19,7 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libvk_nm.so")
 SOURCES = ["vk_capi.cu", "vk_cells.cu", "vk_knn.cu", "vk_knn2d.cu", "vk_metric.cu", "vk_noalloc.cu",
            "vk_tissue.cu", "vk_voronoi.cu", "vk_voronoi3.cu"]
-HEADERS = [os.path.join(CSRC, h) for h in ("vk_internal.cuh", "vk_box2d.cuh", "vk_voronoi.cuh", "vk_voronoi3.cuh")] + \
+HEADERS = [os.path.join(CSRC, h) for h in ("vk_internal.cuh", "vk_box2d.cuh", "vk_voronoi.cuh", "vk_voronoi3.cuh", "vk_voronoi3_api.cuh")] + \
     [os.path.join(ROOT, "include", "vk.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--extended-lambda", "-Xcompiler", "-fPIC",

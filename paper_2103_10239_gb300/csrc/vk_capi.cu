@@ -18,6 +18,7 @@
 
 #include "../../include/vk.h"
 #include "vk_internal.cuh"
+#include "vk_voronoi3_api.cuh"
 
 using namespace vk;
 
@@ -124,7 +125,6 @@ StepParams step_params(const vk_sim* s) {
   P.halo_alpha = s->prm.search_halo > 0.f ? s->prm.search_halo : (s->dim == 3 ? 1.3f : 1.15f);
   P.halo_beta = s->prm.search_halo_step >= 0.f ? s->prm.search_halo_step : 0.f;
   P.fov_cq = fov_cq(s->prm);
-  P.v3_warp = s->prm.voronoi3_kernel;
   P.stats = (s->prof && s->prof_counters) ? s->d_stats : nullptr;
   return P;
 }
@@ -318,7 +318,7 @@ vk_status enqueue_step(vk_sim* s) {
   else if (s->prm.rule == VK_RULE_KNN) VK_CUDA(s, launch_knn_step(s->g, s->b, P, s->stream));
   else if (s->prm.rule == VK_RULE_METRIC) VK_CUDA(s, launch_metric_step(s->g, s->b, P, s->stream));
   else if (s->dim == 2) VK_CUDA(s, launch_voronoi_step(s->g, s->b, P, s->stream));
-  else VK_CUDA(s, launch_voronoi3_step(s->g, s->b, P, s->stream));
+  else VK_CUDA(s, launch_voronoi3_step(s->g, s->b, P, s->prm.voronoi3_kernel, s->stream));
   const int deferred_launches = (s->prm.rule == VK_RULE_KNN && s->dim == 2 && s->prm.knn_search == 0) ? 2 : 0;
   if ((st = record_end(s, 0, e0, search_launches(s) - deferred_launches))) return st;
   if (deferred_launches) {

@@ -68,8 +68,6 @@ struct StepParams {
   // 2D kNN field of view: the cosine of the half-angle in 2^-24 units, or
   // INT_MIN for the full circle (the plain rule)
   int32_t fov_cq;
-  // 3D Voronoi: 0 one thread per cell, 1 one warp per cell
-  int32_t v3_warp;
   // tracing only (NULL = off): [candidates, runs or squares, max candidates,
   // particles, particles whose own coarse cell is split (walk) or that fell
   // back to the walk (radius first), then radius first only: squares, runs,
@@ -731,11 +729,6 @@ cudaError_t launch_tissue(const Geometry& g, const Buffers& b, int rep, int n, d
 cudaError_t launch_voronoi_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st);
 cudaError_t launch_voronoi_export(const Geometry& g, const Buffers& b, int rep, int n, int pass, int32_t* deg,
                                   const int64_t* out_off, int32_t* out_ids, cudaStream_t st);
-// vk_voronoi3.cu (3D Voronoi rule)
-cudaError_t launch_voronoi3_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st);
-cudaError_t launch_voronoi3_export(const Geometry& g, const Buffers& b, int rep, int n, int pass, int32_t* deg,
-                                   const int64_t* out_off, int32_t* out_ids, cudaStream_t st);
-
 // largest Voronoi cell (edges) handled; larger cells latch VK_ERR_CAPACITY
 constexpr int kVoronoiMaxDeg = 256;
 

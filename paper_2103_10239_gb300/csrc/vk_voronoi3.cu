@@ -17,6 +17,7 @@
 
 #include "vk_internal.cuh"
 #include "vk_voronoi3.cuh"
+#include "vk_voronoi3_api.cuh"
 
 namespace vk {
 
@@ -491,8 +492,9 @@ GridView grid_view3(const Buffers& b) {
 
 }  // namespace
 
-cudaError_t launch_voronoi3_step(const Geometry& g, const Buffers& b, const StepParams& P, cudaStream_t st) {
-  if (P.v3_warp) {
+cudaError_t launch_voronoi3_step(const Geometry& g, const Buffers& b, const StepParams& P, int warp,
+                                 cudaStream_t st) {
+  if (warp) {
     // persistent: as many blocks as fit at once; warps take particles from
     // the work counter (ovf_count[1], cleared by every scatter)
     static int per_sm = 0;

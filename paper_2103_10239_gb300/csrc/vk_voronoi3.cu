@@ -3,16 +3,24 @@
 // share a face; the relation is reciprocal) fused with the Vicsek update of
 // Eq. (1) and Eq. (2) (vectorial noise, as every 3D rule here).
 //
-// One thread per particle, in cell-sorted order.  The cell starts as the box
-// bounded by the particle's own periodic images and is clipped by the bisector
-// planes of the candidates that the ring walk of the uniform 3D grid delivers
-// (vk_voronoi3.cuh: exact predicates, dual triangulation).  A site at offset
-// d can cut the cell only if |d| < 2R, R the distance of the farthest vertex,
-// so the walk stops once the scanned block holds that ball.  When 2R reaches a
-// quarter of the box, non-minimum images of other particles can cut too: the
-// cell is then finished against every image of every particle within 2R.
-// Neighbors are the sites of faces of positive area, in id order.
-// Coincident particles latch VK_ERR_DEGENERATE (no cell separates them).
+// The cell starts as the box bounded by the particle's own periodic images
+// and is clipped by the bisector planes of the candidates that the ring walk
+// of the uniform 3D grid delivers (vk_voronoi3.cuh: exact predicates, dual
+// triangulation).  A site at offset d can cut the cell only if |d| < 2R, R the
+// distance of the farthest vertex, so the walk stops once the scanned block
+// holds that ball.  When 2R reaches a quarter of the box, non-minimum images
+// of other particles can cut too: the cell is then finished against every
+// image of every particle within 2R.  Neighbors are the sites of faces of
+// positive area, in id order.  Coincident particles latch VK_ERR_DEGENERATE
+// (no cell separates them).
+//
+// Two kernels build the cells, with the same results:
+//   * voronoi3_step_kernel (the default): one thread per particle, in
+//     cell-sorted order, the cell in thread-local memory;
+//   * voronoi3_warp_kernel: one warp per particle, the cell in shared memory,
+//     vertex tests and vertex solves spread over the lanes.
+// Cells whose intermediate polytope outgrows either are rebuilt by
+// voronoi3_overflow_kernel with room for 128 faces and 256 vertices.
 #include <algorithm>
 
 #include "vk_internal.cuh"

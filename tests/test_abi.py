@@ -89,6 +89,7 @@ def test_rule_variant_argument_errors_without_gpu():
         (dict(k=2, fov=2), vk.VK_ERR_ARG),
         (dict(rule="voronoi", fov=1, fov_cos=0.0), vk.VK_ERR_ARG),
         (dict(rule="metric", r0=1e6), vk.VK_ERR_RANGE),  # r0 * 2^16 above 2^31
+        (dict(rule="voronoi", voronoi3_kernel=2), vk.VK_ERR_ARG),
     ]
     for kw, status in bad:
         with pytest.raises(vk.VKError) as e:
@@ -104,6 +105,7 @@ def test_rule_variant_defaults():
     p = vk.default_params()
     assert (p.fov, p.r0, p.fov_cos) == (0, 1.0, -1.0)
     assert vk.default_params(rule="metric").rule == vk.VK_RULE_METRIC
+    assert vk.default_params().voronoi3_kernel == 0  # one thread per 3D Voronoi cell
 
 
 def test_tissue_argument_errors_without_gpu():

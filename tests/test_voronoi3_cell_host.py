@@ -89,3 +89,121 @@ def test_degenerate_grids(lib):
     # index order sweeps the lattice plane by plane and can outgrow even the
     # larger cell; the kernel's ring walk visits near sites first
     _same(lib, pos, (m * sp,) * 3, orders=(1, 2))
+
+
+def _i32(v):
+    a = np.ascontiguousarray(v, dtype=np.int32)
+    return a, a.ctypes.data
+
+
+def _side(lib, da, db, dc, de):
+    arrs = [_i32(v) for v in (da, db, dc, de)]
+    return lib.v3_host_side(*[p for _, p in arrs])
+
+
+def _setup_predicates(lib):
+    lib.v3_host_side.restype = ctypes.c_int
+    lib.v3_host_side.argtypes = [ctypes.c_void_p] * 4
+    lib.v3_host_vertex.restype = None
+    lib.v3_host_vertex.argtypes = [ctypes.c_void_p] * 4
+
+
+def _random_offsets(rng, m, norm_max):
+    """m integer vectors of Euclidean norm below norm_max (and nonzero)."""
+    out = []
+    while len(out) < m:
+        v = rng.integers(-int(norm_max), int(norm_max), size=3)
+        if 0 < int(v @ v) < norm_max * norm_max:
+            out.append(v)
+    return np.array(out, dtype=np.int64)
+
+
+def test_exact_side_matches_the_oracle_up_to_the_range_limit(lib):
+    """sign(d_e.y - |d_e|^2) at the vertex of planes a, b, c: the builder's
+    int128 determinant against the oracle's independent 256-bit one, for
+    offsets of norm up to 2^24 (the builder's stated range)."""
+    _setup_predicates(lib)
+    rng = np.random.default_rng(21)
+    for norm_max in (1 << 10, 1 << 20, (1 << 24) - 1):
+        d = _random_offsets(rng, 4 * 400, norm_max).reshape(400, 4, 3)
+        for da, db, dc, de in d:
+            if _det_exact(da, db, dc) == 0:
+                continue  # planes without a common point
+            assert _side(lib, da, db, dc, de) == oracle.voronoi3_side(da, db, dc, de)
+
+
+def test_exact_zeros_at_large_coordinates(lib):
+    """Planes through one point: with y = (2a, 2b, 2c), every offset d at a
+    corner of the box [0, 2a] x [0, 2b] x [0, 2c] has d.y = |d|^2, so the
+    vertex of any three of them lies exactly on the fourth (sign 0).  Moving
+    the fourth offset by one grid unit along an axis gives small values of
+    either sign next to large terms; their signs must match the oracle's.
+    Corners up to norm sqrt(3) 2^23 < 2^24."""
+    _setup_predicates(lib)
+    rng = np.random.default_rng(22)
+    for _ in range(60):
+        a, b, c = (int(x) for x in rng.integers(1 << 20, 1 << 23, size=3))
+        corners = [np.array([sx * 2 * a, sy * 2 * b, sz * 2 * c]) for sx in (0, 1) for sy in (0, 1) for sz in (0, 1)
+                   if sx or sy or sz]
+        idx = rng.choice(len(corners), size=4, replace=False)
+        da, db, dc, de = (corners[i] for i in idx)
+        if _det_exact(da, db, dc) == 0:
+            continue
+        assert oracle.voronoi3_side(da, db, dc, de) == 0
+        assert _side(lib, da, db, dc, de) == 0
+        for k in range(3):
+            for step in (-1, 1):
+                e2 = de.copy()
+                e2[k] += step
+                if int(e2 @ e2) >= (1 << 48):
+                    continue
+                assert _side(lib, da, db, dc, e2) == oracle.voronoi3_side(da, db, dc, e2)
+
+
+def test_vertex_estimate_error_bound(lib):
+    """The FP32 vertex y (d_x.y = |d_x|^2, x = a, b, c) errs by at most
+    2^-22 |y_k| per coordinate (the bound the FP32 side filter assumes):
+    checked against the exact rational solution, on random and on
+    ill-conditioned (nearly coplanar) triples up to the range limit."""
+    from fractions import Fraction
+    _setup_predicates(lib)
+    rng = np.random.default_rng(23)
+
+    def exact(da, db, dc):
+        M = [[Fraction(int(x)) for x in r] + [Fraction(int(r @ r))] for r in (da, db, dc)]
+        for col in range(3):
+            piv = next(r for r in range(col, 3) if M[r][col] != 0)
+            M[col], M[piv] = M[piv], M[col]
+            for r in range(3):
+                if r != col and M[r][col] != 0:
+                    f = M[r][col] / M[col][col]
+                    M[r] = [x - f * y for x, y in zip(M[r], M[col])]
+        return [M[k][3] / M[k][k] for k in range(3)]
+
+    cases = []
+    for norm_max in (1 << 12, 1 << 22, (1 << 24) - 1):
+        for t in _random_offsets(rng, 3 * 150, norm_max).reshape(150, 3, 3):
+            cases.append(t)
+    for _ in range(150):  # nearly coplanar: c close to a combination of a and b
+        da, db = _random_offsets(rng, 2, 1 << 22)
+        dc = (da + db) // 2 + rng.integers(-2, 3, size=3)
+        cases.append(np.array([da, db, dc]))
+    checked = 0
+    for da, db, dc in cases:
+        if _det_exact(da, db, dc) == 0:
+            continue
+        y = np.zeros(3, dtype=np.float32)
+        arrs = [_i32(v) for v in (da, db, dc)]
+        lib.v3_host_vertex(arrs[0][1], arrs[1][1], arrs[2][1], y.ctypes.data)
+        ye = exact(da, db, dc)
+        for k in range(3):
+            err = abs(Fraction(float(y[k])) - ye[k])
+            assert err <= Fraction(1, 1 << 22) * abs(Fraction(float(y[k]))), (da, db, dc, k)
+        checked += 1
+    assert checked > 500
+
+
+def _det_exact(a, b, c):
+    a, b, c = ([int(x) for x in v] for v in (a, b, c))
+    return (a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) +
+            a[2] * (b[0] * c[1] - b[1] * c[0]))

@@ -99,3 +99,13 @@ extern "C" int64_t v3_host_neighbors(int64_t n, const int32_t* pos, const int64_
   }
   return n_large;
 }
+
+// The exact side test and the FP32 vertex estimate of the builder, on
+// explicit plane offsets (for the predicate tests).
+extern "C" int v3_host_side(const int32_t* da, const int32_t* db, const int32_t* dc, const int32_t* de) {
+  return side_exact(da, db, dc, de);
+}
+
+extern "C" void v3_host_vertex(const int32_t* da, const int32_t* db, const int32_t* dc, float* y) {
+  vertex_y(da, db, dc, y);
+}

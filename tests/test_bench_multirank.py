@@ -63,7 +63,8 @@ def test_reference_arm_runs_on_rank_zero_only():
 
 def test_oracle_legs_of_the_bench_on_small_systems():
     """The bench's CPU legs (the oracle timed as it stands) run without a GPU:
-    a bounded kNN sample, a 3D sample and a whole Voronoi step."""
+    a bounded kNN sample, a 3D sample, a whole Voronoi step and a sample of
+    3D Voronoi cells."""
     sys.path.insert(0, ROOT)
     import bench
     from paper_2103_10239_gb300 import workloads as W
@@ -75,3 +76,6 @@ def test_oracle_legs_of_the_bench_on_small_systems():
     wv = W.uniform_system(500, 22.4, 16, 2, input_seed=6, rule="voronoi", k=0, v0=0.3, eta=0.1)
     cb = bench.scenario_cpu_baseline(wv, 0.05)
     assert cb["value"] > 0 and cb["kind"] == "oracle" and cb["cores"] == 1
+    wv3 = W.voronoi_3d(n=1500)
+    cb3 = bench.scenario_cpu_baseline(wv3, 0.05)
+    assert cb3["value"] > 0 and cb3["kind"] == "oracle" and "1500 random particles" in cb3["sample"]

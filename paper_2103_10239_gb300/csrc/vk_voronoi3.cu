@@ -505,13 +505,14 @@ cudaError_t launch_voronoi3_step(const Geometry& g, const Buffers& b, const Step
   if (warp) {
     // persistent: as many blocks as fit at once; warps take particles from
     // the work counter (ovf_count[1], cleared by every scatter)
-    static int per_sm = 0;
-    if (per_sm == 0) {
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, voronoi3_warp_kernel,
-                                                                    32 * kV3WarpsPerBlock, 0);
-      if (e != cudaSuccess) return e;
-      per_sm = std::max(per_sm, 1);
-    }
+    // (initialised once, thread-safely; one block per SM if the query fails)
+    static const int per_sm = [] {
+      int blocks = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, voronoi3_warp_kernel, 32 * kV3WarpsPerBlock, 0) !=
+          cudaSuccess)
+        blocks = 1;
+      return std::max(blocks, 1);
+    }();
     voronoi3_warp_kernel<<<device_sm_count() * per_sm, 32 * kV3WarpsPerBlock, 0, st>>>(
         g.reps, g.tasks, g.n_tasks * kBlock, (const int4*)b.S_pos, (const float4*)b.S_dir, b.S_id, grid_view3(b),
         (int4*)b.U_pos, (float4*)b.U_dir, b.U_id, b.counts, b.phi_acc, b.d_step, P, b.d_status, b.ovf_list,
